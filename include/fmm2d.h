@@ -1,0 +1,181 @@
+/*
+ * fmm2d.h -- C ABI of the GB300 (sm_103a) 2D vortex-particle fast multipole
+ * library.
+ *
+ * The library evaluates the velocity induced by N Gaussian-regularised
+ * vortex particles at the particles themselves, following Cruz & Barba,
+ * "Characterization of the errors of the Fast Multipole Method approximation
+ * in particle simulations" (2008):
+ *
+ *   u_sigma(x_i) = sum_{j != i} Gamma_j K_sigma(x_i - x_j)          (Eq. 7, Eq. 9)
+ *   K_sigma(x)   = (-y, x) (1 - exp(-r^2 / 2 sigma^2)) / (2 pi r^2)  (Eq. 6)
+ *
+ * approximated by the FMM of Sec. 3: a uniform quadtree of depth L (Sec. 3.3),
+ * p-term multipole and local expansions of the singular kernel in complex
+ * form (Eqs. 16-22), and the regularised kernel summed directly over each
+ * leaf's local list -- the leaf and its up to 8 neighbours (Eq. 10,
+ * Sec. 3.3.1).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - All pointers named *_dev are device pointers; *_host are host pointers.
+ *   The caller owns every buffer it passes; the library never frees them.
+ * - Positions are interleaved pairs (x0, y0, x1, y1, ...); velocities are
+ *   written the same way (u_x, u_y), in the input order of the particles.
+ * - The element type follows the plan's precision: double for FMM2D_FP64,
+ *   float for FMM2D_FP32 and FMM2D_FP32_TC.
+ * - Calls taking a cudaStream_t enqueue work on that stream and return
+ *   without synchronising unless stated otherwise.
+ * - Nothing crosses the ABI as an exception; every call returns a status.
+ *   Errors the device detects while running (a point outside the root box, a
+ *   non-finite input) are recorded in the plan and reported by
+ *   fmm2d_plan_check() once the stream has reached that point.
+ * - A plan is not thread-safe: calls on one plan must not overlap in time,
+ *   on the host or on the device.
+ */
+#ifndef FMM2D_H
+#define FMM2D_H
+
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FMM2D_OK = 0,
+    FMM2D_INVALID_ARG = 1,    /* p, L, n, sigma or root box out of range; null pointer */
+    FMM2D_OUT_OF_DOMAIN = 2,  /* a particle lies outside the closed root box */
+    FMM2D_NONFINITE = 3,      /* a position or circulation is NaN or infinite */
+    FMM2D_CUDA_ERROR = 4,     /* a CUDA runtime call failed */
+    FMM2D_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+    FMM2D_OUT_OF_MEMORY = 6,  /* workspace allocation failed */
+    FMM2D_UNSUPPORTED = 7     /* valid request this build does not serve */
+} fmm2d_status;
+
+typedef enum {
+    FMM2D_FP64 = 0,    /* every step in double precision */
+    FMM2D_FP32 = 1,    /* float storage and arithmetic; box-size-scaled expansions */
+    FMM2D_FP32_TC = 2  /* as FP32, with M2L as a 3xTF32 tensor-core contraction */
+} fmm2d_precision;
+
+typedef struct {
+    int p;            /* expansion terms, m = 0 .. p-1 (Eq. 21); 1 <= p <= 32 */
+    int L;            /* quadtree depth: leaves are the 4^L boxes of level L; 0 <= L <= 12 */
+    double sigma;     /* Gaussian core size of Eq. 3 / Eq. 6; > 0 */
+    int precision;    /* fmm2d_precision */
+    double x0, y0, W; /* root box [x0, x0 + W] x [y0, y0 + W]; W > 0 */
+    int64_t max_n;    /* largest particle count any call on this plan passes */
+} fmm2d_params;
+
+typedef struct fmm2d_plan fmm2d_plan;
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char* fmm2d_status_string(fmm2d_status s);
+
+/* Detail of the last error raised on the calling host thread (static or
+ * thread-local storage, never NULL; empty when there is none). */
+const char* fmm2d_last_error(void);
+
+/* Create a plan: validates the parameters, allocates the device workspace
+ * for up to max_n particles on the current device, and builds the
+ * translation tables (M2M of Sec. 3.3.2, M2L of Eq. 22, L2L of Sec. 3.3.3)
+ * in double precision on the device.  Synchronous.  On failure *out is set
+ * to NULL and nothing is leaked. */
+fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm);
+
+/* Release the plan and its workspace.  Synchronises the device first.
+ * NULL is accepted. */
+void fmm2d_plan_destroy(fmm2d_plan* plan);
+
+/* FMM velocity at every particle (Eq. 7 with Eq. 9, by the method of Sec. 3):
+ *   xy_dev    n interleaved positions, element type per precision
+ *   gamma_dev n circulations
+ *   uv_dev    n interleaved velocities (output; must not alias the inputs)
+ * 0 <= n <= max_n.  Steps, all on `stream`: Morton keys, stable radix sort
+ * and leaf ranges; P2M; M2M for levels L-1..2; M2L at levels 2..L over the
+ * interaction lists; L2L for levels 3..L; L2P plus the near-field sum over
+ * each leaf's local list.  The sequence is recorded once into a CUDA graph
+ * per (buffers, n) and replayed on later calls with the same arguments.
+ * Device-detected input errors: see fmm2d_plan_check(). */
+fmm2d_status fmm2d_velocity(fmm2d_plan* plan, int64_t n, const void* xy_dev,
+                            const void* gamma_dev, void* uv_dev, cudaStream_t stream);
+
+/* Same computation from host buffers: copies the inputs to the device, runs
+ * fmm2d_velocity on `stream`, copies the velocities back and synchronises
+ * `stream`.  Page-locked host buffers make the copies asynchronous with
+ * respect to other streams.  Returns the device-detected status as well. */
+fmm2d_status fmm2d_velocity_host(fmm2d_plan* plan, int64_t n, const void* xy_host,
+                                 const void* gamma_host, void* uv_host, cudaStream_t stream);
+
+/* Wait for `stream` and report (and clear) any input error the device
+ * recorded during earlier calls on this plan. */
+fmm2d_status fmm2d_plan_check(fmm2d_plan* plan, cudaStream_t stream);
+
+/* Quadtree of the last fmm2d_velocity call, for bit-exact checks
+ * (Sec. 3.3, Fig. 6).  Device outputs, each may be NULL to skip it:
+ *   keys_dev        n Morton keys in sorted order (leaf x index in the even
+ *                   bits, y index in the odd bits)
+ *   perm_dev        n input indices in sorted order (stable: equal keys keep
+ *                   input order)
+ *   leaf_start_dev  4^L + 1 offsets: leaf k holds sorted positions
+ *                   [leaf_start[k], leaf_start[k+1])
+ * Enqueued on `stream` after the call it describes. */
+fmm2d_status fmm2d_tree_debug(fmm2d_plan* plan, uint32_t* keys_dev, uint32_t* perm_dev,
+                              uint32_t* leaf_start_dev, cudaStream_t stream);
+
+/* Reference velocities in double precision at s sampled particles, by direct
+ * summation over all n particles (the accuracy yardstick of Sec. 5):
+ *   kernel 0  regularised kernel of Eq. 6 for every pair (Eq. 7 with Eq. 9)
+ *   kernel 1  the FMM's own limit: Eq. 6 for pairs in each other's 3x3 leaf
+ *             neighbourhood at the plan's L and root box, the singular kernel
+ *             of Eq. 27 for the rest (Eq. 10, Sec. 4.1)
+ *   xy_dev, gamma_dev  inputs in the plan's element type
+ *   target_idx_dev     s particle indices in [0, n)
+ *   uv_ref_dev         2 s doubles (output)
+ * Out-of-range indices are skipped and recorded as FMM2D_INVALID_ARG for
+ * fmm2d_plan_check(). */
+fmm2d_status fmm2d_direct_sampled(fmm2d_plan* plan, int kernel, int64_t n, const void* xy_dev,
+                                  const void* gamma_dev, int64_t s, const int64_t* target_idx_dev,
+                                  double* uv_ref_dev, cudaStream_t stream);
+
+/* Error statistics of an FMM result against sampled references, in double
+ * precision (the normalisation of Sec. 5.1: errors are divided by the
+ * maximum reference speed):
+ *   uv_dev         n velocities from fmm2d_velocity (plan element type)
+ *   target_idx_dev s particle indices; uv_ref_dev the 2 s reference values
+ *   stats_dev      4 doubles (output): max_i |du_i|, max_i |u_ref,i|,
+ *                  sum_i |du_i|^2, sum_i |u_ref,i|^2  (|.| the 2-norm)
+ *   leaf_err_dev   optional (may be NULL): 4^L doubles, the largest |du_i|
+ *                  among sampled particles of each leaf (0 where none);
+ *                  needs the tree of the last fmm2d_velocity call on the
+ *                  same positions.
+ * stats_dev and leaf_err_dev are overwritten, not accumulated. */
+fmm2d_status fmm2d_error_stats(fmm2d_plan* plan, int64_t n, const void* xy_dev, const void* uv_dev,
+                               int64_t s, const int64_t* target_idx_dev, const double* uv_ref_dev,
+                               double* stats_dev, double* leaf_err_dev, cudaStream_t stream);
+
+/* Per-phase device timing of fmm2d_velocity (tracing).  The phases of one
+ * evaluation, in order: 0 tree build (keys, radix sort, leaf ranges), 1 P2M,
+ * 2 M2M, 3 M2L, 4 L2L, 5 L2P plus near field. */
+#define FMM2D_NUM_PHASES 6
+
+/* ring > 0: every later fmm2d_velocity call records CUDA events at its phase
+ * boundaries (event-record nodes inside the CUDA graph) into the next of
+ * `ring` slots, so the last `ring` calls can be read back.  ring = 0 turns
+ * timing off.  Synchronises the device; 0 <= ring <= 4096. */
+fmm2d_status fmm2d_plan_set_timing(fmm2d_plan* plan, int ring);
+
+/* Phase durations in milliseconds of the call made `age` calls ago (0 = the
+ * latest), FMM2D_NUM_PHASES doubles written to ms_host.  Waits for that
+ * call's events.  FMM2D_INVALID_ARG when timing is off or the call has left
+ * the ring. */
+fmm2d_status fmm2d_plan_phase_ms(fmm2d_plan* plan, int age, double* ms_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM2D_H */

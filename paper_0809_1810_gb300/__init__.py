@@ -1,0 +1,174 @@
+"""GB300-native 2D vortex-particle FMM (Cruz & Barba 2008) -- Python binding.
+
+The computation lives in libfmm2d (hand-written CUDA for sm_103a behind the C
+ABI of include/fmm2d.h).  This module only marshals torch tensors (device
+memory and the current CUDA stream) into those calls.
+
+    plan = Plan(p=16, L=7, sigma=2 * h, precision="fp32")
+    uv = plan.velocity(xy, gamma)          # xy (n, 2), gamma (n,) on cuda:0
+
+Everything raises :class:`FMMError` on a non-OK status.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _native
+from ._native import FP32, FP32_TC, FP64, NUM_PHASES, PHASES
+
+__all__ = ["Plan", "FMMError", "FP64", "FP32", "FP32_TC", "PHASES", "library"]
+
+_PREC = {"fp64": FP64, "fp32": FP32, "fp32_tc": FP32_TC}
+
+
+class FMMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = _native.load()
+        name = lib.fmm2d_status_string(status).decode()
+        detail = lib.fmm2d_last_error().decode()
+        super().__init__(f"{where}: {name} ({detail})" if detail else f"{where}: {name}")
+        self.status = status
+
+
+def library():
+    """The loaded ctypes library (built in-tree on first use)."""
+    return _native.load()
+
+
+def _check(status: int, where: str):
+    if status != _native.OK:
+        raise FMMError(status, where)
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr() if t is not None else 0)
+
+
+class Plan:
+    """An FMM configuration (p, L, sigma, precision, root box) and its device
+    workspace for up to ``max_n`` particles (fmm2d_plan_create)."""
+
+    def __init__(self, p: int, L: int, sigma: float, precision="fp32",
+                 root=(-1.0, -1.0, 2.0), max_n: int = 1 << 20):
+        self._lib = _native.load()
+        self.p, self.L, self.sigma = int(p), int(L), float(sigma)
+        self.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+        self.dtype = torch.float64 if self.precision == FP64 else torch.float32
+        self.root = tuple(float(v) for v in root)
+        self.max_n = int(max_n)
+        prm = _native.Params(self.p, self.L, self.sigma, self.precision, self.root[0],
+                             self.root[1], self.root[2], self.max_n)
+        h = ctypes.c_void_p()
+        _check(self._lib.fmm2d_plan_create(ctypes.byref(h), ctypes.byref(prm)), "plan_create")
+        self._h = h
+
+    # -- lifetime ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.fmm2d_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- helpers -----------------------------------------------------------
+    def _inputs(self, xy, gamma):
+        if xy.dtype != self.dtype or gamma.dtype != self.dtype:
+            raise TypeError(f"inputs must be {self.dtype}")
+        if not (xy.is_cuda and gamma.is_cuda):
+            raise TypeError("inputs must be CUDA tensors")
+        xy = xy.contiguous()
+        gamma = gamma.contiguous()
+        n = gamma.shape[0]
+        if xy.numel() != 2 * n:
+            raise ValueError("xy must hold 2 n values")
+        return xy, gamma, n
+
+    # -- the FMM -------------------------------------------------------------
+    def velocity(self, xy, gamma, out=None, stream=None, check=False):
+        """Velocities (n, 2) at the particles (fmm2d_velocity)."""
+        xy, gamma, n = self._inputs(xy, gamma)
+        if out is None:
+            out = torch.empty((n, 2), dtype=self.dtype, device=xy.device)
+        _check(self._lib.fmm2d_velocity(self._h, n, _ptr(xy), _ptr(gamma), _ptr(out),
+                                        _stream(stream)), "velocity")
+        if check:
+            self.check(stream)
+        return out
+
+    def velocity_host(self, xy, gamma, out, stream=None):
+        """Host-buffer form (fmm2d_velocity_host): xy, gamma, out are CPU
+        tensors (page-locked for asynchronous copies); synchronous."""
+        n = gamma.shape[0]
+        for t in (xy, gamma, out):
+            if t.is_cuda or t.dtype != self.dtype or not t.is_contiguous():
+                raise TypeError("host tensors of the plan dtype, contiguous")
+        _check(self._lib.fmm2d_velocity_host(self._h, n, _ptr(xy), _ptr(gamma), _ptr(out),
+                                             _stream(stream)), "velocity_host")
+        return out
+
+    def check(self, stream=None):
+        """Raise if the device recorded an input error (fmm2d_plan_check)."""
+        _check(self._lib.fmm2d_plan_check(self._h, _stream(stream)), "plan_check")
+
+    def tree(self, n, stream=None):
+        """(sorted keys, permutation, leaf_start) of the last evaluation."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        keys = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        perm = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        start = torch.empty((1 << (2 * self.L)) + 1, dtype=torch.int32, device=dev)
+        _check(self._lib.fmm2d_tree_debug(self._h, _ptr(keys), _ptr(perm), _ptr(start),
+                                          _stream(stream)), "tree_debug")
+        return keys[:n], perm[:n], start
+
+    # -- yardsticks ----------------------------------------------------------
+    def direct_sampled(self, xy, gamma, targets, kernel=0, stream=None):
+        """FP64 direct velocities (s, 2) at sampled particle indices:
+        kernel 0 regularised everywhere, 1 the FMM's hybrid limit."""
+        xy, gamma, n = self._inputs(xy, gamma)
+        targets = targets.to(device=xy.device, dtype=torch.int64).contiguous()
+        out = torch.empty((targets.shape[0], 2), dtype=torch.float64, device=xy.device)
+        _check(self._lib.fmm2d_direct_sampled(self._h, int(kernel), n, _ptr(xy), _ptr(gamma),
+                                              targets.shape[0], _ptr(targets), _ptr(out),
+                                              _stream(stream)), "direct_sampled")
+        return out
+
+    def error_stats(self, xy, uv, targets, uv_ref, per_leaf=False, stream=None):
+        """(max|du|, max|u_ref|, sum|du|^2, sum|u_ref|^2) as a float64 device
+        tensor, plus per-leaf max |du| when per_leaf is set."""
+        n = uv.shape[0]
+        targets = targets.to(device=uv.device, dtype=torch.int64).contiguous()
+        stats = torch.empty(4, dtype=torch.float64, device=uv.device)
+        leaf = (torch.empty(1 << (2 * self.L), dtype=torch.float64, device=uv.device)
+                if per_leaf else None)
+        _check(self._lib.fmm2d_error_stats(self._h, n, _ptr(xy.contiguous()),
+                                           _ptr(uv.contiguous()), targets.shape[0],
+                                           _ptr(targets), _ptr(uv_ref.contiguous()), _ptr(stats),
+                                           _ptr(leaf), _stream(stream)), "error_stats")
+        return (stats, leaf) if per_leaf else stats
+
+    # -- tracing ---------------------------------------------------------------
+    def set_timing(self, ring: int):
+        _check(self._lib.fmm2d_plan_set_timing(self._h, int(ring)), "set_timing")
+
+    def phase_ms(self, age: int = 0):
+        buf = (ctypes.c_double * NUM_PHASES)()
+        _check(self._lib.fmm2d_plan_phase_ms(self._h, int(age), buf), "phase_ms")
+        return dict(zip(PHASES, list(buf)))

@@ -1,0 +1,71 @@
+"""ctypes view of libfmm2d (include/fmm2d.h).  Argument marshalling only:
+every step of the computation runs in the library's CUDA kernels.  There is
+no fallback: if the library is missing the import fails loudly."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import build as _build
+
+OK, INVALID_ARG, OUT_OF_DOMAIN, NONFINITE, CUDA_ERROR, TIMEOUT, OUT_OF_MEMORY, UNSUPPORTED = range(8)
+FP64, FP32, FP32_TC = 0, 1, 2
+NUM_PHASES = 6
+PHASES = ("tree", "p2m", "m2m", "m2l", "l2l", "p2p_l2p")
+
+HEADER = os.path.join(_build.INCLUDE, "fmm2d.h")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("L", ctypes.c_int), ("sigma", ctypes.c_double),
+                ("precision", ctypes.c_int), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+                ("W", ctypes.c_double), ("max_n", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def declared_functions():
+    """Names of the functions include/fmm2d.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fmm2d_[a-z_0-9]+)\s*\(", text)))
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"libfmm2d not built: {path} is missing")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sigs = {
+        "fmm2d_status_string": ([i32], ctypes.c_char_p),
+        "fmm2d_last_error": ([], ctypes.c_char_p),
+        "fmm2d_plan_create": ([ctypes.POINTER(vp), ctypes.POINTER(Params)], i32),
+        "fmm2d_plan_destroy": ([vp], None),
+        "fmm2d_velocity": ([vp, i64, vp, vp, vp, vp], i32),
+        "fmm2d_velocity_host": ([vp, i64, vp, vp, vp, vp], i32),
+        "fmm2d_plan_check": ([vp, vp], i32),
+        "fmm2d_tree_debug": ([vp, vp, vp, vp, vp], i32),
+        "fmm2d_direct_sampled": ([vp, i32, i64, vp, vp, i64, vp, vp, vp], i32),
+        "fmm2d_error_stats": ([vp, i64, vp, vp, i64, vp, vp, vp, vp, vp], i32),
+        "fmm2d_plan_set_timing": ([vp, i32], i32),
+        "fmm2d_plan_phase_ms": ([vp, i32, vp], i32),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib

@@ -1,0 +1,491 @@
+// C ABI of the library (include/fmm2d.h): plans, workspace, the evaluation
+// sequence of Sec. 3.1 / Fig. 3 recorded into a CUDA graph, and the
+// accuracy yardsticks.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fmm2d_internal.cuh"
+
+using namespace fmm2d;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+fmm2d_status fail(fmm2d_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+fmm2d_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(e == cudaErrorMemoryAllocation ? FMM2D_OUT_OF_MEMORY : FMM2D_CUDA_ERROR,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+int status_from_flags(int flags) {
+    if (flags & kFlagNonfinite) return FMM2D_NONFINITE;
+    if (flags & kFlagOutOfDomain) return FMM2D_OUT_OF_DOMAIN;
+    if (flags & kFlagInvalid) return FMM2D_INVALID_ARG;
+    if (flags & kFlagTimeout) return FMM2D_TIMEOUT;
+    return FMM2D_OK;
+}
+
+}  // namespace
+
+static constexpr int kPhases = FMM2D_NUM_PHASES;
+
+struct fmm2d_plan {
+    fmm2d_params prm{};
+    Geometry geo{};
+    int device = 0;
+    size_t elem = 0;  // bytes per real
+    // workspace
+    void* ws = nullptr;
+    SortBuffers sb{};
+    void* particles = nullptr;
+    void* me = nullptr;
+    void* le = nullptr;
+    double* tab64 = nullptr;
+    float* tab32 = nullptr;
+    int* d_status = nullptr;
+    int* h_status = nullptr;
+    // host-call staging
+    void* st_xy = nullptr;
+    void* st_gamma = nullptr;
+    void* st_uv = nullptr;
+    // graph cache
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void* g_xy = nullptr;
+    const void* g_gamma = nullptr;
+    void* g_uv = nullptr;
+    int64_t g_n = -1;
+    // timing
+    int ring = 0;
+    int64_t calls = 0;
+    std::vector<cudaEvent_t> ev;        // ring * (kPhases + 1)
+    cudaEvent_t ev_mark[kPhases + 1]{}; // placeholders captured into the graph
+    cudaGraphNode_t ev_node[kPhases + 1]{};
+    bool graph_timed = false;
+};
+
+namespace {
+
+template <typename R>
+Tables<R> tables_of(const fmm2d_plan* pl);
+template <>
+Tables<double> tables_of<double>(const fmm2d_plan* pl) {
+    int64_t per = (int64_t)pl->geo.P * pl->geo.P * 2;
+    return {pl->tab64, pl->tab64 + 4 * per, pl->tab64 + 8 * per};
+}
+template <>
+Tables<float> tables_of<float>(const fmm2d_plan* pl) {
+    int64_t per = (int64_t)pl->geo.P * pl->geo.P * 2;
+    return {pl->tab32, pl->tab32 + 4 * per, pl->tab32 + 8 * per};
+}
+
+// Record phase-boundary event `k` (external record node inside a graph).
+cudaError_t mark(fmm2d_plan* pl, int k, cudaStream_t s) {
+    if (!pl->ring) return cudaSuccess;
+    return cudaEventRecordWithFlags(pl->ev_mark[k], s, cudaEventRecordExternal);
+}
+
+// The evaluation sequence of Sec. 3.1 on stream s.
+template <typename R>
+cudaError_t enqueue(fmm2d_plan* pl, int64_t n, const R* xy, const R* gamma, R* uv,
+                    cudaStream_t s) {
+    const Geometry& g = pl->geo;
+    Tables<R> t = tables_of<R>(pl);
+    R* me = static_cast<R*>(pl->me);
+    R* le = static_cast<R*>(pl->le);
+    cudaError_t e;
+#define STEP(x)                         \
+    if ((e = (x)) != cudaSuccess) return e;
+    STEP(mark(pl, 0, s));
+    STEP(launch_tree_build<R>(g, n, xy, gamma, pl->sb, pl->particles, s));
+    STEP(mark(pl, 1, s));
+    if (g.L >= 2) STEP(launch_p2m<R>(g, pl->particles, pl->sb.leaf_start, me, s));
+    STEP(mark(pl, 2, s));
+    for (int l = g.L - 1; l >= 2; --l) STEP(launch_m2m<R>(g, l, t, me, s));
+    STEP(mark(pl, 3, s));
+    if (g.L >= 2) STEP(launch_m2l<R>(g, t, me, le, s));
+    STEP(mark(pl, 4, s));
+    for (int l = 3; l <= g.L; ++l) STEP(launch_l2l<R>(g, l, t, le, s));
+    STEP(mark(pl, 5, s));
+    STEP(launch_p2p_l2p<R>(g, pl->prm.sigma, pl->particles, pl->sb.leaf_start, le, uv, s));
+    STEP(mark(pl, 6, s));
+#undef STEP
+    return cudaSuccess;
+}
+
+void drop_graph(fmm2d_plan* pl) {
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    pl->exec = nullptr;
+    pl->graph = nullptr;
+    pl->g_n = -1;
+}
+
+fmm2d_status record_graph(fmm2d_plan* pl, int64_t n, const void* xy, const void* gamma, void* uv) {
+    drop_graph(pl);
+    CK(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = pl->elem == 8
+                        ? enqueue<double>(pl, n, static_cast<const double*>(xy),
+                                          static_cast<const double*>(gamma),
+                                          static_cast<double*>(uv), pl->cap)
+                        : enqueue<float>(pl, n, static_cast<const float*>(xy),
+                                         static_cast<const float*>(gamma), static_cast<float*>(uv),
+                                         pl->cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(pl->cap, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(e, "kernel launch during capture");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    pl->graph = graph;
+    CK(cudaGraphInstantiate(&pl->exec, graph, 0));
+    pl->graph_timed = pl->ring > 0;
+    if (pl->graph_timed) {
+        // find the event-record nodes of the phase marks
+        size_t count = 0;
+        CK(cudaGraphGetNodes(graph, nullptr, &count));
+        std::vector<cudaGraphNode_t> nodes(count);
+        CK(cudaGraphGetNodes(graph, nodes.data(), &count));
+        for (auto& nd : pl->ev_node) nd = nullptr;
+        for (size_t i = 0; i < count; ++i) {
+            cudaGraphNodeType ty;
+            CK(cudaGraphNodeGetType(nodes[i], &ty));
+            if (ty != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t evn;
+            CK(cudaGraphEventRecordNodeGetEvent(nodes[i], &evn));
+            for (int k = 0; k <= kPhases; ++k)
+                if (evn == pl->ev_mark[k]) pl->ev_node[k] = nodes[i];
+        }
+        for (int k = 0; k <= kPhases; ++k)
+            if (!pl->ev_node[k]) return fail(FMM2D_CUDA_ERROR, "timing node missing from graph");
+    }
+    pl->g_xy = xy;
+    pl->g_gamma = gamma;
+    pl->g_uv = uv;
+    pl->g_n = n;
+    return FMM2D_OK;
+}
+
+fmm2d_status run(fmm2d_plan* pl, int64_t n, const void* xy, const void* gamma, void* uv,
+                 cudaStream_t stream) {
+    bool timed = pl->ring > 0;
+    if (!pl->exec || pl->g_xy != xy || pl->g_gamma != gamma || pl->g_uv != uv || pl->g_n != n ||
+        pl->graph_timed != timed) {
+        fmm2d_status st = record_graph(pl, n, xy, gamma, uv);
+        if (st != FMM2D_OK) return st;
+    }
+    if (timed) {
+        int slot = (int)(pl->calls % pl->ring);
+        for (int k = 0; k <= kPhases; ++k)
+            CK(cudaGraphExecEventRecordNodeSetEvent(pl->exec, pl->ev_node[k],
+                                                    pl->ev[slot * (kPhases + 1) + k]));
+    }
+    CK(cudaGraphLaunch(pl->exec, stream));
+    pl->calls++;
+    return FMM2D_OK;
+}
+
+bool valid_params(const fmm2d_params* p, std::string* why) {
+    if (!p) return *why = "null params", false;
+    if (p->p < 1 || p->p > kMaxP) return *why = "p must be in [1, 32]", false;
+    if (p->L < 0 || p->L > kMaxL) return *why = "L must be in [0, 12]", false;
+    if (!(p->sigma > 0.0) || !std::isfinite(p->sigma)) return *why = "sigma must be > 0", false;
+    if (!(p->W > 0.0) || !std::isfinite(p->W) || !std::isfinite(p->x0) || !std::isfinite(p->y0))
+        return *why = "root box must be finite with W > 0", false;
+    if (p->precision < FMM2D_FP64 || p->precision > FMM2D_FP32_TC)
+        return *why = "unknown precision", false;
+    if (p->max_n < 0 || p->max_n > (int64_t)0xFFFFFFFF) return *why = "max_n out of range", false;
+    return true;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" {
+
+const char* fmm2d_status_string(fmm2d_status s) {
+    switch (s) {
+        case FMM2D_OK: return "ok";
+        case FMM2D_INVALID_ARG: return "invalid argument";
+        case FMM2D_OUT_OF_DOMAIN: return "particle outside the root box";
+        case FMM2D_NONFINITE: return "non-finite input";
+        case FMM2D_CUDA_ERROR: return "CUDA error";
+        case FMM2D_TIMEOUT: return "device wait timed out";
+        case FMM2D_OUT_OF_MEMORY: return "out of device memory";
+        case FMM2D_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* fmm2d_last_error(void) { return g_last_error.c_str(); }
+
+fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
+    if (!out) return fail(FMM2D_INVALID_ARG, "null output pointer");
+    *out = nullptr;
+    std::string why;
+    if (!valid_params(prm, &why)) return fail(FMM2D_INVALID_ARG, why);
+    if (prm->precision == FMM2D_FP32_TC)
+        return fail(FMM2D_UNSUPPORTED, "FP32_TC precision is not available in this build");
+    auto* pl = new fmm2d_plan();
+    pl->prm = *prm;
+    pl->elem = prm->precision == FMM2D_FP64 ? 8 : 4;
+    Geometry& g = pl->geo;
+    g.x0 = prm->x0;
+    g.y0 = prm->y0;
+    g.W = prm->W;
+    g.L = prm->L;
+    g.p = prm->p;
+    g.P = prm->p <= 16 ? 16 : 32;
+    int64_t acc = 0;
+    for (int l = 0; l <= kMaxL + 1; ++l) g.level_base[l] = 0;
+    for (int l = 2; l <= g.L + 1; ++l) {
+        g.level_base[l] = acc;
+        if (l <= g.L) acc += (int64_t)1 << (2 * l);
+    }
+    g.nboxes = acc;
+
+    auto cleanup = [&](fmm2d_status s) {
+        fmm2d_plan_destroy(pl);
+        return s;
+    };
+    if (cudaGetDevice(&pl->device) != cudaSuccess)
+        return cleanup(fail(FMM2D_CUDA_ERROR, "no current CUDA device"));
+
+    int64_t nmax = prm->max_n > 0 ? prm->max_n : 1;
+    int64_t nblocks = (nmax + kSortTile - 1) / kSortTile;
+    int64_t nleaf = (int64_t)1 << (2 * g.L);
+    size_t psize = pl->elem == 8 ? sizeof(ParticleD) : sizeof(float4);
+    size_t tab_count = (size_t)(8 + kOffsetSlots) * g.P * g.P * 2;
+    size_t sizes[] = {
+        align256(nmax * 4), align256(nmax * 4), align256(nmax * 4), align256(nmax * 4),
+        align256(nmax * 4),                                   // keys x2, vals x2, perm
+        align256((size_t)kRadix * nblocks * 4),               // hist
+        align256((size_t)(nleaf + 1) * 4),                    // leaf_start
+        align256(nmax * psize),                               // particles
+        align256((size_t)(g.nboxes > 0 ? g.nboxes : 1) * 2 * g.P * pl->elem),  // me
+        align256((size_t)(g.nboxes > 0 ? g.nboxes : 1) * 2 * g.P * pl->elem),  // le
+        align256(tab_count * 8),                              // tables fp64
+        align256(tab_count * 4),                              // tables fp32
+        align256((size_t)(2 * g.P + 1) * (2 * g.P + 1) * 8),  // binomials
+        256,                                                  // status
+    };
+    size_t total = 0;
+    for (size_t s : sizes) total += s;
+    cudaError_t e = cudaMalloc(&pl->ws, total);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "workspace cudaMalloc"));
+    char* p = static_cast<char*>(pl->ws);
+    void* slots[14];
+    for (int i = 0; i < 14; ++i) {
+        slots[i] = p;
+        p += sizes[i];
+    }
+    pl->sb.keys[0] = (uint32_t*)slots[0];
+    pl->sb.keys[1] = (uint32_t*)slots[1];
+    pl->sb.vals[0] = (uint32_t*)slots[2];
+    pl->sb.vals[1] = (uint32_t*)slots[3];
+    pl->sb.perm = (uint32_t*)slots[4];
+    pl->sb.hist = (uint32_t*)slots[5];
+    pl->sb.leaf_start = (uint32_t*)slots[6];
+    pl->particles = slots[7];
+    pl->me = slots[8];
+    pl->le = slots[9];
+    pl->tab64 = (double*)slots[10];
+    pl->tab32 = (float*)slots[11];
+    double* binom = (double*)slots[12];
+    pl->d_status = (int*)slots[13];
+    pl->sb.status = pl->d_status;
+
+    e = cudaHostAlloc((void**)&pl->h_status, sizeof(int), cudaHostAllocDefault);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaHostAlloc"));
+    e = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamCreate"));
+    e = cudaMemsetAsync(pl->d_status, 0, sizeof(int), pl->cap);
+    if (e == cudaSuccess) {
+        int64_t per = (int64_t)g.P * g.P * 2;
+        e = launch_build_tables(g.p, g.P, pl->tab64, pl->tab64 + 4 * per, pl->tab64 + 8 * per,
+                                binom, pl->cap);
+    }
+    if (e == cudaSuccess) e = launch_tables_to_f32(pl->tab64, pl->tab32, (int64_t)tab_count, pl->cap);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pl->cap);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "table build"));
+    for (int k = 0; k <= kPhases; ++k) {
+        e = cudaEventCreate(&pl->ev_mark[k]);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaEventCreate"));
+    }
+    *out = pl;
+    return FMM2D_OK;
+}
+
+void fmm2d_plan_destroy(fmm2d_plan* pl) {
+    if (!pl) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(pl->device);
+    cudaDeviceSynchronize();
+    drop_graph(pl);
+    for (auto ev : pl->ev) cudaEventDestroy(ev);
+    for (auto ev : pl->ev_mark)
+        if (ev) cudaEventDestroy(ev);
+    if (pl->cap) cudaStreamDestroy(pl->cap);
+    if (pl->h_status) cudaFreeHost(pl->h_status);
+    if (pl->st_xy) cudaFree(pl->st_xy);
+    if (pl->ws) cudaFree(pl->ws);
+    cudaSetDevice(cur);
+    delete pl;
+}
+
+fmm2d_status fmm2d_velocity(fmm2d_plan* pl, int64_t n, const void* xy, const void* gamma,
+                            void* uv, cudaStream_t stream) {
+    if (!pl) return fail(FMM2D_INVALID_ARG, "null plan");
+    if (n < 0 || n > pl->prm.max_n) return fail(FMM2D_INVALID_ARG, "n out of [0, max_n]");
+    if (n > 0 && (!xy || !gamma || !uv)) return fail(FMM2D_INVALID_ARG, "null buffer");
+    return run(pl, n, xy, gamma, uv, stream);
+}
+
+fmm2d_status fmm2d_plan_check(fmm2d_plan* pl, cudaStream_t stream) {
+    if (!pl) return fail(FMM2D_INVALID_ARG, "null plan");
+    CK(cudaMemcpyAsync(pl->h_status, pl->d_status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemsetAsync(pl->d_status, 0, sizeof(int), stream));
+    CK(cudaStreamSynchronize(stream));
+    int st = status_from_flags(*pl->h_status);
+    if (st != FMM2D_OK) return fail((fmm2d_status)st, "device reported an input error");
+    return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_velocity_host(fmm2d_plan* pl, int64_t n, const void* xy_host,
+                                 const void* gamma_host, void* uv_host, cudaStream_t stream) {
+    if (!pl) return fail(FMM2D_INVALID_ARG, "null plan");
+    if (n < 0 || n > pl->prm.max_n) return fail(FMM2D_INVALID_ARG, "n out of [0, max_n]");
+    if (n > 0 && (!xy_host || !gamma_host || !uv_host)) return fail(FMM2D_INVALID_ARG, "null buffer");
+    if (!pl->st_xy) {
+        size_t nm = (size_t)(pl->prm.max_n > 0 ? pl->prm.max_n : 1);
+        size_t bxy = align256(2 * nm * pl->elem), bg = align256(nm * pl->elem);
+        void* buf = nullptr;
+        CK(cudaMalloc(&buf, 2 * bxy + bg));
+        pl->st_xy = buf;
+        pl->st_gamma = static_cast<char*>(buf) + bxy;
+        pl->st_uv = static_cast<char*>(buf) + bxy + bg;
+    }
+    if (n > 0) {
+        CK(cudaMemcpyAsync(pl->st_xy, xy_host, 2 * n * pl->elem, cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(pl->st_gamma, gamma_host, n * pl->elem, cudaMemcpyHostToDevice, stream));
+    }
+    fmm2d_status st = run(pl, n, pl->st_xy, pl->st_gamma, pl->st_uv, stream);
+    if (st != FMM2D_OK) return st;
+    if (n > 0)
+        CK(cudaMemcpyAsync(uv_host, pl->st_uv, 2 * n * pl->elem, cudaMemcpyDeviceToHost, stream));
+    return fmm2d_plan_check(pl, stream);
+}
+
+fmm2d_status fmm2d_tree_debug(fmm2d_plan* pl, uint32_t* keys, uint32_t* perm,
+                              uint32_t* leaf_start, cudaStream_t stream) {
+    if (!pl) return fail(FMM2D_INVALID_ARG, "null plan");
+    if (pl->g_n < 0) return fail(FMM2D_INVALID_ARG, "no evaluation has run on this plan");
+    int64_t n = pl->g_n;
+    int bits = 2 * pl->geo.L;
+    int passes = bits <= kRadixBits ? 1 : (bits + kRadixBits - 1) / kRadixBits;
+    const uint32_t* sorted = pl->sb.keys[passes & 1];
+    if (keys && n > 0)
+        CK(cudaMemcpyAsync(keys, sorted, n * 4, cudaMemcpyDeviceToDevice, stream));
+    if (perm && n > 0)
+        CK(cudaMemcpyAsync(perm, pl->sb.perm, n * 4, cudaMemcpyDeviceToDevice, stream));
+    if (leaf_start)
+        CK(cudaMemcpyAsync(leaf_start, pl->sb.leaf_start, (((size_t)1 << (2 * pl->geo.L)) + 1) * 4,
+                           cudaMemcpyDeviceToDevice, stream));
+    return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_direct_sampled(fmm2d_plan* pl, int kernel, int64_t n, const void* xy,
+                                  const void* gamma, int64_t s, const int64_t* targets,
+                                  double* uv_ref, cudaStream_t stream) {
+    if (!pl) return fail(FMM2D_INVALID_ARG, "null plan");
+    if (kernel != 0 && kernel != 1) return fail(FMM2D_INVALID_ARG, "kernel must be 0 or 1");
+    if (n < 0 || s < 0) return fail(FMM2D_INVALID_ARG, "negative size");
+    if (s > 0 && (!xy || !gamma || !targets || !uv_ref))
+        return fail(FMM2D_INVALID_ARG, "null buffer");
+    cudaError_t e =
+        pl->elem == 8
+            ? launch_direct_sampled<double>(pl->geo, pl->prm.sigma, kernel, n,
+                                            static_cast<const double*>(xy),
+                                            static_cast<const double*>(gamma), s, targets, uv_ref,
+                                            pl->d_status, stream)
+            : launch_direct_sampled<float>(pl->geo, pl->prm.sigma, kernel, n,
+                                           static_cast<const float*>(xy),
+                                           static_cast<const float*>(gamma), s, targets, uv_ref,
+                                           pl->d_status, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "direct_sampled launch");
+    return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_error_stats(fmm2d_plan* pl, int64_t n, const void* xy, const void* uv,
+                               int64_t s, const int64_t* targets, const double* uv_ref,
+                               double* stats, double* leaf_err, cudaStream_t stream) {
+    if (!pl) return fail(FMM2D_INVALID_ARG, "null plan");
+    if (n < 0 || s < 0) return fail(FMM2D_INVALID_ARG, "negative size");
+    if (!stats || (s > 0 && (!xy || !uv || !targets || !uv_ref)))
+        return fail(FMM2D_INVALID_ARG, "null buffer");
+    cudaError_t e =
+        pl->elem == 8
+            ? launch_error_stats<double>(pl->geo, n, static_cast<const double*>(xy),
+                                         static_cast<const double*>(uv), s, targets, uv_ref, stats,
+                                         leaf_err, pl->d_status, stream)
+            : launch_error_stats<float>(pl->geo, n, static_cast<const float*>(xy),
+                                        static_cast<const float*>(uv), s, targets, uv_ref, stats,
+                                        leaf_err, pl->d_status, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "error_stats launch");
+    return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_plan_set_timing(fmm2d_plan* pl, int ring) {
+    if (!pl) return fail(FMM2D_INVALID_ARG, "null plan");
+    if (ring < 0 || ring > 4096) return fail(FMM2D_INVALID_ARG, "ring must be in [0, 4096]");
+    CK(cudaDeviceSynchronize());
+    for (auto ev : pl->ev) cudaEventDestroy(ev);
+    pl->ev.clear();
+    pl->ring = 0;
+    pl->calls = 0;
+    for (int i = 0; i < ring * (kPhases + 1); ++i) {
+        cudaEvent_t ev;
+        CK(cudaEventCreate(&ev));
+        pl->ev.push_back(ev);
+    }
+    pl->ring = ring;
+    drop_graph(pl);
+    return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_plan_phase_ms(fmm2d_plan* pl, int age, double* ms) {
+    if (!pl || !ms) return fail(FMM2D_INVALID_ARG, "null argument");
+    if (!pl->ring) return fail(FMM2D_INVALID_ARG, "timing is off");
+    if (age < 0 || age >= pl->ring || age >= pl->calls)
+        return fail(FMM2D_INVALID_ARG, "no such call in the timing ring");
+    int slot = (int)((pl->calls - 1 - age) % pl->ring);
+    cudaEvent_t* e = &pl->ev[slot * (kPhases + 1)];
+    CK(cudaEventSynchronize(e[kPhases]));
+    for (int k = 0; k < kPhases; ++k) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e[k], e[k + 1]));
+        ms[k] = t;
+    }
+    return FMM2D_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,209 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Not part of the ABI: everything callers see is in include/fmm2d.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fmm2d.h"
+
+namespace fmm2d {
+
+constexpr int kMaxP = 32;      // largest expansion order served
+constexpr int kMaxL = 12;      // deepest quadtree level served
+constexpr int kRadixBits = 8;  // radix sort digit width
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;  // keys per thread per tile
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+// Device-side status flags (bitwise OR of 1 << fmm2d_status).
+constexpr int kFlagOutOfDomain = 1 << FMM2D_OUT_OF_DOMAIN;
+constexpr int kFlagNonfinite = 1 << FMM2D_NONFINITE;
+constexpr int kFlagInvalid = 1 << FMM2D_INVALID_ARG;
+constexpr int kFlagTimeout = 1 << FMM2D_TIMEOUT;
+
+// Offset tables index the 7 x 7 source-minus-target box offsets (dx, dy) in
+// [-3, 3]^2; the 40 with max(|dx|, |dy|) >= 2 are M2L offsets.
+constexpr int kOffsetSlots = 49;
+__host__ __device__ inline int offset_slot(int dx, int dy) { return (dy + 3) * 7 + (dx + 3); }
+
+// Sorted particle record: position, circulation and input index.
+struct __align__(32) ParticleD {
+    double x, y, z, w;  // position, circulation, input index (an integer below 2^53)
+};
+template <typename R>
+struct ParticleOf;
+template <>
+struct ParticleOf<float> {
+    using type = float4;  // (x, y, Gamma, input index as uint bits)
+    __device__ static inline type make(float x, float y, float g, uint32_t i) {
+        return make_float4(x, y, g, __uint_as_float(i));
+    }
+    __device__ static inline uint32_t index(const type& q) { return __float_as_uint(q.w); }
+};
+template <>
+struct ParticleOf<double> {
+    using type = ParticleD;
+    __device__ static inline type make(double x, double y, double g, uint32_t i) {
+        return ParticleD{x, y, g, (double)i};
+    }
+    __device__ static inline uint32_t index(const type& q) { return (uint32_t)q.w; }
+};
+
+// Geometry shared by the kernels of one evaluation.
+struct Geometry {
+    double x0, y0, W;  // root box
+    int L;             // leaf level
+    int p;             // expansion terms
+    int P;             // padded terms per box in expansion arrays (16 or 32)
+    int64_t level_base[kMaxL + 2];  // first box slot of level l (l >= 2)
+    int64_t nboxes;    // box slots over levels 2..L
+};
+
+// Expansion-array slot of box (ix, iy) at level l >= 2.  Each level is
+// stored as four parity planes (ix & 1, iy & 1), each a row-major grid of
+// (2^(l-1))^2 boxes, so that a fixed box offset maps a run of same-parity
+// target boxes onto a run of source boxes.
+__host__ __device__ inline int64_t box_slot(const int64_t* level_base, int l, uint32_t ix,
+                                            uint32_t iy) {
+    uint32_t h = 1u << (l - 1);
+    uint32_t plane = ((iy & 1u) << 1) | (ix & 1u);
+    return level_base[l] + ((int64_t)(plane * h + (iy >> 1)) * h + (ix >> 1));
+}
+
+__host__ __device__ inline uint32_t morton_spread(uint32_t v) {
+    v &= 0xFFFFu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+__host__ __device__ inline uint32_t morton_compact(uint32_t v) {
+    v &= 0x55555555u;
+    v = (v | (v >> 1)) & 0x33333333u;
+    v = (v | (v >> 2)) & 0x0F0F0F0Fu;
+    v = (v | (v >> 4)) & 0x00FF00FFu;
+    v = (v | (v >> 8)) & 0x0000FFFFu;
+    return v;
+}
+
+__host__ __device__ inline uint32_t morton_key(uint32_t ix, uint32_t iy) {
+    return morton_spread(ix) | (morton_spread(iy) << 1);
+}
+
+// Translation tables in the precision of the evaluation, complex entries as
+// (re, im) pairs, each matrix stored [k][n] (input index major) so that the
+// lanes of a warp, one per output coefficient n, read consecutive entries.
+template <typename R>
+struct Tables {
+    const R* m2m;  // [4 quadrants][P][P] complex: child quadrant (cy*2+cx)
+    const R* l2l;  // [4 quadrants][P][P] complex
+    const R* m2l;  // [49 offset slots][P][P] complex
+};
+
+// Host launchers (one translation unit each).
+cudaError_t launch_build_tables(int p, int P, double* m2m, double* l2l, double* m2l,
+                                double* binom_scratch, cudaStream_t s);
+cudaError_t launch_tables_to_f32(const double* src, float* dst, int64_t count, cudaStream_t s);
+
+struct SortBuffers {
+    uint32_t* keys[2];
+    uint32_t* vals[2];
+    uint32_t* hist;      // kRadix * nblocks
+    uint32_t* leaf_start;
+    uint32_t* perm;      // sorted input index
+    int* status;
+};
+
+template <typename R>
+cudaError_t launch_tree_build(const Geometry& g, int64_t n, const R* xy, const R* gamma,
+                              SortBuffers& sb, void* particles, cudaStream_t s);
+
+template <typename R>
+cudaError_t launch_p2m(const Geometry& g, const void* particles, const uint32_t* leaf_start,
+                       R* me, cudaStream_t s);
+template <typename R>
+cudaError_t launch_m2m(const Geometry& g, int level, const Tables<R>& t, R* me, cudaStream_t s);
+template <typename R>
+cudaError_t launch_m2l(const Geometry& g, const Tables<R>& t, const R* me, R* le, cudaStream_t s);
+template <typename R>
+cudaError_t launch_l2l(const Geometry& g, int level, const Tables<R>& t, R* le, cudaStream_t s);
+template <typename R>
+cudaError_t launch_p2p_l2p(const Geometry& g, double sigma, const void* particles,
+                           const uint32_t* leaf_start, const R* le, R* uv, cudaStream_t s);
+
+template <typename R>
+cudaError_t launch_direct_sampled(const Geometry& g, double sigma, int kernel, int64_t n,
+                                  const R* xy, const R* gamma, int64_t s_count,
+                                  const int64_t* targets, double* uv_ref, int* status,
+                                  cudaStream_t s);
+template <typename R>
+cudaError_t launch_error_stats(const Geometry& g, int64_t n, const R* xy, const R* uv,
+                               int64_t s_count, const int64_t* targets, const double* uv_ref,
+                               double* stats, double* leaf_err, int* status, cudaStream_t s);
+
+}  // namespace fmm2d
+
+namespace fmm2d {
+
+// Complex arithmetic on (re, im) pairs of the evaluation's precision.
+template <typename R>
+struct Cplx;
+template <>
+struct Cplx<float> {
+    using T = float2;
+};
+template <>
+struct Cplx<double> {
+    using T = double2;
+};
+template <typename T>
+__host__ __device__ inline T cmake(decltype(T().x) re, decltype(T().x) im) {
+    T r;
+    r.x = re;
+    r.y = im;
+    return r;
+}
+template <typename T>
+__device__ inline T cmul(T a, T b) {
+    return cmake<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc + a * b
+template <typename T>
+__device__ inline T cfma(T a, T b, T acc) {
+    acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+    acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+    return acc;
+}
+template <typename T>
+__device__ inline T cshfl(T v, int src, int width, unsigned mask = 0xffffffffu) {
+    v.x = __shfl_sync(mask, v.x, src, width);
+    v.y = __shfl_sync(mask, v.y, src, width);
+    return v;
+}
+// Lanes of the G-lane segment (G = 16 or 32) that holds the calling lane.
+__device__ inline unsigned segment_mask(int G) {
+    int lane = threadIdx.x & 31;
+    return G == 32 ? 0xffffffffu : (0xffffu << (lane & 16));
+}
+
+// Decode the box of level l held by expansion slot `slot` (inverse of box_slot).
+__device__ inline int slot_level(const int64_t* level_base, int L, int64_t slot) {
+    int l = 2;
+    while (l < L && slot >= level_base[l + 1]) ++l;
+    return l;
+}
+__device__ inline void slot_box(const int64_t* level_base, int l, int64_t slot, uint32_t* ix,
+                                uint32_t* iy) {
+    int64_t r = slot - level_base[l];
+    uint32_t h = 1u << (l - 1);
+    uint32_t plane = (uint32_t)(r / ((int64_t)h * h));
+    uint32_t rem = (uint32_t)(r % ((int64_t)h * h));
+    *ix = ((rem % h) << 1) | (plane & 1u);
+    *iy = ((rem / h) << 1) | (plane >> 1);
+}
+
+}  // namespace fmm2d

@@ -1,0 +1,244 @@
+// Quadtree build (Sec. 3.3, Fig. 6): Morton keys of the leaves at level L,
+// a stable LSD radix sort of (key, input index), the gather of the sorted
+// particle records, and the leaf ranges.
+//
+// Leaf coordinate along an axis: floor((x - x0) * (2^L / W)) in FP64,
+// clamped into [0, 2^L - 1]; the upper edge of the root box belongs to the
+// last leaf.  Key = leaf x index in the even bits, y index in the odd bits.
+// The sort is stable, so particles of one leaf keep their input order and
+// the permutation is unique.
+//
+// Radix pass (8-bit digit): per-tile digit counts -> exclusive scan over
+// (digit, tile) -> scatter.  Within a tile each warp owns a contiguous run of
+// keys and ranks equal digits with __match_any_sync, which preserves input
+// order; warps are then offset per digit in warp order.
+#include "fmm2d_internal.cuh"
+
+namespace fmm2d {
+namespace {
+
+struct KeyParams {
+    double x0, y0, x1, y1;  // closed root box
+    double scale;           // 2^L / W
+    double top;             // 2^L - 1
+};
+
+__device__ inline uint32_t leaf_coord(double x, double lo, double hi, double scale, double top,
+                                      int* flags) {
+    if (!(x >= lo && x <= hi)) *flags |= (x != x) ? kFlagNonfinite : kFlagOutOfDomain;
+    double f = floor((x - lo) * scale);
+    if (!(f >= 0.0)) f = 0.0;  // also maps NaN to 0 so that no index runs wild
+    if (f > top) f = top;
+    return (uint32_t)f;
+}
+
+// Keys of one tile plus the histogram of the first digit.
+template <typename R>
+__global__ void __launch_bounds__(kSortThreads)
+keys_hist_kernel(int64_t n, const R* __restrict__ xy, const R* __restrict__ gamma, KeyParams kp,
+                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                 uint32_t* __restrict__ hist, int nblocks, int* status) {
+    __shared__ uint32_t cnt[kRadix];
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) cnt[d] = 0;
+    __syncthreads();
+    int flags = 0;
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll 4
+    for (int it = 0; it < kSortItems; ++it) {
+        int64_t i = base + it * kSortThreads + threadIdx.x;
+        if (i < n) {
+            double x = (double)xy[2 * i], y = (double)xy[2 * i + 1];
+            double g = (double)gamma[i];
+            if (!isfinite(g)) flags |= kFlagNonfinite;
+            uint32_t ix = leaf_coord(x, kp.x0, kp.x1, kp.scale, kp.top, &flags);
+            uint32_t iy = leaf_coord(y, kp.y0, kp.y1, kp.scale, kp.top, &flags);
+            uint32_t k = morton_key(ix, iy);
+            keys[i] = k;
+            vals[i] = (uint32_t)i;
+            atomicAdd(&cnt[k & (kRadix - 1)], 1u);
+        }
+    }
+    if (flags) atomicOr(status, flags);
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+        hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+hist_kernel(int64_t n, const uint32_t* __restrict__ keys, int shift, uint32_t* __restrict__ hist,
+            int nblocks) {
+    __shared__ uint32_t cnt[kRadix];
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) cnt[d] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll 4
+    for (int it = 0; it < kSortItems; ++it) {
+        int64_t i = base + it * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & (kRadix - 1)], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+        hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
+}
+
+// Exclusive scan of `total` counts in place, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) scan_kernel(uint32_t* data, int64_t total) {
+    __shared__ uint32_t warp_sums[32];
+    int64_t per = (total + blockDim.x - 1) / blockDim.x;
+    int64_t lo = threadIdx.x * per;
+    int64_t hi = lo + per < total ? lo + per : total;
+    uint32_t sum = 0;
+    for (int64_t i = lo; i < hi; ++i) sum += data[i];
+    // block-wide exclusive scan of the per-thread sums
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = warp_sums[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t v = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += v;
+        }
+        warp_sums[lane] = w;  // inclusive
+    }
+    __syncthreads();
+    uint32_t run = (warp > 0 ? warp_sums[warp - 1] : 0) + incl - sum;
+    for (int64_t i = lo; i < hi; ++i) {
+        uint32_t v = data[i];
+        data[i] = run;
+        run += v;
+    }
+}
+
+// Stable scatter of one tile.  With R != void the pass is the last one and
+// also writes the sorted particle records and the permutation.
+template <typename R, bool kLast>
+__global__ void __launch_bounds__(kSortThreads)
+scatter_kernel(int64_t n, const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+               int shift, const uint32_t* __restrict__ offsets, int nblocks,
+               uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+               const R* __restrict__ xy, const R* __restrict__ gamma,
+               typename ParticleOf<R>::type* __restrict__ particles) {
+    constexpr int kWarps = kSortThreads / 32;
+    constexpr int kPerWarp = kSortTile / kWarps;  // contiguous keys per warp
+    constexpr int kIters = kPerWarp / 32;
+    __shared__ uint32_t wcnt[kWarps][kRadix];
+    __shared__ uint32_t dbase[kRadix];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = lane; d < kRadix; d += 32) wcnt[warp][d] = 0;
+    __syncwarp();
+    int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * kPerWarp;
+    uint32_t key[kIters], val[kIters], rank[kIters];
+    uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int it = 0; it < kIters; ++it) {
+        int64_t i = base + it * 32 + lane;
+        bool ok = i < n;
+        key[it] = ok ? keys_in[i] : 0u;
+        val[it] = ok ? vals_in[i] : 0u;
+        uint32_t d = ok ? ((key[it] >> shift) & (kRadix - 1)) : (uint32_t)kRadix;  // sentinel
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = ok ? wcnt[warp][d] : 0u;
+        __syncwarp();
+        if (ok && (peers & lt_mask) == 0) wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+        rank[it] = before + __popc(peers & lt_mask);
+    }
+    __syncthreads();
+    // exclusive offsets of the warps within each digit, and the tile's base
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            uint32_t c = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += c;
+        }
+        dbase[d] = offsets[(int64_t)d * nblocks + blockIdx.x];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kIters; ++it) {
+        int64_t i = base + it * 32 + lane;
+        if (i < n) {
+            uint32_t d = (key[it] >> shift) & (kRadix - 1);
+            uint32_t pos = dbase[d] + wcnt[warp][d] + rank[it];
+            keys_out[pos] = key[it];
+            vals_out[pos] = val[it];
+            if (kLast) {
+                uint32_t j = val[it];
+                particles[pos] = ParticleOf<R>::make(xy[2 * (int64_t)j], xy[2 * (int64_t)j + 1],
+                                                     gamma[j], j);
+            }
+        }
+    }
+}
+
+// leaf_start[k] = first sorted position whose key is >= k, k = 0 .. 4^L.
+__global__ void leaf_bounds_kernel(int64_t n, const uint32_t* __restrict__ skeys, uint32_t nleaf,
+                                   uint32_t* __restrict__ leaf_start) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t prev = r == 0 ? -1 : (int64_t)skeys[r - 1];
+        int64_t cur = r == n ? (int64_t)nleaf : (int64_t)skeys[r];
+        for (int64_t k = prev + 1; k <= cur; ++k) leaf_start[k] = (uint32_t)r;
+    }
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_tree_build(const Geometry& g, int64_t n, const R* xy, const R* gamma,
+                              SortBuffers& sb, void* particles, cudaStream_t s) {
+    using P = typename ParticleOf<R>::type;
+    uint32_t nleaf = 1u << (2 * g.L);
+    if (n == 0) {
+        leaf_bounds_kernel<<<1, 32, 0, s>>>(0, sb.keys[0], nleaf, sb.leaf_start);
+        return cudaGetLastError();
+    }
+    KeyParams kp;
+    kp.x0 = g.x0;
+    kp.y0 = g.y0;
+    kp.x1 = g.x0 + g.W;
+    kp.y1 = g.y0 + g.W;
+    kp.scale = ldexp(1.0, g.L) / g.W;
+    kp.top = ldexp(1.0, g.L) - 1.0;
+    int nblocks = (int)((n + kSortTile - 1) / kSortTile);
+    int bits = 2 * g.L;
+    int passes = bits <= kRadixBits ? 1 : (bits + kRadixBits - 1) / kRadixBits;
+    int64_t hist_len = (int64_t)kRadix * nblocks;
+    keys_hist_kernel<R><<<nblocks, kSortThreads, 0, s>>>(n, xy, gamma, kp, sb.keys[0], sb.vals[0],
+                                                         sb.hist, nblocks, sb.status);
+    for (int q = 0; q < passes; ++q) {
+        int src = q & 1, dst = src ^ 1;
+        int shift = q * kRadixBits;
+        if (q > 0)
+            hist_kernel<<<nblocks, kSortThreads, 0, s>>>(n, sb.keys[src], shift, sb.hist, nblocks);
+        scan_kernel<<<1, 1024, 0, s>>>(sb.hist, hist_len);
+        if (q == passes - 1)
+            scatter_kernel<R, true><<<nblocks, kSortThreads, 0, s>>>(
+                n, sb.keys[src], sb.vals[src], shift, sb.hist, nblocks, sb.keys[dst], sb.perm, xy,
+                gamma, reinterpret_cast<P*>(particles));
+        else
+            scatter_kernel<R, false><<<nblocks, kSortThreads, 0, s>>>(
+                n, sb.keys[src], sb.vals[src], shift, sb.hist, nblocks, sb.keys[dst], sb.vals[dst],
+                xy, gamma, reinterpret_cast<P*>(particles));
+    }
+    const uint32_t* sorted = sb.keys[passes & 1];
+    int lb_blocks = (int)((n + 1 + 255) / 256);
+    if (lb_blocks > 2048) lb_blocks = 2048;
+    leaf_bounds_kernel<<<lb_blocks, 256, 0, s>>>(n, sorted, nleaf, sb.leaf_start);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_tree_build<float>(const Geometry&, int64_t, const float*, const float*,
+                                              SortBuffers&, void*, cudaStream_t);
+template cudaError_t launch_tree_build<double>(const Geometry&, int64_t, const double*,
+                                               const double*, SortBuffers&, void*, cudaStream_t);
+
+}  // namespace fmm2d

@@ -1,0 +1,78 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, exports every function include/fmm2d.h declares, and rejects
+invalid parameters before touching the device.  Also checks that the oracle
+and the CUDA path stay independent."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_0809_1810_gb300 import _native, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _native.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _native.declared_functions()
+    assert len(names) >= 12
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("field,value", [("p", 0), ("p", 33), ("L", -1), ("L", 13),
+                                         ("sigma", 0.0), ("sigma", float("nan")), ("W", 0.0),
+                                         ("W", -2.0), ("precision", 9), ("max_n", -5)])
+def test_invalid_parameters_are_rejected(lib, field, value):
+    prm = _native.Params(16, 7, 0.01, _native.FP32, -1.0, -1.0, 2.0, 1000)
+    setattr(prm, field, value)
+    h = ctypes.c_void_p(1234)
+    st = lib.fmm2d_plan_create(ctypes.byref(h), ctypes.byref(prm))
+    assert st == _native.INVALID_ARG
+    assert h.value is None
+    assert lib.fmm2d_last_error()
+
+
+def test_null_arguments_are_rejected(lib):
+    assert lib.fmm2d_plan_create(None, None) == _native.INVALID_ARG
+    assert lib.fmm2d_velocity(None, 0, None, None, None, None) == _native.INVALID_ARG
+    assert lib.fmm2d_plan_check(None, None) == _native.INVALID_ARG
+    assert lib.fmm2d_plan_set_timing(None, 4) == _native.INVALID_ARG
+    lib.fmm2d_plan_destroy(None)  # accepted
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert lib.fmm2d_status_string(s)
+    assert lib.fmm2d_status_string(99) == b"unknown status"
+
+
+def _imports(path):
+    with open(path) as f:
+        text = f.read()
+    return set(re.findall(r"^\s*(?:from|import)\s+([A-Za-z_][\w.]*)", text, flags=re.M))
+
+
+def test_oracle_and_cuda_path_share_nothing():
+    pkg = os.path.join(ROOT, "paper_0809_1810_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            p = os.path.join(dirpath, f)
+            if f.endswith(".py"):
+                assert not any(m.split(".")[0] == "oracle" for m in _imports(p)), p
+            if f.endswith((".cu", ".cuh", ".py", ".h")):
+                with open(p) as fh:
+                    assert "fmm2d_oracle" not in fh.read(), p
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        p = os.path.join(ROOT, "oracle", f)
+        if f.endswith(".py"):
+            assert not any(m.split(".")[0] == "paper_0809_1810_gb300" for m in _imports(p)), p
+        if f.endswith(".c"):
+            with open(p) as fh:
+                assert "fmm2d.h" not in fh.read()

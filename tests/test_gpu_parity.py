@@ -1,0 +1,269 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Bars:
+* quadtree: Morton keys, permutation and leaf ranges bit-exact;
+* FP64 FMM: max |du| <= 1e-12 max |u| against the oracle FMM at the same p, L;
+* FP32 FMM: max |du| <= FP32_TOL max |u| against the oracle FMM at the same
+  p, L.  FP32_TOL = 1e-6 is the bound stated for the FP32 form at p >= 16;
+  the arithmetic behind it: near sums of <= ~2400 terms accumulated two-level
+  in FP32 (measured ~1e-7), p-term box-scaled expansions with O(1)
+  coefficients (rounding ~p * 6e-8 relative to the far field);
+* FP64 yardsticks (sampled direct sums): <= 1e-12 against the oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0809_1810_gb300 import build
+
+    build.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+
+
+def _dev(w, dtype):
+    xy = torch.tensor(np.stack([w.x, w.y], 1), dtype=dtype, device="cuda")
+    g = torch.tensor(w.gamma, dtype=dtype, device="cuda")
+    return xy, g
+
+
+def _plan(w, prec, max_n=None):
+    from paper_0809_1810_gb300 import Plan
+
+    return Plan(w.p, w.L, w.sigma, prec, root=w.root, max_n=max_n or max(w.n, 1))
+
+
+def _rel(a, b):
+    scale = np.abs(b).max()
+    return np.abs(a - b).max() / scale if scale > 0 else np.abs(a - b).max()
+
+
+def _edge_lattice(L, m=7):
+    """Points exactly on leaf edges and on the root's upper edge."""
+    k = np.arange(0, (1 << L) + 1, max(1, (1 << L) // m))
+    e = -1.0 + 2.0 * k / (1 << L)
+    gx, gy = np.meshgrid(e, e)
+    return gx.ravel(), gy.ravel()
+
+
+# ---------------------------------------------------------------------------
+# quadtree
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,L", [(0, 3), (1, 0), (1, 5), (4097, 1), (4097, 4), (20011, 8),
+                                 (30000, 12), (70000, 7)])
+def test_tree_is_bit_exact(prec, n, L):
+    dtype = np.float64 if prec == "fp64" else np.float32
+    w = W.uniform_random(n, 100 + n + L, 0.01, sigma_over_h=1.0, p=4, L=L, dtype=dtype)
+    if n > 100:  # put some particles exactly on leaf edges and the root's upper edge
+        ex, ey = _edge_lattice(L)
+        m = min(len(ex), n // 4)
+        w.x[:m] = ex[:m].astype(dtype)
+        w.y[:m] = ey[:m].astype(dtype)
+        w.x[m:2 * m] = w.x[:m]  # duplicates: stability decides their order
+        w.y[m:2 * m] = w.y[:m]
+    xy, g = _dev(w, torch.float64 if prec == "fp64" else torch.float32)
+    with _plan(w, prec) as plan:
+        plan.velocity(xy, g, check=True)
+        keys, perm, start = plan.tree(n)
+        torch.cuda.synchronize()
+    okeys = oracle.morton_keys(w.x, w.y, w.root, L)
+    operm, ostart = oracle.sort_by_key(okeys, L)
+    np.testing.assert_array_equal(perm.cpu().numpy().astype(np.uint32), operm)
+    np.testing.assert_array_equal(keys.cpu().numpy().astype(np.uint32), okeys[operm])
+    np.testing.assert_array_equal(start.cpu().numpy().astype(np.uint32), ostart)
+
+
+# ---------------------------------------------------------------------------
+# FMM vs oracle FMM
+# ---------------------------------------------------------------------------
+
+def _cases():
+    yield "lamb_oseen_4096", lambda dt: W.lamb_oseen_4096() if dt == np.float64 else \
+        W.lamb_oseen_lattice(64, p=10, L=3, dtype=dt)
+    for n, p, L, soh in [(5000, 1, 2, 1.0), (5000, 5, 0, 1.0), (5000, 8, 1, 1.0),
+                         (6007, 16, 4, 2.0), (6007, 17, 3, 1.0), (8191, 24, 5, 1.0),
+                         (3001, 32, 2, 0.8), (12000, 12, 6, 1.5)]:
+        yield (f"uniform_n{n}_p{p}_L{L}",
+               lambda dt, n=n, p=p, L=L, soh=soh: W.uniform_random(
+                   n, n + p, 2.0 / np.sqrt(n), sigma_over_h=soh, p=p, L=L, dtype=dt))
+    yield "clustered_20000", lambda dt: W.clustered_patches(20000, 4, npatch=6, h=2.0 / 140,
+                                                             p=14, L=5, dtype=dt)
+
+
+CASES = list(_cases())
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_fp64_fmm_matches_oracle(name, make):
+    w = make(np.float64)
+    ref = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.p, w.L, w.root)
+    xy, g = _dev(w, torch.float64)
+    with _plan(w, "fp64") as plan:
+        uv = plan.velocity(xy, g, check=True).cpu().numpy()
+    assert _rel(uv, ref) <= FP64_TOL, _rel(uv, ref)
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_fp32_fmm_matches_oracle(name, make):
+    w = make(np.float32)
+    ref = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.p, w.L, w.root)
+    xy, g = _dev(w, torch.float32)
+    with _plan(w, "fp32") as plan:
+        uv = plan.velocity(xy, g, check=True).double().cpu().numpy()
+    assert _rel(uv, ref) <= FP32_TOL, _rel(uv, ref)
+
+
+def test_uniform_1m_full_size():
+    """The 2^20-particle uniform workload (p = 16, L = 7, sigma = 2h) in the
+    FP32 form timed by the benchmark: every output against the FP64 oracle
+    FMM, and the FP64 direct yardsticks against the oracle at sampled targets."""
+    w = W.uniform_1m()
+    xy, g = _dev(w, torch.float32)
+    with _plan(w, "fp32") as plan:
+        uv = plan.velocity(xy, g, check=True).double().cpu().numpy()
+        t = W.sample_targets(w.n, 256, 11)
+        tt = torch.tensor(t, device="cuda")
+        d0 = plan.direct_sampled(xy, g, tt, kernel=0).cpu().numpy()
+        d1 = plan.direct_sampled(xy, g, tt, kernel=1).cpu().numpy()
+        plan.check()
+    ref = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.p, w.L, w.root)
+    assert _rel(uv, ref) <= FP32_TOL, _rel(uv, ref)
+    o1 = oracle.direct(w.x, w.y, w.gamma, w.sigma, targets=t)
+    o2 = oracle.hybrid(w.x, w.y, w.gamma, w.sigma, w.root, w.L, targets=t)
+    assert _rel(d0, o1) <= FP64_TOL
+    assert _rel(d1, o2) <= FP64_TOL
+
+
+# ---------------------------------------------------------------------------
+# yardsticks
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_direct_sampled_matches_oracle(prec, kernel):
+    dtype = np.float64 if prec == "fp64" else np.float32
+    w = W.uniform_random(9000, 31, 2.0 / 95, sigma_over_h=2.0, p=8, L=5, dtype=dtype)
+    t = W.sample_targets(w.n, 333, 2)
+    xy, g = _dev(w, torch.float64 if prec == "fp64" else torch.float32)
+    with _plan(w, prec) as plan:
+        got = plan.direct_sampled(xy, g, torch.tensor(t, device="cuda"), kernel=kernel)
+        plan.check()
+    got = got.cpu().numpy()
+    if kernel == 0:
+        ref = oracle.direct(w.x, w.y, w.gamma, w.sigma, targets=t)
+    else:
+        ref = oracle.hybrid(w.x, w.y, w.gamma, w.sigma, w.root, w.L, targets=t)
+    assert _rel(got, ref) <= 1e-13
+
+
+def test_error_stats_match_numpy():
+    w = W.uniform_random(7000, 8, 2.0 / 84, sigma_over_h=1.0, p=6, L=4, dtype=np.float32)
+    xy, g = _dev(w, torch.float32)
+    t = W.sample_targets(w.n, 500, 5)
+    tt = torch.tensor(t, device="cuda")
+    with _plan(w, "fp32") as plan:
+        uv = plan.velocity(xy, g)
+        ref = plan.direct_sampled(xy, g, tt)
+        stats, leaf = plan.error_stats(xy, uv, tt, ref, per_leaf=True)
+        plan.check()
+    uvn = uv.double().cpu().numpy()[t]
+    refn = ref.cpu().numpy()
+    du = np.linalg.norm(uvn - refn, axis=1)
+    rr = np.linalg.norm(refn, axis=1)
+    s = stats.cpu().numpy()
+    np.testing.assert_allclose(s, [du.max(), rr.max(), (du ** 2).sum(), (rr ** 2).sum()],
+                               rtol=1e-12)
+    keys = oracle.morton_keys(w.x[t], w.y[t], w.root, w.L)
+    want = np.zeros(1 << (2 * w.L))
+    np.maximum.at(want, keys, du)
+    np.testing.assert_allclose(leaf.cpu().numpy(), want, rtol=1e-15, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# error paths, host entry point, graph reuse, timing
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bad,status", [("outside", 2), ("nan_pos", 3), ("inf_gamma", 3)])
+def test_input_errors_are_reported(bad, status):
+    from paper_0809_1810_gb300 import FMMError
+
+    w = W.uniform_random(3000, 1, 0.03, p=6, L=4, dtype=np.float32)
+    if bad == "outside":
+        w.x[17] = 1.5
+    elif bad == "nan_pos":
+        w.y[5] = np.nan
+    else:
+        w.gamma[9] = np.inf
+    xy, g = _dev(w, torch.float32)
+    with _plan(w, "fp32") as plan:
+        plan.velocity(xy, g)
+        with pytest.raises(FMMError) as ei:
+            plan.check()
+        assert ei.value.status == status
+        # the plan stays usable and the flag is cleared
+        good = W.uniform_random(3000, 1, 0.03, p=6, L=4, dtype=np.float32)
+        xy2, g2 = _dev(good, torch.float32)
+        plan.velocity(xy2, g2, check=True)
+
+
+def test_host_entry_point_matches_device_call():
+    w = W.uniform_random(50000, 3, 2.0 / 224, sigma_over_h=2.0, p=12, L=5, dtype=np.float32)
+    xy, g = _dev(w, torch.float32)
+    with _plan(w, "fp32") as plan:
+        uv = plan.velocity(xy, g, check=True).cpu()
+        hx = xy.cpu().pin_memory()
+        hg = g.cpu().pin_memory()
+        out = torch.empty((w.n, 2), dtype=torch.float32).pin_memory()
+        plan.velocity_host(hx, hg, out)
+        out2 = torch.empty((w.n, 2), dtype=torch.float32)  # pageable works too
+        plan.velocity_host(xy.cpu(), g.cpu(), out2)
+    assert torch.equal(out, uv)
+    assert torch.equal(out2, uv)
+
+
+def test_graph_replay_and_rebinding():
+    w = W.uniform_random(40000, 9, 2.0 / 200, sigma_over_h=1.0, p=10, L=5, dtype=np.float32)
+    xy, g = _dev(w, torch.float32)
+    with _plan(w, "fp32", max_n=w.n) as plan:
+        a = plan.velocity(xy, g).clone()
+        b = plan.velocity(xy, g).clone()  # replay
+        xy2, g2 = xy.clone(), g.clone()
+        c = plan.velocity(xy2, g2).clone()  # new buffers: re-recorded
+        half = plan.velocity(xy[: w.n // 2], g[: w.n // 2])  # new n
+        plan.check()
+    assert torch.equal(a, b) and torch.equal(a, c)
+    ref = oracle.fmm(w.x[: w.n // 2], w.y[: w.n // 2], w.gamma[: w.n // 2], w.sigma, w.p, w.L,
+                     w.root)
+    assert _rel(half.double().cpu().numpy(), ref) <= FP32_TOL
+
+
+def test_phase_timing_ring():
+    w = W.uniform_random(100000, 4, 2.0 / 316, sigma_over_h=2.0, p=16, L=6, dtype=np.float32)
+    xy, g = _dev(w, torch.float32)
+    with _plan(w, "fp32") as plan:
+        plan.set_timing(4)
+        for _ in range(6):
+            plan.velocity(xy, g)
+        times = [plan.phase_ms(age) for age in range(4)]
+        with pytest.raises(Exception):
+            plan.phase_ms(4)
+        plan.set_timing(0)
+        plan.velocity(xy, g, check=True)
+    for t in times:
+        assert all(v >= 0 for v in t.values())
+        assert t["p2p_l2p"] > 0 and t["tree"] > 0
