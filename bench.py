@@ -1,0 +1,387 @@
+"""Benchmark: FMM velocity evaluation of N = 2^20 vortex particles.
+
+Workload (one "step" = one full FMM evaluation, tree build to velocities):
+uniform positions in [-1, 1]^2, circulations h^2 N(0,1) with h = 2/1024,
+sigma = 2h, p = 16, L = 7, float32 inputs and arithmetic (the FP32 form).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is whole-job particles/s from CUDA
+events around each step (L2 flushed between steps, outside the events);
+`e2e` times the host-buffer entry point with the copies inside; `accuracy`
+is measured once, outside the timed region, against FP64 direct sums at
+8192 seeded targets; `roofline` covers the dominant kernel (fused L2P + P2P)
+from event-record nodes inside the CUDA graph of the same timed steps.
+With --gpus N > 1 (torchrun) every rank evaluates its own independent
+instance ("replicas only": a single evaluation has no exchange-free split).
+`--impl reference` times the CPU FP64 oracle, the only reference this
+project has.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "FMM particles/sec at ≤1e-6 max rel err vs FP64 direct; % roofline; vs plain FP64"
+WORKLOAD = ("uniform_1m: N=2^20 uniform in [-1,1]^2, Gamma=h^2 N(0,1), h=2/1024, sigma=2h, "
+            "p=16, L=7 (16384 leaves)")
+ACC_TARGETS = 8192
+FLUSH_BYTES = 512 << 20  # > 129 MB L2
+P2P_FLOPS_PER_PAIR = 20  # algorithmic work per near pair
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# P2P unit rates per SM per clock (Blackwell SM: 128 FP32 lanes, 16 MUFU lanes).
+FP32_LANES_PER_SM = 128
+MUFU_LANES_PER_SM = 16
+N_SMS = 152
+
+
+def p2p_peak_pairs_per_s(sm_mhz: float) -> float:
+    """ALU roofline of the near-field pair: min(FP32 rate / 20 flops,
+    MUFU rate / 2 ops) per SM per clock, times SMs and clock."""
+    fp32 = FP32_LANES_PER_SM * 2 / P2P_FLOPS_PER_PAIR
+    mufu = MUFU_LANES_PER_SM / 2
+    return min(fp32, mufu) * N_SMS * sm_mhz * 1e6
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                maxs.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(mhz)), "sm_max_mhz": max(maxs),
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, torch=None):
+    if torch is not None:
+        torch.cuda.synchronize()
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, value, torch=None, device=None):
+    if pg is None:
+        return value
+    if torch is not None:
+        t = torch.tensor([value], dtype=torch.float64, device=device)
+    else:
+        import torch as _t
+
+        t = _t.tensor([value], dtype=_t.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(w, budget_s=12.0):
+    """The oracle FMM on the same workload, repeated while within budget."""
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    runs = 0
+    while True:
+        oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.p, w.L, w.root)
+        runs += 1
+        if time.perf_counter() - t0 > budget_s or runs >= 5:
+            break
+    dt = time.perf_counter() - t0
+    return w.n * runs / dt, runs, oracle.num_threads()
+
+
+def run_reference(args):
+    """CPU FP64 oracle arm: each step one oracle FMM evaluation of the full
+    workload, on the host cores."""
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    w = W.uniform_1m()
+    for _ in range(args.warmup):
+        oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.p, w.L, w.root)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.p, w.L, w.root)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = w.n / dt
+    cores = oracle.num_threads()
+    sample = f"full workload (N=2^20) per step, plain FP64 FMM, {cores} OpenMP threads"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_0809_1810_gb300 import Plan
+
+    w = W.uniform_1m(seed=2 + rank)  # an independent instance per rank
+    n = w.n
+    xy = torch.tensor(np.stack([w.x, w.y], 1), dtype=torch.float32, device=dev)
+    g = torch.tensor(w.gamma, dtype=torch.float32, device=dev)
+    uv = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    plan = Plan(w.p, w.L, w.sigma, args.precision, root=w.root, max_n=n)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    ring = max(args.steps, 1)
+    plan.set_timing(ring)
+    for _ in range(args.warmup):
+        plan.velocity(xy, g, out=uv)
+    plan.check()
+    launches_per_step = plan.kernels_per_call()
+
+    # accuracy, once, outside the timed region
+    t = torch.tensor(W.sample_targets(n, ACC_TARGETS, 1234), device=dev)
+    ref_direct = plan.direct_sampled(xy, g, t, kernel=0)
+    ref_hybrid = plan.direct_sampled(xy, g, t, kernel=1)
+    s_dir = plan.error_stats(xy, uv, t, ref_direct).cpu().numpy()
+    s_hyb = plan.error_stats(xy, uv, t, ref_hybrid).cpu().numpy()
+    plan.check()
+    accuracy = {
+        "targets": ACC_TARGETS,
+        "max_rel_err_vs_fp64_direct": float(s_dir[0] / s_dir[1]),
+        "max_rel_err_vs_fp64_fmm_limit": float(s_hyb[0] / s_hyb[1]),
+        "note": "FP64 direct = regularised sum (Eq. 7); FMM limit = Eq. 6 near / singular "
+                "far (Eq. 10); leaf = 4 sigma here, so the kernel-substitution floor "
+                "(Sec. 4.1) dominates the first",
+    }
+
+    # timed region
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(pg, torch)
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record()
+            plan.velocity(xy, g, out=uv)
+            ends[k].record()
+        torch.cuda.synchronize()
+    barrier(pg, torch)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = max_over_ranks(pg, float(sum(step_ms)), torch, dev)
+    ms_per_step = total_ms / args.steps
+    value = world * n / (ms_per_step * 1e-3)
+
+    phases = [plan.phase_ms(a) for a in range(min(args.steps, ring))]
+    phase_avg = {k: float(np.mean([p[k] for p in phases])) for k in phases[0]}
+
+    # near-pair count of this instance: sum over leaves of n_leaf * n_3x3
+    _, _, start = plan.tree(n)
+    counts = np.diff(start.cpu().numpy().astype(np.int64))
+    nl = 1 << w.L
+    grid = np.zeros((nl, nl), dtype=np.int64)
+    ks = np.arange(nl * nl, dtype=np.uint32)
+    ixs = np.zeros(nl * nl, dtype=np.int64)
+    iys = np.zeros(nl * nl, dtype=np.int64)
+    for b in range(w.L):
+        ixs |= ((ks >> (2 * b)) & 1).astype(np.int64) << b
+        iys |= ((ks >> (2 * b + 1)) & 1).astype(np.int64) << b
+    grid[iys, ixs] = counts
+    padg = np.pad(grid, 1)
+    nb = sum(padg[1 + dy:1 + dy + nl, 1 + dx:1 + dx + nl] for dy in (-1, 0, 1) for dx in (-1, 0, 1))
+    pairs = int((grid * nb).sum()) - n  # self pairs excluded
+
+    peaks, peak_kind = _peaks()
+    clk = clocks.summary()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = p2p_peak_pairs_per_s(sm_max)
+    p2p_ms = phase_avg["p2p_l2p"]
+    achieved = pairs / (p2p_ms * 1e-3)
+    roofline = {
+        "kernel": "p2p_l2p_kernel<float> (fused L2P + near field)",
+        "bound": "alu", "unit": "Gpair/s",
+        "achieved": achieved / 1e9, "peak": peak / 1e9, "frac": achieved / peak,
+        "peak_source": f"derived: min(128 FP32 lanes x 2 / {P2P_FLOPS_PER_PAIR} flops, "
+                       f"16 MUFU lanes / 2 ops) per SM per clock x 152 SMs x "
+                       f"{sm_max:.0f} MHz ({peak_kind} sm_max_mhz)",
+        "pairs_per_launch": pairs, "avg_launch_ms": p2p_ms,
+        "traffic": None,
+        "phase_ms": phase_avg,
+    }
+
+    # end to end through the host-buffer entry point
+    hxy = xy.cpu().pin_memory()
+    hg = g.cpu().pin_memory()
+    huv = torch.empty((n, 2), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        plan.velocity_host(hxy, hg, huv)
+    e_steps = max(3, min(args.steps, 20))
+    es = [torch.cuda.Event(enable_timing=True) for _ in range(e_steps)]
+    ee = [torch.cuda.Event(enable_timing=True) for _ in range(e_steps)]
+    barrier(pg, torch)
+    for k in range(e_steps):
+        es[k].record()
+        plan.velocity_host(hxy, hg, huv)
+        ee[k].record()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(pg, float(np.mean([a.elapsed_time(b) for a, b in zip(es, ee)])),
+                            torch, dev)
+    e2e = {"value": world * n / (e2e_ms * 1e-3), "unit": "particles/s",
+           "h2d_bytes_per_step": int(hxy.numel() * 4 + hg.numel() * 4),
+           "d2h_bytes_per_step": int(huv.numel() * 4), "ms_per_step": e2e_ms}
+
+    # plain FP64 GPU FMM on the same instance, for the "vs plain FP64" part
+    plan64 = Plan(w.p, w.L, w.sigma, "fp64", root=w.root, max_n=n)
+    xy64, g64 = xy.double(), g.double()
+    uv64 = torch.empty((n, 2), dtype=torch.float64, device=dev)
+    for _ in range(2):
+        plan64.velocity(xy64, g64, out=uv64)
+    plan64.check()
+    f_steps = 5
+    fs = [torch.cuda.Event(enable_timing=True) for _ in range(f_steps)]
+    fe = [torch.cuda.Event(enable_timing=True) for _ in range(f_steps)]
+    for k in range(f_steps):
+        flush.zero_()
+        fs[k].record()
+        plan64.velocity(xy64, g64, out=uv64)
+        fe[k].record()
+    torch.cuda.synchronize()
+    fp64_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(fs, fe)]))
+    s64 = plan64.error_stats(xy64, uv64, t, ref_direct).cpu().numpy()
+    plain_fp64 = {"value": n / (fp64_ms * 1e-3), "unit": "particles/s", "ms_per_step": fp64_ms,
+                  "max_rel_err_vs_fp64_direct": float(s64[0] / s64[1]),
+                  "speedup_of_value": (n / (ms_per_step * 1e-3)) / (n / (fp64_ms * 1e-3))}
+    plan64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, runs, cores = cpu_oracle_rate(w)
+        cpu = {"value": rate, "unit": "particles/s", "cores": cores, "kind": "oracle",
+               "sample": f"{runs} full evaluations of the same N=2^20 instance by the plain "
+                         f"FP64 oracle FMM (same p, L)"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.precision,
+                       "l2": "flushed between timed steps (512 MiB write outside the events)",
+                       "parallelism": f"replicas x{world}"},
+            "accuracy": accuracy, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "plain_fp64": plain_fp64, "gpu_launches": int(launches_per_step * args.steps),
+            "launches_per_step": launches_per_step, "clocks": clk,
+        }))
+    plan.close()
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_tc", "fp64"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -174,6 +174,10 @@ fmm2d_status fmm2d_plan_set_timing(fmm2d_plan* plan, int ring);
  * the ring. */
 fmm2d_status fmm2d_plan_phase_ms(fmm2d_plan* plan, int age, double* ms_host);
 
+/* Number of kernel launches one fmm2d_velocity call makes (the kernel nodes
+ * of its recorded CUDA graph); -1 before the first call. */
+int fmm2d_plan_kernels_per_call(const fmm2d_plan* plan);
+
 #ifdef __cplusplus
 }
 #endif

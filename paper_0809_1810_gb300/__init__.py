@@ -168,6 +168,10 @@ class Plan:
     def set_timing(self, ring: int):
         _check(self._lib.fmm2d_plan_set_timing(self._h, int(ring)), "set_timing")
 
+    def kernels_per_call(self) -> int:
+        """Kernel launches one velocity call makes (-1 before the first)."""
+        return int(self._lib.fmm2d_plan_kernels_per_call(self._h))
+
     def phase_ms(self, age: int = 0):
         buf = (ctypes.c_double * NUM_PHASES)()
         _check(self._lib.fmm2d_plan_phase_ms(self._h, int(age), buf), "phase_ms")

@@ -78,6 +78,7 @@ struct fmm2d_plan {
     cudaEvent_t ev_mark[kPhases + 1]{}; // placeholders captured into the graph
     cudaGraphNode_t ev_node[kPhases + 1]{};
     bool graph_timed = false;
+    int kernel_nodes = -1;
 };
 
 namespace {
@@ -156,6 +157,19 @@ fmm2d_status record_graph(fmm2d_plan* pl, int64_t n, const void* xy, const void*
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
     pl->graph = graph;
     CK(cudaGraphInstantiate(&pl->exec, graph, 0));
+    {
+        size_t count = 0;
+        CK(cudaGraphGetNodes(graph, nullptr, &count));
+        std::vector<cudaGraphNode_t> nodes(count);
+        CK(cudaGraphGetNodes(graph, nodes.data(), &count));
+        int kernels = 0;
+        for (size_t i = 0; i < count; ++i) {
+            cudaGraphNodeType ty;
+            CK(cudaGraphNodeGetType(nodes[i], &ty));
+            kernels += ty == cudaGraphNodeTypeKernel;
+        }
+        pl->kernel_nodes = kernels;
+    }
     pl->graph_timed = pl->ring > 0;
     if (pl->graph_timed) {
         // find the event-record nodes of the phase marks
@@ -487,5 +501,7 @@ fmm2d_status fmm2d_plan_phase_ms(fmm2d_plan* pl, int age, double* ms) {
     }
     return FMM2D_OK;
 }
+
+int fmm2d_plan_kernels_per_call(const fmm2d_plan* pl) { return pl ? pl->kernel_nodes : -1; }
 
 }  // extern "C"

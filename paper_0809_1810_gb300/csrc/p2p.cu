@@ -17,9 +17,10 @@
 // subtraction would cancel, so g is summed from its Taylor series
 //   g(q2) = sum_k (-1)^k ln2^(k+1) q2^k / (k+1)!   (truncated after q2^9,
 // relative truncation error below 5e-8 on [0, 1/ln 2)).
-// Each lane accumulates kInner pairs in a fresh register before adding them
-// to its running sum (two-level summation), which keeps the FP32 rounding of
-// the ~600-2400-term near sums near 1e-7 of max |u|.
+// Each lane accumulates kInner pairs in a fresh register, then adds that
+// partial sum to its running sum with Neumaier's compensated addition, so
+// the FP32 rounding of a near sum stays at the level of one kInner-term sum
+// however many sources the local list holds.
 #include "fmm2d_internal.cuh"
 
 namespace fmm2d {
@@ -67,6 +68,14 @@ __device__ __forceinline__ double radial(const NearF64& nm, double r2) {
     return r2 > 0.0 ? -expm1(-r2 * nm.inv2s2) / r2 : 0.0;
 }
 __device__ __forceinline__ float k0_of(const NearF32& nm) { return nm.k0; }
+
+// Neumaier's compensated summation step: s + c tracks the exact sum.
+template <typename R>
+__device__ __forceinline__ void neumaier_add(R& s, R& c, R x) {
+    R t = s + x;
+    c += (fabs(s) >= fabs(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+}
 __device__ __forceinline__ double k0_of(const NearF64& nm) { return nm.k0; }
 
 template <typename R, typename NM>
@@ -119,7 +128,7 @@ p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
         const bool active = tl < ntc;
         P self = active ? sp[t0 + tb + tl] : P{};
         const R xi = self.x, yi = self.y;
-        R au = R(0), av = R(0);
+        R au = R(0), av = R(0), cu = R(0), cv = R(0);
         for (uint32_t cb = 0; cb < total; cb += kChunk) {
             const uint32_t cnt = min(total - cb, (uint32_t)kChunk);
             const uint32_t step = kInner * ns;
@@ -147,10 +156,12 @@ p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
                     iu = fma(-dy, w, iu);
                     iv = fma(dx, w, iv);
                 }
-                au += iu;
-                av += iv;
+                neumaier_add(au, cu, iu);
+                neumaier_add(av, cv, iv);
             }
         }
+        au += cu;
+        av += cv;
         for (int o = 1; o < ns; o <<= 1) {
             au += __shfl_xor_sync(0xffffffffu, au, o);
             av += __shfl_xor_sync(0xffffffffu, av, o);
