@@ -174,6 +174,38 @@ fmm2d_status fmm2d_plan_set_timing(fmm2d_plan* plan, int ring);
  * the ring. */
 fmm2d_status fmm2d_plan_phase_ms(fmm2d_plan* plan, int age, double* ms_host);
 
+/* Quadtree build that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory -- for
+ * example a host framework whose memory manager owns the whole device budget
+ * and forbids allocations behind its back, or a latency-critical loop in
+ * which cudaMalloc / cudaFree, which can synchronise the whole device, are
+ * not acceptable.  It computes exactly what fmm2d_velocity's first step
+ * computes (Morton keys, stable radix sort, leaf ranges; the outputs match
+ * fmm2d_tree_debug bit for bit) without a plan:
+ *   precision          FMM2D_FP64 (double inputs) or FMM2D_FP32 / FMM2D_FP32_TC (float)
+ *   xy_dev, gamma_dev  n interleaved positions and n circulations (device)
+ *   L, x0, y0, W       leaf level (0..12) and the root box
+ *   keys_dev, perm_dev n sorted keys and n input indices (device, caller-owned)
+ *   leaf_start_dev     4^L + 1 leaf offsets (device, caller-owned)
+ *   flags_dev          optional device int: overwritten with the input-error
+ *                      flags (bit 1 << FMM2D_OUT_OF_DOMAIN, 1 << FMM2D_NONFINITE)
+ * Limit: n <= 262144 (2^18); larger n returns FMM2D_INVALID_ARG before any
+ * work is enqueued.  Its scratch (key/value ping-pong buffers, digit counts,
+ * a status word; about 4.06 MB) is one fixed device array inside the
+ * library, held by every GPU that loads the library until the process exits.
+ * The call makes no cudaMalloc, cudaFree or other allocating call.
+ * The first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents (the status word is cleared at the start of each call): calls
+ * whose work overlaps on the GPU -- on different streams, or from different
+ * host threads -- race on it and must be serialised by the caller. */
+fmm2d_status fmm2d_tree_build_noalloc(int precision, int64_t n, const void* xy_dev,
+                                      const void* gamma_dev, int L, double x0, double y0,
+                                      double W, uint32_t* keys_dev, uint32_t* perm_dev,
+                                      uint32_t* leaf_start_dev, int* flags_dev,
+                                      cudaStream_t stream);
+
 /* Number of kernel launches one fmm2d_velocity call makes (the kernel nodes
  * of its recorded CUDA graph); -1 before the first call. */
 int fmm2d_plan_kernels_per_call(const fmm2d_plan* plan);

@@ -63,6 +63,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "fmm2d_plan_set_timing": ([vp, i32], i32),
         "fmm2d_plan_phase_ms": ([vp, i32, vp], i32),
         "fmm2d_plan_kernels_per_call": ([vp], i32),
+        "fmm2d_tree_build_noalloc": ([i32, i64, vp, vp, i32, d, d, d, vp, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)

@@ -12,6 +12,8 @@
 // (digit, tile) -> scatter.  Within a tile each warp owns a contiguous run of
 // keys and ranks equal digits with __match_any_sync, which preserves input
 // order; warps are then offset per digit in warp order.
+#include <mutex>
+
 #include "fmm2d_internal.cuh"
 
 namespace fmm2d {
@@ -241,4 +243,123 @@ template cudaError_t launch_tree_build<float>(const Geometry&, int64_t, const fl
 template cudaError_t launch_tree_build<double>(const Geometry&, int64_t, const double*,
                                                const double*, SortBuffers&, void*, cudaStream_t);
 
+
+// ---------------------------------------------------------------------------
+// Tree build without allocation (fmm2d_tree_build_noalloc).
+//
+// For callers that cannot allocate device memory.  The scratch the build
+// needs (two key/value ping-pong buffers, the digit counts and a status
+// word) lives in one file-scope device array of fixed size, so the call
+// itself allocates nothing.  Every GPU that loads the library holds this
+// array (about 4.06 MB) until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocMaxN = int64_t(1) << 18;  // particles per call at most
+constexpr int64_t kNoAllocMaxBlocks = (kNoAllocMaxN + kSortTile - 1) / kSortTile;
+constexpr size_t kNoAllocWords = 4 * kNoAllocMaxN + kRadix * kNoAllocMaxBlocks + 64;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
+
+std::mutex g_noalloc_mu;
+uint32_t* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is asked of
+// the runtime once per device (with that device current) and cached.
+cudaError_t noalloc_scratch(uint32_t** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<uint32_t*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t tree_build_noalloc(int64_t n, const R* xy, const R* gamma, int L, double x0,
+                               double y0, double W, uint32_t* keys_out, uint32_t* perm_out,
+                               uint32_t* leaf_start_out, int* flags_out, uint32_t* scratch,
+                               cudaStream_t s) {
+    uint32_t* kA = scratch;
+    uint32_t* vA = kA + kNoAllocMaxN;
+    uint32_t* kB = vA + kNoAllocMaxN;
+    uint32_t* vB = kB + kNoAllocMaxN;
+    uint32_t* hist = vB + kNoAllocMaxN;
+    int* status = flags_out ? flags_out
+                            : reinterpret_cast<int*>(hist + kRadix * kNoAllocMaxBlocks);
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);  // flags start clear
+    if (e != cudaSuccess) return e;
+    uint32_t nleaf = 1u << (2 * L);
+    if (n == 0) {
+        leaf_bounds_kernel<<<1, 32, 0, s>>>(0, keys_out, nleaf, leaf_start_out);
+        return cudaGetLastError();
+    }
+    KeyParams kp;
+    kp.x0 = x0;
+    kp.y0 = y0;
+    kp.x1 = x0 + W;
+    kp.y1 = y0 + W;
+    kp.scale = ldexp(1.0, L) / W;
+    kp.top = ldexp(1.0, L) - 1.0;
+    int nblocks = (int)((n + kSortTile - 1) / kSortTile);
+    int bits = 2 * L;
+    int passes = bits <= kRadixBits ? 1 : (bits + kRadixBits - 1) / kRadixBits;
+    keys_hist_kernel<R><<<nblocks, kSortThreads, 0, s>>>(n, xy, gamma, kp, kA, vA, hist, nblocks,
+                                                         status);
+    for (int q = 0; q < passes; ++q) {
+        bool even = (q & 1) == 0;
+        uint32_t* sk = even ? kA : kB;
+        uint32_t* sv = even ? vA : vB;
+        bool last = q == passes - 1;
+        uint32_t* dk = last ? keys_out : (even ? kB : kA);
+        uint32_t* dv = last ? perm_out : (even ? vB : vA);
+        int shift = q * kRadixBits;
+        if (q > 0) hist_kernel<<<nblocks, kSortThreads, 0, s>>>(n, sk, shift, hist, nblocks);
+        scan_kernel<<<1, 1024, 0, s>>>(hist, (int64_t)kRadix * nblocks);
+        scatter_kernel<R, false><<<nblocks, kSortThreads, 0, s>>>(
+            n, sk, sv, shift, hist, nblocks, dk, dv, xy, gamma, nullptr);
+    }
+    int lb_blocks = (int)((n + 1 + 255) / 256);
+    leaf_bounds_kernel<<<lb_blocks, 256, 0, s>>>(n, keys_out, nleaf, leaf_start_out);
+    return cudaGetLastError();
+}
+
+}  // namespace
 }  // namespace fmm2d
+
+extern "C" fmm2d_status fmm2d_tree_build_noalloc(int precision, int64_t n, const void* xy_dev,
+                                                 const void* gamma_dev, int L, double x0,
+                                                 double y0, double W, uint32_t* keys_dev,
+                                                 uint32_t* perm_dev, uint32_t* leaf_start_dev,
+                                                 int* flags_dev, cudaStream_t stream) {
+    using namespace fmm2d;
+    if (precision < FMM2D_FP64 || precision > FMM2D_FP32_TC) return FMM2D_INVALID_ARG;
+    if (L < 0 || L > kMaxL || !(W > 0.0) || !isfinite(W) || !isfinite(x0) || !isfinite(y0))
+        return FMM2D_INVALID_ARG;
+    if (n < 0 || n > kNoAllocMaxN) return FMM2D_INVALID_ARG;  // beyond the static scratch
+    if (!leaf_start_dev || (n > 0 && (!xy_dev || !gamma_dev || !keys_dev || !perm_dev)))
+        return FMM2D_INVALID_ARG;
+    uint32_t* scratch = nullptr;
+    if (noalloc_scratch(&scratch) != cudaSuccess) return FMM2D_CUDA_ERROR;
+    cudaError_t e =
+        precision == FMM2D_FP64
+            ? tree_build_noalloc<double>(n, static_cast<const double*>(xy_dev),
+                                         static_cast<const double*>(gamma_dev), L, x0, y0, W,
+                                         keys_dev, perm_dev, leaf_start_dev, flags_dev, scratch,
+                                         stream)
+            : tree_build_noalloc<float>(n, static_cast<const float*>(xy_dev),
+                                        static_cast<const float*>(gamma_dev), L, x0, y0, W,
+                                        keys_dev, perm_dev, leaf_start_dev, flags_dev, scratch,
+                                        stream);
+    return e == cudaSuccess ? FMM2D_OK : FMM2D_CUDA_ERROR;
+}
+
