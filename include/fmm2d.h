@@ -191,7 +191,7 @@ fmm2d_status fmm2d_plan_phase_ms(fmm2d_plan* plan, int age, double* ms_host);
  *                      flags (bit 1 << FMM2D_OUT_OF_DOMAIN, 1 << FMM2D_NONFINITE)
  * Limit: n <= 262144 (2^18); larger n returns FMM2D_INVALID_ARG before any
  * work is enqueued.  Its scratch (key/value ping-pong buffers, digit counts,
- * a status word; about 4.06 MB) is one fixed device array inside the
+ * a status word; about 4.3 MB) is one fixed device array inside the
  * library, held by every GPU that loads the library until the process exits.
  * The call makes no cudaMalloc, cudaFree or other allocating call.
  * The first call on a device looks up that array's device address (once per

@@ -291,7 +291,7 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
     size_t sizes[] = {
         align256(nmax * 4), align256(nmax * 4), align256(nmax * 4), align256(nmax * 4),
         align256(nmax * 4),                                   // keys x2, vals x2, perm
-        align256((size_t)kRadix * nblocks * 4),               // hist
+        align256(((size_t)kRadix * nblocks + kRadix) * 4),    // hist + digit totals
         align256((size_t)(nleaf + 1) * 4),                    // leaf_start
         align256(nmax * psize),                               // particles
         align256((size_t)(g.nboxes > 0 ? g.nboxes : 1) * 2 * g.P * pl->elem),  // me

@@ -7,11 +7,10 @@
 namespace fmm2d {
 namespace {
 
-template <typename R>
+template <typename R, int G>
 __global__ void __launch_bounds__(128)
 l2l_kernel(Geometry g, int level, const R* __restrict__ l2l, R* __restrict__ le) {
-    using C = typename Cplx<R>::T;
-    const int G = g.P;
+    using C = typename Cplx<R>::T;  // G = P lanes per box (16 or 32)
     int lane = threadIdx.x & 31;
     int n = lane % G;
     int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
@@ -26,7 +25,8 @@ l2l_kernel(Geometry g, int level, const R* __restrict__ l2l, R* __restrict__ le)
     C l_own = parent[n];
     const C* t = reinterpret_cast<const C*>(l2l) + (int64_t)q * G * G;
     C acc = cmake<C>(R(0), R(0));
-    for (int k = 0; k < g.p; ++k) {
+#pragma unroll
+    for (int k = 0; k < G; ++k) {  // entries with k >= p are zero
         C lk = cshfl(l_own, k, G);
         acc = cfma(t[k * G + n], lk, acc);
     }
@@ -45,7 +45,10 @@ template <typename R>
 cudaError_t launch_l2l(const Geometry& g, int level, const Tables<R>& t, R* le, cudaStream_t s) {
     int64_t nb = (int64_t)1 << (2 * level);
     int blocks = (int)((nb * g.P + 127) / 128);
-    l2l_kernel<R><<<blocks, 128, 0, s>>>(g, level, t.l2l, le);
+    if (g.P <= 16)
+        l2l_kernel<R, 16><<<blocks, 128, 0, s>>>(g, level, t.l2l, le);
+    else
+        l2l_kernel<R, 32><<<blocks, 128, 0, s>>>(g, level, t.l2l, le);
     return cudaGetLastError();
 }
 

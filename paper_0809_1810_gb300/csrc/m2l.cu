@@ -13,11 +13,10 @@
 namespace fmm2d {
 namespace {
 
-template <typename R>
+template <typename R, int G>
 __global__ void __launch_bounds__(128)
 m2l_kernel(Geometry g, const R* __restrict__ m2l, const R* __restrict__ me, R* __restrict__ le) {
-    using C = typename Cplx<R>::T;
-    const int G = g.P;
+    using C = typename Cplx<R>::T;  // G = P lanes per target box (16 or 32)
     int lane = threadIdx.x & 31;
     int n = lane % G;
     unsigned seg = segment_mask(G);
@@ -41,7 +40,8 @@ m2l_kernel(Geometry g, const R* __restrict__ m2l, const R* __restrict__ me, R* _
                 me + box_slot(g.level_base, l, (uint32_t)sx, (uint32_t)sy) * (2 * g.P));
             C a_own = src[n];
             const C* t = tab + (int64_t)offset_slot(dx, dy) * G * G;
-            for (int k = 0; k < g.p; ++k) {
+#pragma unroll
+            for (int k = 0; k < G; ++k) {  // entries with k >= p are zero
                 C ak = cshfl(a_own, k, G, seg);
                 acc = cfma(t[k * G + n], ak, acc);
             }
@@ -57,7 +57,10 @@ cudaError_t launch_m2l(const Geometry& g, const Tables<R>& t, const R* me, R* le
     if (g.L < 2) return cudaSuccess;
     int64_t threads = g.nboxes * g.P;
     int blocks = (int)((threads + 127) / 128);
-    m2l_kernel<R><<<blocks, 128, 0, s>>>(g, t.m2l, me, le);
+    if (g.P <= 16)
+        m2l_kernel<R, 16><<<blocks, 128, 0, s>>>(g, t.m2l, me, le);
+    else
+        m2l_kernel<R, 32><<<blocks, 128, 0, s>>>(g, t.m2l, me, le);
     return cudaGetLastError();
 }
 

@@ -31,14 +31,7 @@ constexpr int kChunk = 1024;   // source records per shared-memory chunk
 constexpr int kInner = 16;     // pairs per first-level partial sum
 constexpr int kMaxSlices = 8;  // lanes per target when a leaf holds few particles
 constexpr int kPad = kInner * kMaxSlices;
-constexpr int kSeries = 10;    // Taylor coefficients of g
 
-struct NearF32 {
-    float c2;              // log2(e) / (2 sigma^2)
-    float qthr;            // 1 / ln 2  (q = 1)
-    float k0;              // 1 / (4 pi sigma^2 ln 2)
-    float coef[kSeries];   // Taylor coefficients of g in q2
-};
 struct NearF64 {
     double inv2s2;  // 1 / (2 sigma^2)
     double k0;      // 1 / (2 pi)
@@ -56,18 +49,9 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // Radial weight Gamma_j * (1 - e^-q)/r^2 up to the constant k0.
-__device__ __forceinline__ float radial(const NearF32& nm, float r2) {
-    float q2 = r2 * nm.c2;
-    float naive = (1.0f - ex2_approx(-q2)) * rcp_approx(q2);
-    float ser = nm.coef[kSeries - 1];
-#pragma unroll
-    for (int k = kSeries - 2; k >= 0; --k) ser = fmaf(ser, q2, nm.coef[k]);
-    return q2 < nm.qthr ? ser : naive;
-}
 __device__ __forceinline__ double radial(const NearF64& nm, double r2) {
     return r2 > 0.0 ? -expm1(-r2 * nm.inv2s2) / r2 : 0.0;
 }
-__device__ __forceinline__ float k0_of(const NearF32& nm) { return nm.k0; }
 
 // Neumaier's compensated summation step: s + c tracks the exact sum.
 template <typename R>
@@ -187,6 +171,288 @@ p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 near field, the dominant kernel of the FP32 form.
+//
+// Work split: one warp per target leaf (four consecutive Morton leaves per
+// CTA), no CTA-wide barriers.  The warp gathers its local list -- the 9
+// source ranges of the 3x3 neighbourhood, coalesced loads -- into a
+// per-warp shared-memory buffer, sorted by a ballot compaction into a near
+// band (front) and a far band (back): a source whose distance to the leaf's
+// square is at least sqrt(2) sigma (q = 1) is at q >= 1 from every target of
+// the leaf, so the far band never needs the polynomial.
+// Targets go in rounds of 32, one per lane; all lanes read the same source
+// (a shared-memory broadcast).  In a leaf's last, partial round, ns adjacent
+// lanes share a target and split its sources (combined by shuffles).  Both
+// band loops are straight-line code (4 sources unrolled, no per-pair
+// branches).  Lists longer than the buffer are processed in chunks.
+//
+// Pair arithmetic in physical FP32 coordinates: dx = x_i - x_j is exact for
+// nearby particles, q2 = (dx^2 + dy^2) log2(e) / (2 sigma^2).
+// Radial factor g(q2) = (1 - 2^-q2) / q2: MUFU ex2 and rcp for q2 >= 1/ln 2
+// (q >= 1); below that a degree-6 polynomial interpolating g at the
+// Chebyshev nodes of [0, 1/ln 2] (interpolation error 3e-9, below FP32
+// rounding), fitted on the host when the kernel is launched.
+// Sums: kInner sources into fresh registers, then Neumaier-compensated
+// addition into the running sums.
+// ---------------------------------------------------------------------------
+constexpr int kLeafWarps = 4;
+constexpr int kListCap = 640;  // source records per warp buffer (10 KB)
+constexpr int kF32Deg = 6;
+
+struct NearF32v3 {
+    float c2;                 // log2(e) / (2 sigma^2)
+    float qthr;               // polynomial below, MUFU at and above (q2 = 1/ln 2)
+    float kvel;               // 1 / (4 pi sigma^2 ln 2): sum -> velocity
+    float inv_s;              // 1 / s (leaf width)
+    float half_leaf;          // s / 2
+    float band2;              // squared physical distance to the leaf square
+                              // below which a source may be at q < 1
+    float coef[kF32Deg + 1];  // g(q2) ~ sum_k coef[k] q2^k on [0, qthr)
+};
+
+__device__ __forceinline__ float g_far(float q2) {
+    return (1.0f - ex2_approx(-q2)) * rcp_approx(q2);
+}
+__device__ __forceinline__ float g_near(const NearF32v3& nm, float q2) {
+    float poly = nm.coef[kF32Deg];
+#pragma unroll
+    for (int k = kF32Deg - 1; k >= 0; --k) poly = fmaf(poly, q2, nm.coef[k]);
+    return q2 < nm.qthr ? poly : g_far(q2);
+}
+
+template <bool kNear>
+__device__ __forceinline__ void one_source(const NearF32v3& nm, const float4 s, float x, float y,
+                                           float& iu, float& iv) {
+    const float dx = x - s.x, dy = y - s.y;
+    const float q2 = fmaf(dx, dx, dy * dy) * nm.c2;
+    const float w = s.z * (kNear ? g_near(nm, q2) : g_far(q2));
+    iu = fmaf(-dy, w, iu);
+    iv = fmaf(dx, w, iv);
+}
+
+// list[lo, hi) against the lane's target, ns lanes per target (sl = this
+// lane's slot): blocks of kInner sources into fresh sums, then compensated.
+template <bool kNear>
+__device__ __forceinline__ void band_loop(const float4* list, uint32_t lo, uint32_t hi, int ns,
+                                          int sl, const NearF32v3& nm, float x, float y,
+                                          float& su, float& sv, float& cu, float& cv) {
+    if (ns == 1) {
+        uint32_t j = lo;
+        for (; j + kInner <= hi; j += kInner) {
+            float iu = 0.f, iv = 0.f;
+#pragma unroll 1
+            for (int q = 0; q < kInner; q += 4) {
+                one_source<kNear>(nm, list[j + q], x, y, iu, iv);
+                one_source<kNear>(nm, list[j + q + 1], x, y, iu, iv);
+                one_source<kNear>(nm, list[j + q + 2], x, y, iu, iv);
+                one_source<kNear>(nm, list[j + q + 3], x, y, iu, iv);
+            }
+            neumaier_add(su, cu, iu);
+            neumaier_add(sv, cv, iv);
+        }
+        float iu = 0.f, iv = 0.f;
+#pragma unroll 1
+        for (; j < hi; ++j) one_source<kNear>(nm, list[j], x, y, iu, iv);
+        neumaier_add(su, cu, iu);
+        neumaier_add(sv, cv, iv);
+    } else {
+        float iu = 0.f, iv = 0.f;
+        int cnt = 0;
+#pragma unroll 1
+        for (uint32_t jj = lo; jj < hi; jj += ns) {
+            const uint32_t j = jj + sl;
+            float4 r = make_float4(0.f, 0.f, 0.f, 0.f);  // past the end: zero circulation
+            if (j < hi) r = list[j];
+            one_source<kNear>(nm, r, x, y, iu, iv);
+            if (++cnt == kInner) {
+                neumaier_add(su, cu, iu);
+                neumaier_add(sv, cv, iv);
+                iu = iv = 0.f;
+                cnt = 0;
+            }
+        }
+        neumaier_add(su, cu, iu);
+        neumaier_add(sv, cv, iv);
+    }
+}
+
+struct LeafCtx {
+    uint32_t t0, nt;           // the leaf's targets in sorted order
+    const float* le_leaf;      // its local expansion (null when L < 2)
+    float cxh, cxl, cyh, cyl;  // leaf centre as FP32 hi/lo
+    uint32_t rbeg[9], rpre[10];  // the 9 source ranges, prefix of their lengths
+};
+
+// Gather local-list records [cb, cb + cnt) into the warp's buffer: near band
+// at the front (returns its size via nn), far band at the back (nf).
+__device__ __forceinline__ void gather_bands(const float4* __restrict__ sp, const LeafCtx& c,
+                                             const NearF32v3& nm, uint32_t cb, uint32_t cnt,
+                                             float4* buf, uint32_t& nn, uint32_t& nf) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    nn = 0;
+    nf = 0;
+    for (uint32_t vb = 0; vb < cnt; vb += 32) {
+        const uint32_t v = vb + lane;
+        float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool ok = v < cnt, near = false;
+        if (ok) {
+            uint32_t gv = cb + v;
+            int r = 0;
+            while (gv >= c.rpre[r + 1]) ++r;
+            rec = sp[c.rbeg[r] + (gv - c.rpre[r])];
+            float ex = fmaxf(fabsf(rec.x - c.cxh) - nm.half_leaf, 0.f);
+            float ey = fmaxf(fabsf(rec.y - c.cyh) - nm.half_leaf, 0.f);
+            near = fmaf(ex, ex, ey * ey) < nm.band2;
+        }
+        const unsigned bn = __ballot_sync(0xffffffffu, near);
+        const unsigned bf = __ballot_sync(0xffffffffu, ok && !near);
+        if (near) buf[nn + __popc(bn & lt)] = rec;
+        else if (ok) buf[kListCap - 1 - (nf + __popc(bf & lt))] = rec;
+        nn += __popc(bn);
+        nf += __popc(bf);
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kLeafWarps * 32)
+p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
+                   Geometry g, NearF32v3 nm, const float* __restrict__ le,
+                   float* __restrict__ uv) {
+    __shared__ float4 lists[kLeafWarps][kListCap];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t leaf = blockIdx.x * kLeafWarps + warp;
+    const uint32_t nleaf = 1u << (2 * g.L);
+    if (leaf >= nleaf) return;
+    const int nl = 1 << g.L;
+    const uint32_t lx = morton_compact(leaf), ly = morton_compact(leaf >> 1);
+    LeafCtx c;
+    c.t0 = leaf_start[leaf];
+    c.nt = leaf_start[leaf + 1] - c.t0;
+    if (c.nt == 0) return;
+    {  // lane r < 9 reads range r, then every lane learns all nine
+        uint32_t b = 0, len = 0;
+        if (lane < 9) {
+            int sx = (int)lx + lane % 3 - 1, sy = (int)ly + lane / 3 - 1;
+            if (sx >= 0 && sy >= 0 && sx < nl && sy < nl) {
+                uint32_t k = morton_key((uint32_t)sx, (uint32_t)sy);
+                b = leaf_start[k];
+                len = leaf_start[k + 1] - b;
+            }
+        }
+        c.rpre[0] = 0;
+        for (int r = 0; r < 9; ++r) {
+            c.rbeg[r] = __shfl_sync(0xffffffffu, b, r);
+            c.rpre[r + 1] = c.rpre[r] + __shfl_sync(0xffffffffu, len, r);
+        }
+    }
+    const double s = g.W / (double)nl;
+    const double ccx = g.x0 + ((double)lx + 0.5) * s, ccy = g.y0 + ((double)ly + 0.5) * s;
+    c.cxh = (float)ccx;
+    c.cyh = (float)ccy;
+    c.cxl = (float)(ccx - (double)c.cxh);
+    c.cyl = (float)(ccy - (double)c.cyh);
+    c.le_leaf = g.L >= 2 ? le + box_slot(g.level_base, g.L, lx, ly) * (2 * g.P) : nullptr;
+    float4* buf = lists[warp];
+    const uint32_t total = c.rpre[9];
+    const bool one_chunk = total <= kListCap;
+    uint32_t nn = 0, nf = 0;
+    if (one_chunk) gather_bands(sp, c, nm, 0, total, buf, nn, nf);
+
+    for (uint32_t tb = 0; tb < c.nt; tb += 32) {
+        const uint32_t tc = min(32u, c.nt - tb);
+        int ns = 1;  // lanes per target: largest power of two with tc * ns <= 32
+        while (tc * (uint32_t)(2 * ns) <= 32u) ns *= 2;
+        const uint32_t tl = lane / ns;
+        const int sl = lane % ns;
+        const bool active = tl < tc;
+        const float4 rec = sp[c.t0 + tb + (active ? tl : 0)];
+        const float x = rec.x, y = rec.y;
+        float su = 0.f, sv = 0.f, cu = 0.f, cv = 0.f;
+        for (uint32_t cb = 0; cb < total; cb += kListCap) {
+            if (!one_chunk) {
+                __syncwarp();
+                gather_bands(sp, c, nm, cb, min((uint32_t)kListCap, total - cb), buf, nn, nf);
+            }
+            band_loop<true>(buf, 0, nn, ns, sl, nm, x, y, su, sv, cu, cv);
+            band_loop<false>(buf, kListCap - nf, kListCap, ns, sl, nm, x, y, su, sv, cu, cv);
+        }
+        su += cu;
+        sv += cv;
+        for (int o = 1; o < ns; o <<= 1) {
+            su += __shfl_xor_sync(0xffffffffu, su, o);
+            sv += __shfl_xor_sync(0xffffffffu, sv, o);
+        }
+        if (active && sl == 0) {
+            float u = nm.kvel * su, v = nm.kvel * sv;
+            if (c.le_leaf) {  // L2P: w = (1/s) sum_n L~_n zeta^n, zeta = (z - z_leaf) / s
+                float2 zeta = make_float2(((x - c.cxh) - c.cxl) * nm.inv_s,
+                                          ((y - c.cyh) - c.cyl) * nm.inv_s);
+                const float2* Lc = reinterpret_cast<const float2*>(c.le_leaf);
+                float2 w = Lc[g.p - 1];
+                for (int m = g.p - 2; m >= 0; --m) {
+                    float2 t = cmul(w, zeta);
+                    float2 lm = Lc[m];
+                    w = make_float2(t.x + lm.x, t.y + lm.y);
+                }
+                u += nm.inv_s * w.x;
+                v -= nm.inv_s * w.y;
+            }
+            const uint32_t idx = __float_as_uint(rec.w);
+            uv[2 * (int64_t)idx] = u;
+            uv[2 * (int64_t)idx + 1] = v;
+        }
+    }
+}
+
+// Polynomial interpolating g(q2) = (1 - 2^-q2)/q2 at the Chebyshev nodes of
+// [0, a]; coefficients of q2^k.  Solved in double by Gaussian elimination
+// with partial pivoting on the scaled variable u = q2 / a.  Returns the
+// largest relative error on a fine grid (double evaluation).
+double fit_near_polynomial(double a, double* coef) {
+    const int n = kF32Deg + 1;
+    const double pi = 3.14159265358979323846, ln2 = 0.69314718055994530942;
+    auto gfun = [&](double x) { return x > 0.0 ? -expm1(-x * ln2) / x : ln2; };
+    double A[kF32Deg + 1][kF32Deg + 2];
+    for (int i = 0; i < n; ++i) {
+        double u = 0.5 * (cos(pi * (i + 0.5) / n) + 1.0);
+        double pw = 1.0;
+        for (int k = 0; k < n; ++k) {
+            A[i][k] = pw;
+            pw *= u;
+        }
+        A[i][n] = gfun(a * u);
+    }
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        for (int k = 0; k <= n; ++k) {
+            double t = A[c][k];
+            A[c][k] = A[piv][k];
+            A[piv][k] = t;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            double f = A[r][c] / A[c][c];
+            for (int k = c; k <= n; ++k) A[r][k] -= f * A[c][k];
+        }
+    }
+    double scale = 1.0;
+    for (int k = 0; k < n; ++k) {
+        coef[k] = A[k][n] / A[k][k] / scale;
+        scale *= a;
+    }
+    double worst = 0.0;
+    for (int i = 0; i <= 4000; ++i) {
+        double x = a * i / 4000.0, p = coef[n - 1];
+        for (int k = n - 2; k >= 0; --k) p = p * x + coef[k];
+        worst = fmax(worst, fabs(p - gfun(x)) / gfun(x));
+    }
+    return worst;
+}
+
 }  // namespace
 
 template <>
@@ -195,20 +461,22 @@ cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, const void* p
                                   cudaStream_t s) {
     const double ln2 = 0.69314718055994530942;
     const double pi = 3.14159265358979323846;
-    NearF32 nm;
+    NearF32v3 nm;
+    double qthr = 1.0 / ln2;
     nm.c2 = (float)(1.0 / (2.0 * sigma * sigma * ln2));
-    nm.qthr = (float)(1.0 / ln2);
-    nm.k0 = (float)(1.0 / (4.0 * pi * sigma * sigma * ln2));
-    double lk = ln2, fact = 1.0;
-    for (int k = 0; k < kSeries; ++k) {  // (-1)^k ln2^(k+1) / (k+1)!
-        fact *= (double)(k + 1);
-        nm.coef[k] = (float)(((k & 1) ? -1.0 : 1.0) * lk / fact);
-        lk *= ln2;
-    }
+    nm.qthr = (float)qthr;
+    nm.kvel = (float)(1.0 / (4.0 * pi * sigma * sigma * ln2));
+    nm.inv_s = (float)(ldexp(1.0, g.L) / g.W);
+    double coef[kF32Deg + 1];
+    if (fit_near_polynomial(qthr, coef) > 1e-8) return cudaErrorInvalidValue;
+    for (int k = 0; k <= kF32Deg; ++k) nm.coef[k] = (float)coef[k];
+    nm.half_leaf = (float)(0.5 * g.W / ldexp(1.0, g.L));
+    // q < 1 needs a physical distance below sqrt(2) sigma; 2% margin for rounding
+    nm.band2 = (float)(2.0 * sigma * sigma * 1.02);
     unsigned nleaf = 1u << (2 * g.L);
-    p2p_l2p_kernel<float, NearF32><<<nleaf, kThreads, 0, s>>>(
-        reinterpret_cast<const float4*>(particles), leaf_start, g, ldexp(1.0, g.L) / g.W, nm, le,
-        uv);
+    unsigned blocks = (nleaf + kLeafWarps - 1) / kLeafWarps;
+    p2p_l2p_f32_kernel<<<blocks, kLeafWarps * 32, 0, s>>>(
+        reinterpret_cast<const float4*>(particles), leaf_start, g, nm, le, uv);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,13 @@ struct KeyParams {
     double x0, y0, x1, y1;  // closed root box
     double scale;           // 2^L / W
     double top;             // 2^L - 1
+    // FP32 fast path for float inputs: the FP32 estimate of (x - x0) 2^L / W
+    // is trusted when it lies farther than `margin` cells from every cell
+    // edge; otherwise the FP64 expression decides.  Domain bounds are the
+    // float values that bracket the closed root box exactly.
+    bool fast;
+    float x0f, y0f, scalef, margin;
+    float lox, hix, loy, hiy;
 };
 
 __device__ inline uint32_t leaf_coord(double x, double lo, double hi, double scale, double top,
@@ -32,6 +39,21 @@ __device__ inline uint32_t leaf_coord(double x, double lo, double hi, double sca
     if (!(f >= 0.0)) f = 0.0;  // also maps NaN to 0 so that no index runs wild
     if (f > top) f = top;
     return (uint32_t)f;
+}
+
+__device__ inline uint32_t leaf_coord_f32(float x, float lo, float hi, float x0f, float scalef,
+                                          float margin, double lo_d, double scale, double top,
+                                          int* flags) {
+    if (!(x >= lo && x <= hi)) *flags |= (x != x) ? kFlagNonfinite : kFlagOutOfDomain;
+    float f = (x - x0f) * scalef;
+    float fl = floorf(f);
+    float fr = f - fl;
+    if (fr > margin && fr < 1.0f - margin && fl >= 0.0f && fl <= (float)top)
+        return (uint32_t)fl;
+    double fd = floor(((double)x - lo_d) * scale);  // the defining FP64 expression
+    if (!(fd >= 0.0)) fd = 0.0;
+    if (fd > top) fd = top;
+    return (uint32_t)fd;
 }
 
 // Keys of one tile plus the histogram of the first digit.
@@ -49,11 +71,20 @@ keys_hist_kernel(int64_t n, const R* __restrict__ xy, const R* __restrict__ gamm
     for (int it = 0; it < kSortItems; ++it) {
         int64_t i = base + it * kSortThreads + threadIdx.x;
         if (i < n) {
-            double x = (double)xy[2 * i], y = (double)xy[2 * i + 1];
-            double g = (double)gamma[i];
-            if (!isfinite(g)) flags |= kFlagNonfinite;
-            uint32_t ix = leaf_coord(x, kp.x0, kp.x1, kp.scale, kp.top, &flags);
-            uint32_t iy = leaf_coord(y, kp.y0, kp.y1, kp.scale, kp.top, &flags);
+            uint32_t ix, iy;
+            if (sizeof(R) == 4 && kp.fast) {
+                float x = (float)xy[2 * i], y = (float)xy[2 * i + 1];
+                if (!isfinite((float)gamma[i])) flags |= kFlagNonfinite;
+                ix = leaf_coord_f32(x, kp.lox, kp.hix, kp.x0f, kp.scalef, kp.margin, kp.x0,
+                                    kp.scale, kp.top, &flags);
+                iy = leaf_coord_f32(y, kp.loy, kp.hiy, kp.y0f, kp.scalef, kp.margin, kp.y0,
+                                    kp.scale, kp.top, &flags);
+            } else {
+                double x = (double)xy[2 * i], y = (double)xy[2 * i + 1];
+                if (!isfinite((double)gamma[i])) flags |= kFlagNonfinite;
+                ix = leaf_coord(x, kp.x0, kp.x1, kp.scale, kp.top, &flags);
+                iy = leaf_coord(y, kp.y0, kp.y1, kp.scale, kp.top, &flags);
+            }
             uint32_t k = morton_key(ix, iy);
             keys[i] = k;
             vals[i] = (uint32_t)i;
@@ -83,38 +114,35 @@ hist_kernel(int64_t n, const uint32_t* __restrict__ keys, int shift, uint32_t* _
         hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
 }
 
-// Exclusive scan of `total` counts in place, one block of 1024 threads.
-__global__ void __launch_bounds__(1024) scan_kernel(uint32_t* data, int64_t total) {
-    __shared__ uint32_t warp_sums[32];
-    int64_t per = (total + blockDim.x - 1) / blockDim.x;
-    int64_t lo = threadIdx.x * per;
-    int64_t hi = lo + per < total ? lo + per : total;
-    uint32_t sum = 0;
-    for (int64_t i = lo; i < hi; ++i) sum += data[i];
-    // block-wide exclusive scan of the per-thread sums
+// Exclusive scan of each digit's per-tile counts in place (one CTA per
+// digit, counts stored digit-major), and the digit's total count.
+__global__ void __launch_bounds__(256)
+scan_digits_kernel(uint32_t* __restrict__ hist, int nblocks, uint32_t* __restrict__ digit_total) {
+    __shared__ uint32_t warp_sums[8];
+    uint32_t* row = hist + (int64_t)blockIdx.x * nblocks;
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t incl = sum;
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) warp_sums[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = warp_sums[lane];
+    uint32_t carry = 0;
+    for (int base = 0; base < nblocks; base += 256) {
+        int i = base + threadIdx.x;
+        uint32_t v = i < nblocks ? row[i] : 0u;
+        uint32_t incl = v;
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t v = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += v;
+            uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
         }
-        warp_sums[lane] = w;  // inclusive
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        uint32_t before = 0, tile = 0;
+        for (int w = 0; w < 8; ++w) {
+            uint32_t ws = warp_sums[w];
+            if (w < warp) before += ws;
+            tile += ws;
+        }
+        if (i < nblocks) row[i] = carry + before + incl - v;
+        carry += tile;
+        __syncthreads();
     }
-    __syncthreads();
-    uint32_t run = (warp > 0 ? warp_sums[warp - 1] : 0) + incl - sum;
-    for (int64_t i = lo; i < hi; ++i) {
-        uint32_t v = data[i];
-        data[i] = run;
-        run += v;
-    }
+    if (threadIdx.x == 0) digit_total[blockIdx.x] = carry;
 }
 
 // Stable scatter of one tile.  With R != void the pass is the last one and
@@ -122,7 +150,8 @@ __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* data, int64_t tota
 template <typename R, bool kLast>
 __global__ void __launch_bounds__(kSortThreads)
 scatter_kernel(int64_t n, const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-               int shift, const uint32_t* __restrict__ offsets, int nblocks,
+               int shift, const uint32_t* __restrict__ offsets,
+               const uint32_t* __restrict__ digit_total, int nblocks,
                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                const R* __restrict__ xy, const R* __restrict__ gamma,
                typename ParticleOf<R>::type* __restrict__ particles) {
@@ -131,6 +160,7 @@ scatter_kernel(int64_t n, const uint32_t* __restrict__ keys_in, const uint32_t* 
     constexpr int kIters = kPerWarp / 32;
     __shared__ uint32_t wcnt[kWarps][kRadix];
     __shared__ uint32_t dbase[kRadix];
+    __shared__ uint32_t dsum[kWarps];
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int d = lane; d < kRadix; d += 32) wcnt[warp][d] = 0;
     __syncwarp();
@@ -151,8 +181,22 @@ scatter_kernel(int64_t n, const uint32_t* __restrict__ keys_in, const uint32_t* 
         __syncwarp();
         rank[it] = before + __popc(peers & lt_mask);
     }
-    __syncthreads();
-    // exclusive offsets of the warps within each digit, and the tile's base
+    // exclusive scan of the digit totals: where each digit starts overall
+    static_assert(kRadix == kSortThreads, "one thread per digit");
+    {
+        uint32_t tot = digit_total[threadIdx.x], incl = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) dsum[warp] = incl;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += dsum[w];
+        dbase[threadIdx.x] = before + incl - tot +
+                             offsets[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+    }
+    // exclusive offsets of the warps within each digit
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
         uint32_t run = 0;
 #pragma unroll
@@ -161,7 +205,6 @@ scatter_kernel(int64_t n, const uint32_t* __restrict__ keys_in, const uint32_t* 
             wcnt[w][d] = run;
             run += c;
         }
-        dbase[d] = offsets[(int64_t)d * nblocks + blockIdx.x];
     }
     __syncthreads();
 #pragma unroll
@@ -192,6 +235,38 @@ __global__ void leaf_bounds_kernel(int64_t n, const uint32_t* __restrict__ skeys
     }
 }
 
+// Key parameters for root box (x0, y0, W) at level L.  The FP32 fast path
+// is enabled for float inputs when its error bound stays well below a cell.
+KeyParams make_key_params(double x0, double y0, double W, int L) {
+    KeyParams kp;
+    kp.x0 = x0;
+    kp.y0 = y0;
+    kp.x1 = x0 + W;
+    kp.y1 = y0 + W;
+    kp.scale = ldexp(1.0, L) / W;
+    kp.top = ldexp(1.0, L) - 1.0;
+    kp.x0f = (float)x0;
+    kp.y0f = (float)y0;
+    kp.scalef = (float)kp.scale;
+    // |error of the FP32 estimate| <= 2^-24 (4 * 2^L + max|x0,y0| * 2^L / W) cells
+    double err = ldexp(4.0 * ldexp(1.0, L) + fmax(fabs(x0), fabs(y0)) * kp.scale, -24);
+    kp.margin = (float)(2.0 * err);
+    kp.fast = 2.0 * err < 0.05;
+    auto up = [](double v) {  // smallest float >= v
+        float f = (float)v;
+        return (double)f < v ? nextafterf(f, INFINITY) : f;
+    };
+    auto down = [](double v) {  // largest float <= v
+        float f = (float)v;
+        return (double)f > v ? nextafterf(f, -INFINITY) : f;
+    };
+    kp.lox = up(kp.x0);
+    kp.hix = down(kp.x1);
+    kp.loy = up(kp.y0);
+    kp.hiy = down(kp.y1);
+    return kp;
+}
+
 }  // namespace
 
 template <typename R>
@@ -203,17 +278,11 @@ cudaError_t launch_tree_build(const Geometry& g, int64_t n, const R* xy, const R
         leaf_bounds_kernel<<<1, 32, 0, s>>>(0, sb.keys[0], nleaf, sb.leaf_start);
         return cudaGetLastError();
     }
-    KeyParams kp;
-    kp.x0 = g.x0;
-    kp.y0 = g.y0;
-    kp.x1 = g.x0 + g.W;
-    kp.y1 = g.y0 + g.W;
-    kp.scale = ldexp(1.0, g.L) / g.W;
-    kp.top = ldexp(1.0, g.L) - 1.0;
+    KeyParams kp = make_key_params(g.x0, g.y0, g.W, g.L);
     int nblocks = (int)((n + kSortTile - 1) / kSortTile);
     int bits = 2 * g.L;
     int passes = bits <= kRadixBits ? 1 : (bits + kRadixBits - 1) / kRadixBits;
-    int64_t hist_len = (int64_t)kRadix * nblocks;
+    uint32_t* digit_total = sb.hist + (int64_t)kRadix * nblocks;
     keys_hist_kernel<R><<<nblocks, kSortThreads, 0, s>>>(n, xy, gamma, kp, sb.keys[0], sb.vals[0],
                                                          sb.hist, nblocks, sb.status);
     for (int q = 0; q < passes; ++q) {
@@ -221,15 +290,15 @@ cudaError_t launch_tree_build(const Geometry& g, int64_t n, const R* xy, const R
         int shift = q * kRadixBits;
         if (q > 0)
             hist_kernel<<<nblocks, kSortThreads, 0, s>>>(n, sb.keys[src], shift, sb.hist, nblocks);
-        scan_kernel<<<1, 1024, 0, s>>>(sb.hist, hist_len);
+        scan_digits_kernel<<<kRadix, 256, 0, s>>>(sb.hist, nblocks, digit_total);
         if (q == passes - 1)
             scatter_kernel<R, true><<<nblocks, kSortThreads, 0, s>>>(
-                n, sb.keys[src], sb.vals[src], shift, sb.hist, nblocks, sb.keys[dst], sb.perm, xy,
-                gamma, reinterpret_cast<P*>(particles));
+                n, sb.keys[src], sb.vals[src], shift, sb.hist, digit_total, nblocks, sb.keys[dst],
+                sb.perm, xy, gamma, reinterpret_cast<P*>(particles));
         else
             scatter_kernel<R, false><<<nblocks, kSortThreads, 0, s>>>(
-                n, sb.keys[src], sb.vals[src], shift, sb.hist, nblocks, sb.keys[dst], sb.vals[dst],
-                xy, gamma, reinterpret_cast<P*>(particles));
+                n, sb.keys[src], sb.vals[src], shift, sb.hist, digit_total, nblocks, sb.keys[dst],
+                sb.vals[dst], xy, gamma, reinterpret_cast<P*>(particles));
     }
     const uint32_t* sorted = sb.keys[passes & 1];
     int lb_blocks = (int)((n + 1 + 255) / 256);
@@ -251,13 +320,13 @@ template cudaError_t launch_tree_build<double>(const Geometry&, int64_t, const d
 // needs (two key/value ping-pong buffers, the digit counts and a status
 // word) lives in one file-scope device array of fixed size, so the call
 // itself allocates nothing.  Every GPU that loads the library holds this
-// array (about 4.06 MB) until the process exits.
+// array (about 4.07 MB) until the process exits.
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr int64_t kNoAllocMaxN = int64_t(1) << 18;  // particles per call at most
 constexpr int64_t kNoAllocMaxBlocks = (kNoAllocMaxN + kSortTile - 1) / kSortTile;
-constexpr size_t kNoAllocWords = 4 * kNoAllocMaxN + kRadix * kNoAllocMaxBlocks + 64;
+constexpr size_t kNoAllocWords = 4 * kNoAllocMaxN + kRadix * kNoAllocMaxBlocks + kRadix + 64;
 constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
@@ -294,8 +363,8 @@ cudaError_t tree_build_noalloc(int64_t n, const R* xy, const R* gamma, int L, do
     uint32_t* kB = vA + kNoAllocMaxN;
     uint32_t* vB = kB + kNoAllocMaxN;
     uint32_t* hist = vB + kNoAllocMaxN;
-    int* status = flags_out ? flags_out
-                            : reinterpret_cast<int*>(hist + kRadix * kNoAllocMaxBlocks);
+    uint32_t* digit_total = hist + kRadix * kNoAllocMaxBlocks;
+    int* status = flags_out ? flags_out : reinterpret_cast<int*>(digit_total + kRadix);
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);  // flags start clear
     if (e != cudaSuccess) return e;
     uint32_t nleaf = 1u << (2 * L);
@@ -303,13 +372,7 @@ cudaError_t tree_build_noalloc(int64_t n, const R* xy, const R* gamma, int L, do
         leaf_bounds_kernel<<<1, 32, 0, s>>>(0, keys_out, nleaf, leaf_start_out);
         return cudaGetLastError();
     }
-    KeyParams kp;
-    kp.x0 = x0;
-    kp.y0 = y0;
-    kp.x1 = x0 + W;
-    kp.y1 = y0 + W;
-    kp.scale = ldexp(1.0, L) / W;
-    kp.top = ldexp(1.0, L) - 1.0;
+    KeyParams kp = make_key_params(x0, y0, W, L);
     int nblocks = (int)((n + kSortTile - 1) / kSortTile);
     int bits = 2 * L;
     int passes = bits <= kRadixBits ? 1 : (bits + kRadixBits - 1) / kRadixBits;
@@ -324,9 +387,9 @@ cudaError_t tree_build_noalloc(int64_t n, const R* xy, const R* gamma, int L, do
         uint32_t* dv = last ? perm_out : (even ? vB : vA);
         int shift = q * kRadixBits;
         if (q > 0) hist_kernel<<<nblocks, kSortThreads, 0, s>>>(n, sk, shift, hist, nblocks);
-        scan_kernel<<<1, 1024, 0, s>>>(hist, (int64_t)kRadix * nblocks);
+        scan_digits_kernel<<<kRadix, 256, 0, s>>>(hist, nblocks, digit_total);
         scatter_kernel<R, false><<<nblocks, kSortThreads, 0, s>>>(
-            n, sk, sv, shift, hist, nblocks, dk, dv, xy, gamma, nullptr);
+            n, sk, sv, shift, hist, digit_total, nblocks, dk, dv, xy, gamma, nullptr);
     }
     int lb_blocks = (int)((n + 1 + 255) / 256);
     leaf_bounds_kernel<<<lb_blocks, 256, 0, s>>>(n, keys_out, nleaf, leaf_start_out);

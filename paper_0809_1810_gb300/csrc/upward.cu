@@ -3,9 +3,10 @@
 //   P2M  a~_m = sum_{i in leaf} c_i zeta_i^m,  c_i = -j Gamma_i / 2pi,
 //        zeta_i = (z_i - z_leaf) / s_leaf                          (Eq. 20-21)
 //   M2M  parent b~_n = sum_quadrants sum_{k<=n} M2M[q]_{nk} a~_k(child)  (Sec. 3.3.2)
-// The local coordinate zeta is formed in FP64 from the FP64 leaf coordinate
-// (x - x0) 2^L / W, so that FP32 expansions are centred exactly where the
-// translation tables assume.
+// The leaf centre is formed once per leaf in FP64 and held as an FP32 hi/lo
+// pair, so that zeta = ((x - c_hi) - c_lo) / s is accurate to FP32 relative
+// to the leaf size and the expansion is centred where the translation
+// tables assume.
 #include "fmm2d_internal.cuh"
 
 namespace fmm2d {
@@ -26,15 +27,17 @@ p2m_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
     if (leaf >= nleaf) return;
     uint32_t ix = morton_compact((uint32_t)leaf), iy = morton_compact((uint32_t)leaf >> 1);
     uint32_t b = leaf_start[leaf], e = leaf_start[leaf + 1];
+    double cx = g.x0 + ((double)ix + 0.5) / scale, cy = g.y0 + ((double)iy + 0.5) / scale;
+    R cxh = (R)cx, cyh = (R)cy;
+    R cxl = (R)(cx - (double)cxh), cyl = (R)(cy - (double)cyh);
+    R inv_s = (R)scale;
     C acc[PMAX];
 #pragma unroll
     for (int m = 0; m < PMAX; ++m) acc[m] = cmake<C>(R(0), R(0));
     for (uint32_t r = b + lane; r < e; r += 32) {
         auto q = sp[r];
-        double xi = ((double)q.x - g.x0) * scale - ((double)ix + 0.5);
-        double eta = ((double)q.y - g.y0) * scale - ((double)iy + 0.5);
-        C zeta = cmake<C>((R)xi, (R)eta);
-        C pw = cmake<C>(R(0), (R)(-(double)q.z / kTwoPi));  // c_i = -j Gamma / 2pi
+        C zeta = cmake<C>(((q.x - cxh) - cxl) * inv_s, ((q.y - cyh) - cyl) * inv_s);
+        C pw = cmake<C>(R(0), -q.z * (R)(1.0 / kTwoPi));  // c_i = -j Gamma / 2pi
 #pragma unroll
         for (int m = 0; m < PMAX; ++m) {
             if (m < g.p) {
@@ -63,11 +66,10 @@ p2m_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
 }
 
 // One group of P lanes per parent box at `level`; lane n computes b~_n.
-template <typename R>
+template <typename R, int G>
 __global__ void __launch_bounds__(128)
 m2m_kernel(Geometry g, int level, const R* __restrict__ m2m, R* __restrict__ me) {
-    using C = typename Cplx<R>::T;
-    const int G = g.P;  // 16 or 32 lanes per box
+    using C = typename Cplx<R>::T;  // G = P lanes per box (16 or 32)
     int lane = threadIdx.x & 31;
     int n = lane % G;
     int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
@@ -84,7 +86,8 @@ m2m_kernel(Geometry g, int level, const R* __restrict__ m2m, R* __restrict__ me)
                                                              (2 * g.P));
         C a_own = child[n];
         const C* tq = tab + (int64_t)q * G * G;
-        for (int k = 0; k < g.p; ++k) {
+#pragma unroll
+        for (int k = 0; k < G; ++k) {  // entries with k >= p are zero
             C ak = cshfl(a_own, k, G);
             acc = cfma(tq[k * G + n], ak, acc);
         }
@@ -115,7 +118,10 @@ cudaError_t launch_m2m(const Geometry& g, int level, const Tables<R>& t, R* me, 
     int64_t nb = (int64_t)1 << (2 * level);
     int64_t threads = nb * g.P;
     int blocks = (int)((threads + 127) / 128);
-    m2m_kernel<R><<<blocks, 128, 0, s>>>(g, level, t.m2m, me);
+    if (g.P <= 16)
+        m2m_kernel<R, 16><<<blocks, 128, 0, s>>>(g, level, t.m2m, me);
+    else
+        m2m_kernel<R, 32><<<blocks, 128, 0, s>>>(g, level, t.m2m, me);
     return cudaGetLastError();
 }
 
