@@ -116,15 +116,16 @@ cudaError_t enqueue(fmm2d_plan* pl, int64_t n, const R* xy, const R* gamma, R* u
     STEP(mark(pl, 0, s));
     STEP(launch_tree_build<R>(g, n, xy, gamma, pl->sb, pl->particles, s));
     STEP(mark(pl, 1, s));
-    if (g.L >= 2) STEP(launch_p2m<R>(g, pl->particles, pl->sb.leaf_start, me, s));
+    if (g.L >= 2) STEP(launch_p2m<R>(g, pl->particles, pl->sb.leaf_start, t, me, s));
     STEP(mark(pl, 2, s));
-    for (int l = g.L - 1; l >= 2; --l) STEP(launch_m2m<R>(g, l, t, me, s));
+    if (g.L >= 4) STEP(launch_m2m<R>(g, t, me, s));
     STEP(mark(pl, 3, s));
     if (g.L >= 2) STEP(launch_m2l<R>(g, t, me, le, s));
     STEP(mark(pl, 4, s));
-    for (int l = 3; l <= g.L; ++l) STEP(launch_l2l<R>(g, l, t, le, s));
+    if (g.L >= 4) STEP(launch_l2l<R>(g, t, le, s));
     STEP(mark(pl, 5, s));
-    STEP(launch_p2p_l2p<R>(g, pl->prm.sigma, pl->particles, pl->sb.leaf_start, le, uv, s));
+    STEP(launch_p2p_l2p<R>(g, pl->prm.sigma, pl->particles, pl->sb.leaf_start, le, t.l2l, uv,
+                           s));
     STEP(mark(pl, 6, s));
 #undef STEP
     return cudaSuccess;

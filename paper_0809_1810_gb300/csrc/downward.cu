@@ -1,34 +1,34 @@
 // Downward sweep, L2L part (Sec. 3.3.3): for levels 3..L each box adds its
 // parent's complete local expansion, re-expanded about its own centre:
 //   L~_n(child) += sum_{k>=n} L2L[q]_{nk} L~_k(parent),  q = child quadrant.
-// Level l runs after level l-1 is complete, one launch per level.
+// Level l runs after level l-1 is complete.  Levels 3 .. 4 run in one
+// single-CTA launch (a barrier between levels), levels 5 .. L-1 one launch
+// each; the leaf level is folded into the near-field kernel, which forms
+// each leaf's expansion from its own M2L part and its parent's.  The
+// 4-quadrant L2L table is staged in shared memory.
 #include "fmm2d_internal.cuh"
 
 namespace fmm2d {
 namespace {
 
+constexpr int kTopLevel = 4;
+
 template <typename R, int G>
-__global__ void __launch_bounds__(128)
-l2l_kernel(Geometry g, int level, const R* __restrict__ l2l, R* __restrict__ le) {
-    using C = typename Cplx<R>::T;  // G = P lanes per box (16 or 32)
-    int lane = threadIdx.x & 31;
-    int n = lane % G;
-    int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
-    int64_t nb = (int64_t)1 << (2 * level);
-    bool valid = gid < nb;
-    int64_t slot = g.level_base[level] + (valid ? gid : 0);
+__device__ __forceinline__ void l2l_box(const Geometry& g, int level, int64_t slot, bool valid,
+                                        const typename Cplx<R>::T* tab, R* __restrict__ le) {
+    using C = typename Cplx<R>::T;
+    const int n = (threadIdx.x & 31) % G;
     uint32_t ix, iy;
     slot_box(g.level_base, level, slot, &ix, &iy);
-    int q = (int)(((iy & 1u) << 1) | (ix & 1u));
+    const int q = (int)(((iy & 1u) << 1) | (ix & 1u));
     const C* parent = reinterpret_cast<const C*>(
         le + box_slot(g.level_base, level - 1, ix >> 1, iy >> 1) * (2 * g.P));
     C l_own = parent[n];
-    const C* t = reinterpret_cast<const C*>(l2l) + (int64_t)q * G * G;
     C acc = cmake<C>(R(0), R(0));
 #pragma unroll
-    for (int k = 0; k < G; ++k) {  // entries with k >= p are zero
+    for (int k = 0; k < G; ++k) {  // entries with k >= p or k < n are zero
         C lk = cshfl(l_own, k, G);
-        acc = cfma(t[k * G + n], lk, acc);
+        acc = cfma(tab[(q * G + k) * G + n], lk, acc);
     }
     if (valid) {
         C* dst = reinterpret_cast<C*>(le + slot * (2 * g.P));
@@ -39,22 +39,69 @@ l2l_kernel(Geometry g, int level, const R* __restrict__ l2l, R* __restrict__ le)
     }
 }
 
+template <typename R, int G>
+__device__ __forceinline__ void stage_l2l_table(const R* __restrict__ src,
+                                                typename Cplx<R>::T* dst) {
+    using C = typename Cplx<R>::T;
+    const C* s = reinterpret_cast<const C*>(src);
+    for (int i = threadIdx.x; i < 4 * G * G; i += blockDim.x) dst[i] = s[i];
+    __syncthreads();
+}
+
+template <typename R, int G>
+__global__ void __launch_bounds__(256)
+l2l_level_kernel(Geometry g, int level, const R* __restrict__ l2l, R* __restrict__ le) {
+    using C = typename Cplx<R>::T;
+    __shared__ C tab[4 * G * G];
+    stage_l2l_table<R, G>(l2l, tab);
+    int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    int64_t nb = (int64_t)1 << (2 * level);
+    bool valid = gid < nb;
+    l2l_box<R, G>(g, level, g.level_base[level] + (valid ? gid : 0), valid, tab, le);
+}
+
+template <typename R, int G>
+__global__ void __launch_bounds__(1024)
+l2l_top_kernel(Geometry g, int lhi, const R* __restrict__ l2l, R* __restrict__ le) {
+    using C = typename Cplx<R>::T;
+    __shared__ C tab[4 * G * G];
+    stage_l2l_table<R, G>(l2l, tab);
+    for (int level = 3; level <= lhi; ++level) {
+        int64_t nb = (int64_t)1 << (2 * level);
+        for (int64_t base = 0; base < nb * G; base += blockDim.x) {
+            int64_t gid = (base + threadIdx.x) / G;
+            bool valid = gid < nb;
+            l2l_box<R, G>(g, level, g.level_base[level] + (valid ? gid : 0), valid, tab, le);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 template <typename R>
-cudaError_t launch_l2l(const Geometry& g, int level, const Tables<R>& t, R* le, cudaStream_t s) {
-    int64_t nb = (int64_t)1 << (2 * level);
-    int blocks = (int)((nb * g.P + 127) / 128);
-    if (g.P <= 16)
-        l2l_kernel<R, 16><<<blocks, 128, 0, s>>>(g, level, t.l2l, le);
-    else
-        l2l_kernel<R, 32><<<blocks, 128, 0, s>>>(g, level, t.l2l, le);
+cudaError_t launch_l2l(const Geometry& g, const Tables<R>& t, R* le, cudaStream_t s) {
+    int lhi = g.L - 1 < kTopLevel ? g.L - 1 : kTopLevel;
+    if (lhi >= 3) {
+        if (g.P <= 16)
+            l2l_top_kernel<R, 16><<<1, 1024, 0, s>>>(g, lhi, t.l2l, le);
+        else
+            l2l_top_kernel<R, 32><<<1, 1024, 0, s>>>(g, lhi, t.l2l, le);
+    }
+    for (int level = kTopLevel + 1; level <= g.L - 1; ++level) {
+        int64_t threads = ((int64_t)1 << (2 * level)) * g.P;
+        int blocks = (int)((threads + 255) / 256);
+        if (g.P <= 16)
+            l2l_level_kernel<R, 16><<<blocks, 256, 0, s>>>(g, level, t.l2l, le);
+        else
+            l2l_level_kernel<R, 32><<<blocks, 256, 0, s>>>(g, level, t.l2l, le);
+    }
     return cudaGetLastError();
 }
 
-template cudaError_t launch_l2l<float>(const Geometry&, int, const Tables<float>&, float*,
+template cudaError_t launch_l2l<float>(const Geometry&, const Tables<float>&, float*,
                                        cudaStream_t);
-template cudaError_t launch_l2l<double>(const Geometry&, int, const Tables<double>&, double*,
+template cudaError_t launch_l2l<double>(const Geometry&, const Tables<double>&, double*,
                                         cudaStream_t);
 
 }  // namespace fmm2d

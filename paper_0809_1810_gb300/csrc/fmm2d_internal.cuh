@@ -124,16 +124,17 @@ cudaError_t launch_tree_build(const Geometry& g, int64_t n, const R* xy, const R
 
 template <typename R>
 cudaError_t launch_p2m(const Geometry& g, const void* particles, const uint32_t* leaf_start,
-                       R* me, cudaStream_t s);
+                       const Tables<R>& t, R* me, cudaStream_t s);
 template <typename R>
-cudaError_t launch_m2m(const Geometry& g, int level, const Tables<R>& t, R* me, cudaStream_t s);
+cudaError_t launch_m2m(const Geometry& g, const Tables<R>& t, R* me, cudaStream_t s);
 template <typename R>
 cudaError_t launch_m2l(const Geometry& g, const Tables<R>& t, const R* me, R* le, cudaStream_t s);
 template <typename R>
-cudaError_t launch_l2l(const Geometry& g, int level, const Tables<R>& t, R* le, cudaStream_t s);
+cudaError_t launch_l2l(const Geometry& g, const Tables<R>& t, R* le, cudaStream_t s);
 template <typename R>
 cudaError_t launch_p2p_l2p(const Geometry& g, double sigma, const void* particles,
-                           const uint32_t* leaf_start, const R* le, R* uv, cudaStream_t s);
+                           const uint32_t* leaf_start, const R* le, const R* l2l, R* uv,
+                           cudaStream_t s);
 
 template <typename R>
 cudaError_t launch_direct_sampled(const Geometry& g, double sigma, int kernel, int64_t n,
@@ -188,6 +189,27 @@ __device__ inline T cshfl(T v, int src, int width, unsigned mask = 0xffffffffu) 
 __device__ inline unsigned segment_mask(int G) {
     int lane = threadIdx.x & 31;
     return G == 32 ? 0xffffffffu : (0xffffu << (lane & 16));
+}
+
+// Centre of leaf (ix, iy) at level L as an FP32 hi/lo pair, formed in FP64
+// by lane 0 of the warp and broadcast (FP64 is slow; this is its only use).
+// Every lane of the warp must call it.
+__device__ inline void leaf_centre_hilo(double x0, double y0, double W, int L, uint32_t ix,
+                                        uint32_t iy, float* cxh, float* cxl, float* cyh,
+                                        float* cyl) {
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if ((threadIdx.x & 31) == 0) {
+        double s = W * ldexp(1.0, -L);
+        double cx = x0 + ((double)ix + 0.5) * s, cy = y0 + ((double)iy + 0.5) * s;
+        v[0] = (float)cx;
+        v[1] = (float)(cx - (double)v[0]);
+        v[2] = (float)cy;
+        v[3] = (float)(cy - (double)v[2]);
+    }
+    *cxh = __shfl_sync(0xffffffffu, v[0], 0);
+    *cxl = __shfl_sync(0xffffffffu, v[1], 0);
+    *cyh = __shfl_sync(0xffffffffu, v[2], 0);
+    *cyl = __shfl_sync(0xffffffffu, v[3], 0);
 }
 
 // Decode the box of level l held by expansion slot `slot` (inverse of box_slot).

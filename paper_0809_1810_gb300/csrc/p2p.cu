@@ -66,7 +66,7 @@ template <typename R, typename NM>
 __global__ void __launch_bounds__(kThreads)
 p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
                const uint32_t* __restrict__ leaf_start, Geometry g, double scale, NM nm,
-               const R* __restrict__ le, R* __restrict__ uv) {
+               const R* __restrict__ le, const R* __restrict__ l2l, R* __restrict__ uv) {
     using PT = ParticleOf<R>;
     using P = typename PT::type;
     using C = typename Cplx<R>::T;
@@ -92,9 +92,17 @@ p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
         rpre[tid + 1] = len;
     }
     const bool far = g.L >= 2;
-    if (far && tid < g.P)
-        le_s[tid] = reinterpret_cast<const C*>(le + box_slot(g.level_base, g.L, ix, iy) *
-                                                        (2 * g.P))[tid];
+    if (far && tid < g.P) {  // the leaf's LE: its M2L part plus L2L of its parent's
+        C v = reinterpret_cast<const C*>(le + box_slot(g.level_base, g.L, ix, iy) * (2 * g.P))[tid];
+        if (g.L >= 3) {
+            const C* par = reinterpret_cast<const C*>(
+                le + box_slot(g.level_base, g.L - 1, ix >> 1, iy >> 1) * (2 * g.P));
+            const C* t = reinterpret_cast<const C*>(l2l) +
+                         (int64_t)(((iy & 1u) << 1) | (ix & 1u)) * g.P * g.P;
+            for (int k = 0; k < g.P; ++k) v = cfma(t[k * g.P + tid], par[k], v);
+        }
+        le_s[tid] = v;
+    }
     __syncthreads();
     if (tid == 0) {
         rpre[0] = 0;
@@ -197,17 +205,21 @@ p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
 // addition into the running sums.
 // ---------------------------------------------------------------------------
 constexpr int kLeafWarps = 4;
-constexpr int kListCap = 640;  // source records per warp buffer (10 KB)
+#ifndef FMM2D_P2P_LIST_CAP
+#define FMM2D_P2P_LIST_CAP 640
+#endif
+constexpr int kListCap = FMM2D_P2P_LIST_CAP;  // source records per warp buffer
 constexpr int kF32Deg = 6;
 
 struct NearF32v3 {
-    float c2;                 // log2(e) / (2 sigma^2)
+    float sc;                 // coordinate scale: q2 = |dX|^2 with X = (x - centre) sc
     float qthr;               // polynomial below, MUFU at and above (q2 = 1/ln 2)
-    float kvel;               // 1 / (4 pi sigma^2 ln 2): sum -> velocity
+    float kvel;               // 1 / (4 pi sigma^2 ln 2 sc): sum -> velocity
+    float kzeta;              // 1 / (sc s): scaled coordinate -> zeta
     float inv_s;              // 1 / s (leaf width)
-    float half_leaf;          // s / 2
-    float band2;              // squared physical distance to the leaf square
-                              // below which a source may be at q < 1
+    float half_leaf;          // s sc / 2, half the leaf in scaled units
+    float band2;              // squared scaled distance to the leaf square below
+                              // which a source may be at q < 1
     float coef[kF32Deg + 1];  // g(q2) ~ sum_k coef[k] q2^k on [0, qthr)
 };
 
@@ -225,7 +237,7 @@ template <bool kNear>
 __device__ __forceinline__ void one_source(const NearF32v3& nm, const float4 s, float x, float y,
                                            float& iu, float& iv) {
     const float dx = x - s.x, dy = y - s.y;
-    const float q2 = fmaf(dx, dx, dy * dy) * nm.c2;
+    const float q2 = fmaf(dx, dx, dy * dy);
     const float w = s.z * (kNear ? g_near(nm, q2) : g_far(q2));
     iu = fmaf(-dy, w, iu);
     iv = fmaf(dx, w, iv);
@@ -251,11 +263,13 @@ __device__ __forceinline__ void band_loop(const float4* list, uint32_t lo, uint3
             neumaier_add(su, cu, iu);
             neumaier_add(sv, cv, iv);
         }
-        float iu = 0.f, iv = 0.f;
+        if (j < hi) {
+            float iu = 0.f, iv = 0.f;
 #pragma unroll 1
-        for (; j < hi; ++j) one_source<kNear>(nm, list[j], x, y, iu, iv);
-        neumaier_add(su, cu, iu);
-        neumaier_add(sv, cv, iv);
+            for (; j < hi; ++j) one_source<kNear>(nm, list[j], x, y, iu, iv);
+            neumaier_add(su, cu, iu);
+            neumaier_add(sv, cv, iv);
+        }
     } else {
         float iu = 0.f, iv = 0.f;
         int cnt = 0;
@@ -281,11 +295,13 @@ struct LeafCtx {
     uint32_t t0, nt;           // the leaf's targets in sorted order
     const float* le_leaf;      // its local expansion (null when L < 2)
     float cxh, cxl, cyh, cyl;  // leaf centre as FP32 hi/lo
-    uint32_t rbeg[9], rpre[10];  // the 9 source ranges, prefix of their lengths
+    const uint32_t* rbeg;      // the 9 source ranges (shared memory)
+    const uint32_t* rpre;      // prefix sums of their lengths (10 entries)
 };
 
-// Gather local-list records [cb, cb + cnt) into the warp's buffer: near band
-// at the front (returns its size via nn), far band at the back (nf).
+// Gather local-list records [cb, cb + cnt) into the warp's buffer in scaled
+// leaf-relative coordinates: near band at the front (nn records), far band
+// at the back (nf records).
 __device__ __forceinline__ void gather_bands(const float4* __restrict__ sp, const LeafCtx& c,
                                              const NearF32v3& nm, uint32_t cb, uint32_t cnt,
                                              float4* buf, uint32_t& nn, uint32_t& nf) {
@@ -293,6 +309,7 @@ __device__ __forceinline__ void gather_bands(const float4* __restrict__ sp, cons
     const unsigned lt = (1u << lane) - 1u;
     nn = 0;
     nf = 0;
+    __syncwarp();  // earlier readers of the buffer are done
     for (uint32_t vb = 0; vb < cnt; vb += 32) {
         const uint32_t v = vb + lane;
         float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -301,9 +318,11 @@ __device__ __forceinline__ void gather_bands(const float4* __restrict__ sp, cons
             uint32_t gv = cb + v;
             int r = 0;
             while (gv >= c.rpre[r + 1]) ++r;
-            rec = sp[c.rbeg[r] + (gv - c.rpre[r])];
-            float ex = fmaxf(fabsf(rec.x - c.cxh) - nm.half_leaf, 0.f);
-            float ey = fmaxf(fabsf(rec.y - c.cyh) - nm.half_leaf, 0.f);
+            float4 q = sp[c.rbeg[r] + (gv - c.rpre[r])];
+            rec = make_float4(((q.x - c.cxh) - c.cxl) * nm.sc, ((q.y - c.cyh) - c.cyl) * nm.sc,
+                              q.z, 0.f);
+            float ex = fmaxf(fabsf(rec.x) - nm.half_leaf, 0.f);
+            float ey = fmaxf(fabsf(rec.y) - nm.half_leaf, 0.f);
             near = fmaf(ex, ex, ey * ey) < nm.band2;
         }
         const unsigned bn = __ballot_sync(0xffffffffu, near);
@@ -316,11 +335,13 @@ __device__ __forceinline__ void gather_bands(const float4* __restrict__ sp, cons
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(kLeafWarps * 32)
+__global__ void __launch_bounds__(kLeafWarps * 32, 8)
 p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
                    Geometry g, NearF32v3 nm, const float* __restrict__ le,
-                   float* __restrict__ uv) {
+                   const float* __restrict__ l2l, float* __restrict__ uv) {
     __shared__ float4 lists[kLeafWarps][kListCap];
+    __shared__ uint32_t ranges[kLeafWarps][20];
+    __shared__ float2 leaf_le[kLeafWarps][kMaxP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t leaf = blockIdx.x * kLeafWarps + warp;
     const uint32_t nleaf = 1u << (2 * g.L);
@@ -331,7 +352,9 @@ p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ l
     c.t0 = leaf_start[leaf];
     c.nt = leaf_start[leaf + 1] - c.t0;
     if (c.nt == 0) return;
-    {  // lane r < 9 reads range r, then every lane learns all nine
+    uint32_t* rbeg = ranges[warp];
+    uint32_t* rpre = ranges[warp] + 9;
+    {  // lane r < 9 reads range r
         uint32_t b = 0, len = 0;
         if (lane < 9) {
             int sx = (int)lx + lane % 3 - 1, sy = (int)ly + lane / 3 - 1;
@@ -341,21 +364,43 @@ p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ l
                 len = leaf_start[k + 1] - b;
             }
         }
-        c.rpre[0] = 0;
-        for (int r = 0; r < 9; ++r) {
-            c.rbeg[r] = __shfl_sync(0xffffffffu, b, r);
-            c.rpre[r + 1] = c.rpre[r] + __shfl_sync(0xffffffffu, len, r);
+        uint32_t incl = len;  // inclusive prefix over lanes 0..8
+        for (int o = 1; o < 16; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
         }
+        if (lane < 9) {
+            rbeg[lane] = b;
+            rpre[lane + 1] = incl;
+        }
+        if (lane == 0) rpre[0] = 0;
+        __syncwarp();
     }
-    const double s = g.W / (double)nl;
-    const double ccx = g.x0 + ((double)lx + 0.5) * s, ccy = g.y0 + ((double)ly + 0.5) * s;
-    c.cxh = (float)ccx;
-    c.cyh = (float)ccy;
-    c.cxl = (float)(ccx - (double)c.cxh);
-    c.cyl = (float)(ccy - (double)c.cyh);
-    c.le_leaf = g.L >= 2 ? le + box_slot(g.level_base, g.L, lx, ly) * (2 * g.P) : nullptr;
+    c.rbeg = rbeg;
+    c.rpre = rpre;
+    leaf_centre_hilo(g.x0, g.y0, g.W, g.L, lx, ly, &c.cxh, &c.cxl, &c.cyh, &c.cyl);
+    c.le_leaf = nullptr;
+    if (g.L >= 2) {  // the leaf's LE: its M2L part plus L2L of its parent's (Sec. 3.3.3)
+        const float2* own = reinterpret_cast<const float2*>(
+            le + box_slot(g.level_base, g.L, lx, ly) * (2 * g.P));
+        float2 v = lane < g.P ? own[lane] : make_float2(0.f, 0.f);
+        if (g.L >= 3) {
+            const float2* par = reinterpret_cast<const float2*>(
+                le + box_slot(g.level_base, g.L - 1, lx >> 1, ly >> 1) * (2 * g.P));
+            const float2* t = reinterpret_cast<const float2*>(l2l) +
+                              (int64_t)(((ly & 1u) << 1) | (lx & 1u)) * g.P * g.P;
+            float2 pk_own = lane < g.P ? par[lane] : make_float2(0.f, 0.f);
+            for (int k = 0; k < g.P; ++k) {
+                float2 pk = cshfl(pk_own, k, 32);
+                if (lane < g.P) v = cfma(t[k * g.P + lane], pk, v);
+            }
+        }
+        if (lane < g.P) leaf_le[warp][lane] = v;
+        __syncwarp();
+        c.le_leaf = reinterpret_cast<const float*>(leaf_le[warp]);
+    }
     float4* buf = lists[warp];
-    const uint32_t total = c.rpre[9];
+    const uint32_t total = rpre[9];
     const bool one_chunk = total <= kListCap;
     uint32_t nn = 0, nf = 0;
     if (one_chunk) gather_bands(sp, c, nm, 0, total, buf, nn, nf);
@@ -368,13 +413,11 @@ p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ l
         const int sl = lane % ns;
         const bool active = tl < tc;
         const float4 rec = sp[c.t0 + tb + (active ? tl : 0)];
-        const float x = rec.x, y = rec.y;
+        const float x = ((rec.x - c.cxh) - c.cxl) * nm.sc, y = ((rec.y - c.cyh) - c.cyl) * nm.sc;
         float su = 0.f, sv = 0.f, cu = 0.f, cv = 0.f;
         for (uint32_t cb = 0; cb < total; cb += kListCap) {
-            if (!one_chunk) {
-                __syncwarp();
+            if (!one_chunk)
                 gather_bands(sp, c, nm, cb, min((uint32_t)kListCap, total - cb), buf, nn, nf);
-            }
             band_loop<true>(buf, 0, nn, ns, sl, nm, x, y, su, sv, cu, cv);
             band_loop<false>(buf, kListCap - nf, kListCap, ns, sl, nm, x, y, su, sv, cu, cv);
         }
@@ -387,8 +430,7 @@ p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ l
         if (active && sl == 0) {
             float u = nm.kvel * su, v = nm.kvel * sv;
             if (c.le_leaf) {  // L2P: w = (1/s) sum_n L~_n zeta^n, zeta = (z - z_leaf) / s
-                float2 zeta = make_float2(((x - c.cxh) - c.cxl) * nm.inv_s,
-                                          ((y - c.cyh) - c.cyl) * nm.inv_s);
+                float2 zeta = make_float2(x * nm.kzeta, y * nm.kzeta);
                 const float2* Lc = reinterpret_cast<const float2*>(c.le_leaf);
                 float2 w = Lc[g.p - 1];
                 for (int m = g.p - 2; m >= 0; --m) {
@@ -457,40 +499,41 @@ double fit_near_polynomial(double a, double* coef) {
 
 template <>
 cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, const void* particles,
-                                  const uint32_t* leaf_start, const float* le, float* uv,
-                                  cudaStream_t s) {
+                                  const uint32_t* leaf_start, const float* le, const float* l2l,
+                                  float* uv, cudaStream_t s) {
     const double ln2 = 0.69314718055994530942;
     const double pi = 3.14159265358979323846;
     NearF32v3 nm;
     double qthr = 1.0 / ln2;
-    nm.c2 = (float)(1.0 / (2.0 * sigma * sigma * ln2));
+    double box = g.W / ldexp(1.0, g.L);
+    nm.sc = (float)sqrt(1.0 / (2.0 * sigma * sigma * ln2));
     nm.qthr = (float)qthr;
-    nm.kvel = (float)(1.0 / (4.0 * pi * sigma * sigma * ln2));
-    nm.inv_s = (float)(ldexp(1.0, g.L) / g.W);
+    nm.kvel = (float)(1.0 / (4.0 * pi * sigma * sigma * ln2 * (double)nm.sc));
+    nm.kzeta = (float)(1.0 / ((double)nm.sc * box));
+    nm.inv_s = (float)(1.0 / box);
+    nm.half_leaf = (float)(0.5 * box * (double)nm.sc);
+    nm.band2 = (float)(qthr * 1.02);  // q < 1 needs |dX|^2 < 1/ln 2; 2% margin for rounding
     double coef[kF32Deg + 1];
     if (fit_near_polynomial(qthr, coef) > 1e-8) return cudaErrorInvalidValue;
     for (int k = 0; k <= kF32Deg; ++k) nm.coef[k] = (float)coef[k];
-    nm.half_leaf = (float)(0.5 * g.W / ldexp(1.0, g.L));
-    // q < 1 needs a physical distance below sqrt(2) sigma; 2% margin for rounding
-    nm.band2 = (float)(2.0 * sigma * sigma * 1.02);
     unsigned nleaf = 1u << (2 * g.L);
     unsigned blocks = (nleaf + kLeafWarps - 1) / kLeafWarps;
     p2p_l2p_f32_kernel<<<blocks, kLeafWarps * 32, 0, s>>>(
-        reinterpret_cast<const float4*>(particles), leaf_start, g, nm, le, uv);
+        reinterpret_cast<const float4*>(particles), leaf_start, g, nm, le, l2l, uv);
     return cudaGetLastError();
 }
 
 template <>
 cudaError_t launch_p2p_l2p<double>(const Geometry& g, double sigma, const void* particles,
-                                   const uint32_t* leaf_start, const double* le, double* uv,
-                                   cudaStream_t s) {
+                                   const uint32_t* leaf_start, const double* le,
+                                   const double* l2l, double* uv, cudaStream_t s) {
     NearF64 nm;
     nm.inv2s2 = 1.0 / (2.0 * sigma * sigma);
     nm.k0 = 1.0 / (2.0 * 3.14159265358979323846);
     unsigned nleaf = 1u << (2 * g.L);
     p2p_l2p_kernel<double, NearF64><<<nleaf, kThreads, 0, s>>>(
         reinterpret_cast<const ParticleD*>(particles), leaf_start, g, ldexp(1.0, g.L) / g.W, nm,
-        le, uv);
+        le, l2l, uv);
     return cudaGetLastError();
 }
 

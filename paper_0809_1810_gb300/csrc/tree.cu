@@ -145,8 +145,36 @@ scan_digits_kernel(uint32_t* __restrict__ hist, int nblocks, uint32_t* __restric
     if (threadIdx.x == 0) digit_total[blockIdx.x] = carry;
 }
 
-// Stable scatter of one tile.  With R != void the pass is the last one and
-// also writes the sorted particle records and the permutation.
+// Block-wide exclusive scan of one value per thread (kSortThreads threads);
+// returns the exclusive prefix, writes the block total to *total.
+__device__ inline uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tmp, uint32_t* total) {
+    constexpr int kWarps = kSortThreads / 32;
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tmp[warp] = incl;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        uint32_t ws = warp_tmp[w];
+        before += w < warp ? ws : 0u;
+        all += ws;
+    }
+    *total = all;
+    __syncthreads();  // warp_tmp may be reused
+    return before + incl - v;
+}
+
+// Stable scatter of one tile.  Keys are first ranked within the tile (each
+// warp owns a contiguous run and ranks equal digits with __match_any_sync,
+// which keeps input order), staged in shared memory in tile-sorted order,
+// then written out as contiguous per-digit runs (coalesced).  With kLast the
+// pass is the final one and also writes the permutation and the sorted
+// particle records.
 template <typename R, bool kLast>
 __global__ void __launch_bounds__(kSortThreads)
 scatter_kernel(int64_t n, const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
@@ -159,14 +187,17 @@ scatter_kernel(int64_t n, const uint32_t* __restrict__ keys_in, const uint32_t* 
     constexpr int kPerWarp = kSortTile / kWarps;  // contiguous keys per warp
     constexpr int kIters = kPerWarp / 32;
     __shared__ uint32_t wcnt[kWarps][kRadix];
-    __shared__ uint32_t dbase[kRadix];
-    __shared__ uint32_t dsum[kWarps];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ uint32_t gbase[kRadix];  // where the tile's digit-d run starts overall
+    __shared__ uint32_t tbase[kRadix];  // where it starts within the tile
+    __shared__ uint32_t tmp[kWarps];
+    __shared__ uint32_t skey[kSortTile], sval[kSortTile];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int d = lane; d < kRadix; d += 32) wcnt[warp][d] = 0;
     __syncwarp();
-    int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * kPerWarp;
+    const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    const int64_t base = tile0 + (int64_t)warp * kPerWarp;
     uint32_t key[kIters], val[kIters], rank[kIters];
-    uint32_t lt_mask = (1u << lane) - 1u;
+    const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
     for (int it = 0; it < kIters; ++it) {
         int64_t i = base + it * 32 + lane;
@@ -181,46 +212,45 @@ scatter_kernel(int64_t n, const uint32_t* __restrict__ keys_in, const uint32_t* 
         __syncwarp();
         rank[it] = before + __popc(peers & lt_mask);
     }
-    // exclusive scan of the digit totals: where each digit starts overall
+    __syncthreads();
     static_assert(kRadix == kSortThreads, "one thread per digit");
     {
-        uint32_t tot = digit_total[threadIdx.x], incl = tot;
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) dsum[warp] = incl;
-        __syncthreads();
-        uint32_t before = 0;
-        for (int w = 0; w < warp; ++w) before += dsum[w];
-        dbase[threadIdx.x] = before + incl - tot +
-                             offsets[(int64_t)threadIdx.x * nblocks + blockIdx.x];
-    }
-    // exclusive offsets of the warps within each digit
-    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
-        uint32_t run = 0;
+        const int d = threadIdx.x;
+        uint32_t cnt = 0;  // the tile's count of digit d; warps offset in warp order
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) {
             uint32_t c = wcnt[w][d];
-            wcnt[w][d] = run;
-            run += c;
+            wcnt[w][d] = cnt;
+            cnt += c;
         }
+        uint32_t all;
+        uint32_t dstart = block_exclusive_scan(digit_total[d], tmp, &all);
+        tbase[d] = block_exclusive_scan(cnt, tmp, &all);
+        gbase[d] = dstart + offsets[(int64_t)d * nblocks + blockIdx.x];
     }
     __syncthreads();
+    // stage in tile-sorted order
 #pragma unroll
     for (int it = 0; it < kIters; ++it) {
         int64_t i = base + it * 32 + lane;
         if (i < n) {
             uint32_t d = (key[it] >> shift) & (kRadix - 1);
-            uint32_t pos = dbase[d] + wcnt[warp][d] + rank[it];
-            keys_out[pos] = key[it];
-            vals_out[pos] = val[it];
-            if (kLast) {
-                uint32_t j = val[it];
-                particles[pos] = ParticleOf<R>::make(xy[2 * (int64_t)j], xy[2 * (int64_t)j + 1],
-                                                     gamma[j], j);
-            }
+            uint32_t lp = tbase[d] + wcnt[warp][d] + rank[it];
+            skey[lp] = key[it];
+            sval[lp] = val[it];
         }
+    }
+    __syncthreads();
+    const int tile_n = (int)min((int64_t)kSortTile, n - tile0);
+    for (int lp = threadIdx.x; lp < tile_n; lp += kSortThreads) {
+        uint32_t k = skey[lp], v = sval[lp];
+        uint32_t d = (k >> shift) & (kRadix - 1);
+        uint32_t pos = gbase[d] + (uint32_t)lp - tbase[d];
+        keys_out[pos] = k;
+        vals_out[pos] = v;
+        if (kLast)
+            particles[pos] = ParticleOf<R>::make(xy[2 * (int64_t)v], xy[2 * (int64_t)v + 1],
+                                                 gamma[v], v);
     }
 }
 

@@ -3,7 +3,13 @@
 //   P2M  a~_m = sum_{i in leaf} c_i zeta_i^m,  c_i = -j Gamma_i / 2pi,
 //        zeta_i = (z_i - z_leaf) / s_leaf                          (Eq. 20-21)
 //   M2M  parent b~_n = sum_quadrants sum_{k<=n} M2M[q]_{nk} a~_k(child)  (Sec. 3.3.2)
-// The leaf centre is formed once per leaf in FP64 and held as an FP32 hi/lo
+// Launches: the P2M kernel runs one CTA per parent box (four warps, one per
+// child leaf) and also forms the parent's expansion at level L-1 from the
+// four children in shared memory.  Levels L-2 .. 5 take one launch each;
+// levels 4 .. 2 (at most 336 boxes) run in one single-CTA launch with a
+// barrier between levels.  The 4-quadrant M2M table is staged in shared
+// memory by every kernel that loops over it.
+// The leaf centre is formed once per warp in FP64 and held as an FP32 hi/lo
 // pair, so that zeta = ((x - c_hi) - c_lo) / s is accurate to FP32 relative
 // to the leaf size and the expansion is centred where the translation
 // tables assume.
@@ -13,31 +19,43 @@ namespace fmm2d {
 namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int kTopLevel = 4;  // levels <= kTopLevel run in the single-CTA kernel
 
-// One warp per leaf; lanes stride over the leaf's particles, accumulate all
-// p coefficients, then reduce across the warp.
+// One warp per leaf, four sibling leaves per CTA; lanes stride over the
+// leaf's particles, accumulate all coefficients, then reduce across the warp.
 template <typename R, int PMAX>
 __global__ void __launch_bounds__(128)
 p2m_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
-           const uint32_t* __restrict__ leaf_start, Geometry g, double scale, R* __restrict__ me) {
+           const uint32_t* __restrict__ leaf_start, Geometry g, double scale,
+           const R* __restrict__ m2m, bool fuse_parent, R* __restrict__ me) {
     using C = typename Cplx<R>::T;
-    int lane = threadIdx.x & 31;
-    int64_t leaf = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nleaf = (int64_t)1 << (2 * g.L);
-    if (leaf >= nleaf) return;
-    uint32_t ix = morton_compact((uint32_t)leaf), iy = morton_compact((uint32_t)leaf >> 1);
-    uint32_t b = leaf_start[leaf], e = leaf_start[leaf + 1];
-    double cx = g.x0 + ((double)ix + 0.5) / scale, cy = g.y0 + ((double)iy + 0.5) / scale;
-    R cxh = (R)cx, cyh = (R)cy;
-    R cxl = (R)(cx - (double)cxh), cyl = (R)(cy - (double)cyh);
-    R inv_s = (R)scale;
+    __shared__ C child_me[4][PMAX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t leaf = (int64_t)blockIdx.x * 4 + warp;
+    const uint32_t ix = morton_compact((uint32_t)leaf), iy = morton_compact((uint32_t)leaf >> 1);
+    const uint32_t b = leaf_start[leaf], e = leaf_start[leaf + 1];
+    R cxh, cxl, cyh, cyl;
+    if (sizeof(R) == 4) {
+        float a0, a1, a2, a3;
+        leaf_centre_hilo(g.x0, g.y0, g.W, g.L, ix, iy, &a0, &a1, &a2, &a3);
+        cxh = a0;
+        cxl = a1;
+        cyh = a2;
+        cyl = a3;
+    } else {
+        cxh = (R)(g.x0 + ((double)ix + 0.5) / scale);
+        cyh = (R)(g.y0 + ((double)iy + 0.5) / scale);
+        cxl = cyl = R(0);
+    }
+    const R inv_s = (R)scale;
+    const R inv2pi = (R)(1.0 / kTwoPi);
     C acc[PMAX];
 #pragma unroll
     for (int m = 0; m < PMAX; ++m) acc[m] = cmake<C>(R(0), R(0));
     for (uint32_t r = b + lane; r < e; r += 32) {
         auto q = sp[r];
         C zeta = cmake<C>(((q.x - cxh) - cxl) * inv_s, ((q.y - cyh) - cyl) * inv_s);
-        C pw = cmake<C>(R(0), -q.z * (R)(1.0 / kTwoPi));  // c_i = -j Gamma / 2pi
+        C pw = cmake<C>(R(0), -q.z * inv2pi);  // c_i = -j Gamma / 2pi
 #pragma unroll
         for (int m = 0; m < PMAX; ++m) {
             if (m < g.p) {
@@ -55,83 +73,141 @@ p2m_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
             acc[m].y += __shfl_xor_sync(0xffffffffu, acc[m].y, o);
         }
     }
-    R* dst = me + box_slot(g.level_base, g.L, ix, iy) * (2 * g.P);
+    C* dst = reinterpret_cast<C*>(me + box_slot(g.level_base, g.L, ix, iy) * (2 * g.P));
 #pragma unroll
     for (int m = 0; m < PMAX; ++m) {
         if ((m & 31) == lane && m < g.P) {
-            dst[2 * m] = acc[m].x;
-            dst[2 * m + 1] = acc[m].y;
+            dst[m] = acc[m];
+            child_me[warp][m] = acc[m];
         }
+    }
+    if (!fuse_parent) return;  // uniform over the grid
+    __syncthreads();
+    if (warp == 0 && lane < g.P) {  // parent at level L-1; child quadrant q is warp q
+        const C* tab = reinterpret_cast<const C*>(m2m);
+        C out = cmake<C>(R(0), R(0));
+        for (int q = 0; q < 4; ++q) {
+            const C* tq = tab + (int64_t)q * g.P * g.P;
+#pragma unroll
+            for (int k = 0; k < PMAX; ++k)
+                if (k < g.P) out = cfma(tq[k * g.P + lane], child_me[q][k], out);
+        }
+        reinterpret_cast<C*>(me + box_slot(g.level_base, g.L - 1, ix >> 1, iy >> 1) *
+                                      (2 * g.P))[lane] = out;
     }
 }
 
-// One group of P lanes per parent box at `level`; lane n computes b~_n.
+// M2M of one box with G lanes (lane n computes b~_n); children read by lane k
+// and broadcast with shuffles, the table from shared memory.
 template <typename R, int G>
-__global__ void __launch_bounds__(128)
-m2m_kernel(Geometry g, int level, const R* __restrict__ m2m, R* __restrict__ me) {
-    using C = typename Cplx<R>::T;  // G = P lanes per box (16 or 32)
-    int lane = threadIdx.x & 31;
-    int n = lane % G;
-    int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
-    int64_t nb = (int64_t)1 << (2 * level);
-    bool valid = gid < nb;
-    int64_t slot = g.level_base[level] + (valid ? gid : 0);
+__device__ __forceinline__ void m2m_box(const Geometry& g, int level, int64_t slot, bool valid,
+                                        const typename Cplx<R>::T* tab, R* __restrict__ me) {
+    using C = typename Cplx<R>::T;
+    const int n = (threadIdx.x & 31) % G;
     uint32_t ix, iy;
     slot_box(g.level_base, level, slot, &ix, &iy);
-    const C* tab = reinterpret_cast<const C*>(m2m);
     C acc = cmake<C>(R(0), R(0));
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
         uint32_t cx = 2 * ix + (q & 1), cy = 2 * iy + (q >> 1);
         const C* child = reinterpret_cast<const C*>(me + box_slot(g.level_base, level + 1, cx, cy) *
                                                              (2 * g.P));
         C a_own = child[n];
-        const C* tq = tab + (int64_t)q * G * G;
 #pragma unroll
         for (int k = 0; k < G; ++k) {  // entries with k >= p are zero
             C ak = cshfl(a_own, k, G);
-            acc = cfma(tq[k * G + n], ak, acc);
+            acc = cfma(tab[(q * G + k) * G + n], ak, acc);
         }
     }
     if (valid) reinterpret_cast<C*>(me + slot * (2 * g.P))[n] = acc;
 }
 
+template <typename R, int G>
+__device__ __forceinline__ void stage_table(const R* __restrict__ src, typename Cplx<R>::T* dst) {
+    using C = typename Cplx<R>::T;
+    const C* s = reinterpret_cast<const C*>(src);
+    for (int i = threadIdx.x; i < 4 * G * G; i += blockDim.x) dst[i] = s[i];
+    __syncthreads();
+}
+
+// One level, G lanes per box.
+template <typename R, int G>
+__global__ void __launch_bounds__(256)
+m2m_level_kernel(Geometry g, int level, const R* __restrict__ m2m, R* __restrict__ me) {
+    using C = typename Cplx<R>::T;
+    __shared__ C tab[4 * G * G];
+    stage_table<R, G>(m2m, tab);
+    int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    int64_t nb = (int64_t)1 << (2 * level);
+    bool valid = gid < nb;
+    m2m_box<R, G>(g, level, g.level_base[level] + (valid ? gid : 0), valid, tab, me);
+}
+
+// Levels lhi .. 2 in one CTA, a barrier between levels.
+template <typename R, int G>
+__global__ void __launch_bounds__(1024)
+m2m_top_kernel(Geometry g, int lhi, const R* __restrict__ m2m, R* __restrict__ me) {
+    using C = typename Cplx<R>::T;
+    __shared__ C tab[4 * G * G];
+    stage_table<R, G>(m2m, tab);
+    for (int level = lhi; level >= 2; --level) {
+        int64_t nb = (int64_t)1 << (2 * level);
+        for (int64_t base = 0; base < nb * G; base += blockDim.x) {
+            int64_t gid = (base + threadIdx.x) / G;
+            bool valid = gid < nb;
+            m2m_box<R, G>(g, level, g.level_base[level] + (valid ? gid : 0), valid, tab, me);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 template <typename R>
-cudaError_t launch_p2m(const Geometry& g, const void* particles, const uint32_t* leaf_start, R* me,
-                       cudaStream_t s) {
+cudaError_t launch_p2m(const Geometry& g, const void* particles, const uint32_t* leaf_start,
+                       const Tables<R>& t, R* me, cudaStream_t s) {
     using P = typename ParticleOf<R>::type;
     int64_t nleaf = (int64_t)1 << (2 * g.L);
-    int blocks = (int)((nleaf * 32 + 127) / 128);
+    int blocks = (int)(nleaf / 4);
     double scale = ldexp(1.0, g.L) / g.W;
+    bool fuse = g.L >= 3;
     if (g.P <= 16)
         p2m_kernel<R, 16><<<blocks, 128, 0, s>>>(reinterpret_cast<const P*>(particles), leaf_start,
-                                                 g, scale, me);
+                                                 g, scale, t.m2m, fuse, me);
     else
         p2m_kernel<R, 32><<<blocks, 128, 0, s>>>(reinterpret_cast<const P*>(particles), leaf_start,
-                                                 g, scale, me);
+                                                 g, scale, t.m2m, fuse, me);
     return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_m2m(const Geometry& g, int level, const Tables<R>& t, R* me, cudaStream_t s) {
-    int64_t nb = (int64_t)1 << (2 * level);
-    int64_t threads = nb * g.P;
-    int blocks = (int)((threads + 127) / 128);
-    if (g.P <= 16)
-        m2m_kernel<R, 16><<<blocks, 128, 0, s>>>(g, level, t.m2m, me);
-    else
-        m2m_kernel<R, 32><<<blocks, 128, 0, s>>>(g, level, t.m2m, me);
+cudaError_t launch_m2m(const Geometry& g, const Tables<R>& t, R* me, cudaStream_t s) {
+    // level L-1 was formed by the P2M kernel
+    for (int level = g.L - 2; level > kTopLevel; --level) {
+        int64_t threads = ((int64_t)1 << (2 * level)) * g.P;
+        int blocks = (int)((threads + 255) / 256);
+        if (g.P <= 16)
+            m2m_level_kernel<R, 16><<<blocks, 256, 0, s>>>(g, level, t.m2m, me);
+        else
+            m2m_level_kernel<R, 32><<<blocks, 256, 0, s>>>(g, level, t.m2m, me);
+    }
+    int lhi = g.L - 2 < kTopLevel ? g.L - 2 : kTopLevel;
+    if (lhi >= 2) {
+        if (g.P <= 16)
+            m2m_top_kernel<R, 16><<<1, 1024, 0, s>>>(g, lhi, t.m2m, me);
+        else
+            m2m_top_kernel<R, 32><<<1, 1024, 0, s>>>(g, lhi, t.m2m, me);
+    }
     return cudaGetLastError();
 }
 
-template cudaError_t launch_p2m<float>(const Geometry&, const void*, const uint32_t*, float*,
+template cudaError_t launch_p2m<float>(const Geometry&, const void*, const uint32_t*,
+                                       const Tables<float>&, float*, cudaStream_t);
+template cudaError_t launch_p2m<double>(const Geometry&, const void*, const uint32_t*,
+                                        const Tables<double>&, double*, cudaStream_t);
+template cudaError_t launch_m2m<float>(const Geometry&, const Tables<float>&, float*,
                                        cudaStream_t);
-template cudaError_t launch_p2m<double>(const Geometry&, const void*, const uint32_t*, double*,
-                                        cudaStream_t);
-template cudaError_t launch_m2m<float>(const Geometry&, int, const Tables<float>&, float*,
-                                       cudaStream_t);
-template cudaError_t launch_m2m<double>(const Geometry&, int, const Tables<double>&, double*,
+template cudaError_t launch_m2m<double>(const Geometry&, const Tables<double>&, double*,
                                         cudaStream_t);
 
 }  // namespace fmm2d
