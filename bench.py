@@ -2,7 +2,8 @@
 
 Workload (one "step" = one full FMM evaluation, tree build to velocities):
 uniform positions in [-1, 1]^2, circulations h^2 N(0,1) with h = 2/1024,
-sigma = 2h, p = 16, L = 7, float32 inputs and arithmetic (the FP32 form).
+sigma = 2h, p = 16, L = 7, float32 inputs and arithmetic, M2L as a 3xTF32
+tensor-core contraction (the FP32_TC form; --precision selects another).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -372,7 +373,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_tc", "fp64"])
+    ap.add_argument("--precision", default="fp32_tc", choices=["fp32", "fp32_tc", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -79,6 +79,15 @@ struct fmm2d_plan {
     cudaGraphNode_t ev_node[kPhases + 1]{};
     bool graph_timed = false;
     int kernel_nodes = -1;
+    // tensor-core M2L (FMM2D_FP32_TC)
+    void* tc_ws = nullptr;
+    float* me_hi = nullptr;
+    float* me_lo = nullptr;
+    float* bt_hi = nullptr;
+    float* bt_lo = nullptr;
+    int4* tiles = nullptr;
+    int ntiles = 0;
+    M2LTcMaps* maps = nullptr;
 };
 
 namespace {
@@ -120,7 +129,15 @@ cudaError_t enqueue(fmm2d_plan* pl, int64_t n, const R* xy, const R* gamma, R* u
     STEP(mark(pl, 2, s));
     if (g.L >= 4) STEP(launch_m2m<R>(g, t, me, s));
     STEP(mark(pl, 3, s));
-    if (g.L >= 2) STEP(launch_m2l<R>(g, t, me, le, s));
+    if (g.L >= 2) {
+        if (pl->prm.precision == FMM2D_FP32_TC) {
+            STEP(launch_m2l_tc(g, *pl->maps, pl->tiles, pl->ntiles,
+                               reinterpret_cast<const float*>(me), pl->me_hi, pl->me_lo,
+                               reinterpret_cast<float*>(le), pl->d_status, s));
+        } else {
+            STEP(launch_m2l<R>(g, t, me, le, s));
+        }
+    }
     STEP(mark(pl, 4, s));
     if (g.L >= 4) STEP(launch_l2l<R>(g, t, le, s));
     STEP(mark(pl, 5, s));
@@ -257,8 +274,6 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
     *out = nullptr;
     std::string why;
     if (!valid_params(prm, &why)) return fail(FMM2D_INVALID_ARG, why);
-    if (prm->precision == FMM2D_FP32_TC)
-        return fail(FMM2D_UNSUPPORTED, "FP32_TC precision is not available in this build");
     auto* pl = new fmm2d_plan();
     pl->prm = *prm;
     pl->elem = prm->precision == FMM2D_FP64 ? 8 : 4;
@@ -345,6 +360,54 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
         e = cudaEventCreate(&pl->ev_mark[k]);
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaEventCreate"));
     }
+    if (prm->precision == FMM2D_FP32_TC && g.L >= 2) {
+        static bool configured = false;
+        if (!configured) {
+            e = m2l_tc_configure();
+            if (e != cudaSuccess) return cleanup(cuda_fail(e, "tensor-core M2L configuration"));
+            configured = true;
+        }
+        int ntiles = 0;
+        size_t me_floats = (size_t)g.nboxes * 2 * g.P;
+        size_t bt_floats = (size_t)kOffsetSlots * 4 * g.P * g.P;
+        // tile count first (no device work), then one allocation for everything
+        {
+            int cnt = 0;
+            for (int l = 2; l <= g.L; ++l) {
+                int Wh = 1 << (l - 1), bw = Wh < 128 ? Wh : 128;
+                int bh = (128 / bw) < Wh ? 128 / bw : Wh;
+                cnt += 4 * ((Wh + bh - 1) / bh) * ((Wh + bw - 1) / bw);
+            }
+            ntiles = cnt;
+        }
+        size_t bytes = align256(me_floats * 4) * 2 + align256(bt_floats * 4) * 2 +
+                       align256((size_t)ntiles * sizeof(int4));
+        e = cudaMalloc(&pl->tc_ws, bytes);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "tensor-core workspace cudaMalloc"));
+        char* q = static_cast<char*>(pl->tc_ws);
+        pl->me_hi = (float*)q;
+        q += align256(me_floats * 4);
+        pl->me_lo = (float*)q;
+        q += align256(me_floats * 4);
+        pl->bt_hi = (float*)q;
+        q += align256(bt_floats * 4);
+        pl->bt_lo = (float*)q;
+        q += align256(bt_floats * 4);
+        pl->tiles = (int4*)q;
+        pl->maps = new M2LTcMaps();
+        std::vector<int4> tiles(ntiles);
+        int count = 0;
+        int64_t per = (int64_t)g.P * g.P * 2;
+        e = m2l_tc_prepare(g, pl->tab64 + 8 * per, pl->me_hi, pl->me_lo, pl->bt_hi, pl->bt_lo,
+                           pl->maps, tiles.data(), &count, pl->cap);
+        if (e == cudaSuccess && count != ntiles) e = cudaErrorInvalidValue;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(pl->tiles, tiles.data(), (size_t)ntiles * sizeof(int4),
+                                cudaMemcpyHostToDevice, pl->cap);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(pl->cap);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "tensor-core M2L set-up"));
+        pl->ntiles = ntiles;
+    }
     *out = pl;
     return FMM2D_OK;
 }
@@ -362,6 +425,8 @@ void fmm2d_plan_destroy(fmm2d_plan* pl) {
     if (pl->cap) cudaStreamDestroy(pl->cap);
     if (pl->h_status) cudaFreeHost(pl->h_status);
     if (pl->st_xy) cudaFree(pl->st_xy);
+    if (pl->tc_ws) cudaFree(pl->tc_ws);
+    delete pl->maps;
     if (pl->ws) cudaFree(pl->ws);
     cudaSetDevice(cur);
     delete pl;

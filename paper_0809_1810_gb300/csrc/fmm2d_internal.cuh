@@ -2,6 +2,7 @@
 // Not part of the ABI: everything callers see is in include/fmm2d.h.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -135,6 +136,23 @@ template <typename R>
 cudaError_t launch_p2p_l2p(const Geometry& g, double sigma, const void* particles,
                            const uint32_t* leaf_start, const R* le, const R* l2l, R* uv,
                            cudaStream_t s);
+
+// Tensor maps of the tensor-core M2L: multipole hi/lo parts per level (4D:
+// 2P reals x row x column x parity plane) and the real-ified offset matrices
+// (3D: k' x n' x offset slot).
+struct M2LTcMaps {
+    CUtensorMap me_hi[kMaxL + 1];
+    CUtensorMap me_lo[kMaxL + 1];
+    CUtensorMap b_hi, b_lo;
+};
+int m2l_tc_smem_bytes(int P);
+cudaError_t m2l_tc_configure();
+cudaError_t m2l_tc_prepare(const Geometry& g, const double* m2l64, float* me_hi, float* me_lo,
+                           float* bhi, float* blo, M2LTcMaps* maps, int4* tiles_host, int* ntiles,
+                           cudaStream_t s);
+cudaError_t launch_m2l_tc(const Geometry& g, const M2LTcMaps& maps, const int4* tiles, int ntiles,
+                          const float* me, float* me_hi, float* me_lo, float* le, int* status,
+                          cudaStream_t s);
 
 template <typename R>
 cudaError_t launch_direct_sampled(const Geometry& g, double sigma, int kernel, int64_t n,

@@ -118,23 +118,25 @@ def test_fp64_fmm_matches_oracle(name, make):
     assert _rel(uv, ref) <= FP64_TOL, _rel(uv, ref)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp32_tc"])
 @pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
-def test_fp32_fmm_matches_oracle(name, make):
+def test_fp32_fmm_matches_oracle(name, make, prec):
     w = make(np.float32)
     ref = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.p, w.L, w.root)
     xy, g = _dev(w, torch.float32)
-    with _plan(w, "fp32") as plan:
+    with _plan(w, prec) as plan:
         uv = plan.velocity(xy, g, check=True).double().cpu().numpy()
     assert _rel(uv, ref) <= FP32_TOL, _rel(uv, ref)
 
 
-def test_uniform_1m_full_size():
+@pytest.mark.parametrize("prec", ["fp32", "fp32_tc"])
+def test_uniform_1m_full_size(prec):
     """The 2^20-particle uniform workload (p = 16, L = 7, sigma = 2h) in the
-    FP32 form timed by the benchmark: every output against the FP64 oracle
+    FP32 forms timed by the benchmark: every output against the FP64 oracle
     FMM, and the FP64 direct yardsticks against the oracle at sampled targets."""
     w = W.uniform_1m()
     xy, g = _dev(w, torch.float32)
-    with _plan(w, "fp32") as plan:
+    with _plan(w, prec) as plan:
         uv = plan.velocity(xy, g, check=True).double().cpu().numpy()
         t = W.sample_targets(w.n, 256, 11)
         tt = torch.tensor(t, device="cuda")
