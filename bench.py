@@ -205,6 +205,42 @@ def run_reference(args):
     }))
 
 
+def run_batch_sweep(torch, dev, flush, rank, pg, steps=10):
+    """The 512-instance sweep (N log-uniform in [2^12, 2^17], p in {4..24},
+    L in {3..7}, sigma/h in {0.8, 1, 1.5, 2}, half Lamb-Oseen lattices) as one
+    batched graph launch, after the autotuner has chosen launch shapes."""
+    from paper_0809_1810_gb300 import BatchPlan
+
+    specs = W.batch_instances(512, seed=3 + rank)
+    ws = [W.make_instance(s) for s in specs]
+    xy = torch.tensor(np.concatenate([np.stack([w.x, w.y], 1) for w in ws]), device=dev)
+    g = torch.tensor(np.concatenate([w.gamma for w in ws]), device=dev)
+    with BatchPlan([{"n": w.n, "p": w.p, "L": w.L, "sigma": w.sigma} for w in ws]) as bp:
+        uv = torch.empty((bp.n_total, 2), dtype=torch.float32, device=dev)
+        tuned = bp.autotune(xy, g, uv)
+        for _ in range(3):
+            bp.velocity(xy, g, out=uv)
+        bp.check()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record()
+            bp.velocity(xy, g, out=uv)
+            b.record()
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        ms = max_over_ranks(pg, ms, torch, dev)
+        info = bp.info()
+    n = int(sum(w.n for w in ws))
+    return {"instances": len(ws), "particles": n, "value": n / (ms * 1e-3),
+            "unit": "particles/s", "ms_per_batch": ms, "steps": steps,
+            "kernels_per_call": info["kernels_per_call"],
+            "autotuned": {"p2p_ctas_per_sm": tuned["p2p_ctas_per_sm"],
+                          "m2l_threads": tuned["m2l_threads"]},
+            "precision": "fp32 (M2L on CUDA cores)"}
+
+
 def run_ours(args):
     import torch
 
@@ -342,6 +378,8 @@ def run_ours(args):
                   "speedup_of_value": (n / (ms_per_step * 1e-3)) / (n / (fp64_ms * 1e-3))}
     plan64.close()
 
+    batch = None if args.no_batch else run_batch_sweep(torch, dev, flush, rank, pg)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, runs, cores = cpu_oracle_rate(w)
@@ -359,7 +397,8 @@ def run_ours(args):
                        "l2": "flushed between timed steps (512 MiB write outside the events)",
                        "parallelism": f"replicas x{world}"},
             "accuracy": accuracy, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "plain_fp64": plain_fp64, "gpu_launches": int(launches_per_step * args.steps),
+            "plain_fp64": plain_fp64, "batch_sweep": batch,
+            "gpu_launches": int(launches_per_step * args.steps),
             "launches_per_step": launches_per_step, "clocks": clk,
         }))
     plan.close()
@@ -375,6 +414,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", default="fp32_tc", choices=["fp32", "fp32_tc", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep line item")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

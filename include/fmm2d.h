@@ -174,6 +174,82 @@ fmm2d_status fmm2d_plan_set_timing(fmm2d_plan* plan, int ring);
  * the ring. */
 fmm2d_status fmm2d_plan_phase_ms(fmm2d_plan* plan, int age, double* ms_host);
 
+/* ------------------------------------------------------------------------
+ * Batched evaluation: many independent problems of uneven size, expansion
+ * order and depth, like the parameter sweeps of Sec. 5, in one packed
+ * evaluation.  FP32 form (float inputs and arithmetic, M2L on CUDA cores).
+ * Instance i owns particles [offset_i, offset_i + n_i) of the packed arrays,
+ * offset_i = n_0 + ... + n_{i-1}; its velocities are exactly those of a
+ * single-instance FMM2D_FP32 plan with the same parameters.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n;        /* particles of this instance (>= 0) */
+    int p;            /* expansion terms, 1..32 */
+    int L;            /* quadtree depth, 0..12 */
+    double sigma;     /* core size, > 0 */
+    double x0, y0, W; /* root box, W > 0 */
+} fmm2d_instance;
+
+typedef struct fmm2d_batch_plan fmm2d_batch_plan;
+
+/* Detail of the last batch-call error on the calling host thread. */
+const char* fmm2d_batch_last_error(void);
+
+/* Create a batch plan for `count` instances (copied): validates them, packs
+ * them (sum of n and sum of 4^L below 2^32), allocates the workspace on the
+ * current device and builds the translation tables.  Synchronous. */
+fmm2d_status fmm2d_batch_plan_create(fmm2d_batch_plan** out, int count,
+                                     const fmm2d_instance* instances);
+void fmm2d_batch_plan_destroy(fmm2d_batch_plan* plan);
+
+/* Velocities of every instance (packed xy: 2 sum(n) floats, gamma: sum(n),
+ * uv: 2 sum(n) floats, device).  The whole batch -- tree build, the upward
+ * and downward sweeps of every instance, and the near field as one
+ * persistent launch -- is recorded once per (buffers) into a CUDA graph and
+ * replayed.  Asynchronous on `stream`; input errors via fmm2d_batch_check. */
+fmm2d_status fmm2d_batch_velocity(fmm2d_batch_plan* plan, const float* xy_dev,
+                                  const float* gamma_dev, float* uv_dev, cudaStream_t stream);
+
+/* Wait for `stream`; report and clear device-recorded input errors. */
+fmm2d_status fmm2d_batch_check(fmm2d_batch_plan* plan, cudaStream_t stream);
+
+/* Autotuner: times candidate launch shapes of the two heaviest steps on the
+ * given batch (persistent near-field CTAs per SM in {2..5}; M2L block size in
+ * {64, 128, 256}), keeps the fastest and leaves uv_dev holding the
+ * velocities.  Synchronous; later fmm2d_batch_velocity calls use the
+ * choices. */
+fmm2d_status fmm2d_batch_autotune(fmm2d_batch_plan* plan, const float* xy_dev,
+                                  const float* gamma_dev, float* uv_dev, cudaStream_t stream);
+
+/* FP64 direct sums at s sampled particles (global packed indices), each
+ * over its own instance only; kernel 0/1 as in fmm2d_direct_sampled. */
+fmm2d_status fmm2d_batch_direct_sampled(fmm2d_batch_plan* plan, int kernel, const float* xy_dev,
+                                        const float* gamma_dev, int64_t s,
+                                        const int64_t* target_idx_dev, double* uv_ref_dev,
+                                        cudaStream_t stream);
+
+/* Error statistics per instance (4 doubles each, as in fmm2d_error_stats)
+ * and, when leaf_err_dev is not NULL, the max |du| of sampled particles per
+ * leaf in the global leaf order (instance i's leaves follow instance i-1's,
+ * 4^L_i of them, in Morton order). */
+fmm2d_status fmm2d_batch_error_stats(fmm2d_batch_plan* plan, const float* xy_dev,
+                                     const float* uv_dev, int64_t s,
+                                     const int64_t* target_idx_dev, const double* uv_ref_dev,
+                                     double* stats_dev, double* leaf_err_dev, cudaStream_t stream);
+
+/* Sizes and chosen launch shapes (each output may be NULL): total particles,
+ * total leaves, kernel launches per fmm2d_batch_velocity call (after the
+ * first), persistent near-field CTAs per SM, M2L block size. */
+fmm2d_status fmm2d_batch_info(const fmm2d_batch_plan* plan, int64_t* n_total,
+                              int64_t* leaves_total, int* kernels_per_call, int* p2p_ctas_per_sm,
+                              int* m2l_threads);
+
+/* Quadtree of the last batch evaluation in the global leaf order (keys are
+ * leaf_base_i + Morton key): as fmm2d_tree_debug, leaf_start has
+ * sum(4^L) + 1 entries. */
+fmm2d_status fmm2d_batch_tree_debug(fmm2d_batch_plan* plan, uint32_t* keys_dev, uint32_t* perm_dev,
+                                    uint32_t* leaf_start_dev, cudaStream_t stream);
+
 /* Quadtree build that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory -- for
  * example a host framework whose memory manager owns the whole device budget

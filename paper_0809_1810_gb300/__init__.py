@@ -18,7 +18,7 @@ import torch
 from . import _native
 from ._native import FP32, FP32_TC, FP64, NUM_PHASES, PHASES
 
-__all__ = ["Plan", "FMMError", "FP64", "FP32", "FP32_TC", "PHASES", "library"]
+__all__ = ["Plan", "BatchPlan", "FMMError", "FP64", "FP32", "FP32_TC", "PHASES", "library"]
 
 _PREC = {"fp64": FP64, "fp32": FP32, "fp32_tc": FP32_TC}
 
@@ -27,7 +27,8 @@ class FMMError(RuntimeError):
     def __init__(self, status: int, where: str):
         lib = _native.load()
         name = lib.fmm2d_status_string(status).decode()
-        detail = lib.fmm2d_last_error().decode()
+        getter = lib.fmm2d_batch_last_error if where.startswith("batch") else lib.fmm2d_last_error
+        detail = getter().decode()
         super().__init__(f"{where}: {name} ({detail})" if detail else f"{where}: {name}")
         self.status = status
 
@@ -176,3 +177,101 @@ class Plan:
         buf = (ctypes.c_double * NUM_PHASES)()
         _check(self._lib.fmm2d_plan_phase_ms(self._h, int(age), buf), "phase_ms")
         return dict(zip(PHASES, list(buf)))
+
+
+class BatchPlan:
+    """Many independent instances evaluated together (fmm2d_batch_*): FP32,
+    one CUDA graph per call.  ``instances`` is a list of dicts with keys n, p,
+    L, sigma and optionally root=(x0, y0, W)."""
+
+    def __init__(self, instances):
+        self._lib = _native.load()
+        arr = (_native.Instance * len(instances))()
+        for k, d in enumerate(instances):
+            root = d.get("root", (-1.0, -1.0, 2.0))
+            arr[k] = _native.Instance(int(d["n"]), int(d["p"]), int(d["L"]), float(d["sigma"]),
+                                      float(root[0]), float(root[1]), float(root[2]))
+        self.instances = [dict(d) for d in instances]
+        self.offsets = [0]
+        for d in instances:
+            self.offsets.append(self.offsets[-1] + int(d["n"]))
+        h = ctypes.c_void_p()
+        _check(self._lib.fmm2d_batch_plan_create(ctypes.byref(h), len(instances), arr),
+               "batch_plan_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.fmm2d_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def n_total(self) -> int:
+        return self.offsets[-1]
+
+    def velocity(self, xy, gamma, out=None, stream=None):
+        if xy.dtype != torch.float32 or gamma.dtype != torch.float32 or not xy.is_cuda:
+            raise TypeError("float32 CUDA tensors")
+        if gamma.shape[0] != self.n_total:
+            raise ValueError("packed arrays must hold every instance")
+        if out is None:
+            out = torch.empty((self.n_total, 2), dtype=torch.float32, device=xy.device)
+        _check(self._lib.fmm2d_batch_velocity(self._h, _ptr(xy.contiguous()),
+                                              _ptr(gamma.contiguous()), _ptr(out),
+                                              _stream(stream)), "batch_velocity")
+        return out
+
+    def check(self, stream=None):
+        _check(self._lib.fmm2d_batch_check(self._h, _stream(stream)), "batch_check")
+
+    def autotune(self, xy, gamma, out, stream=None):
+        _check(self._lib.fmm2d_batch_autotune(self._h, _ptr(xy), _ptr(gamma), _ptr(out),
+                                              _stream(stream)), "batch_autotune")
+        return self.info()
+
+    def info(self):
+        n = ctypes.c_int64()
+        leaves = ctypes.c_int64()
+        k = ctypes.c_int()
+        cps = ctypes.c_int()
+        th = ctypes.c_int()
+        _check(self._lib.fmm2d_batch_info(self._h, ctypes.byref(n), ctypes.byref(leaves),
+                                          ctypes.byref(k), ctypes.byref(cps), ctypes.byref(th)),
+               "batch_info")
+        return {"n_total": n.value, "leaves_total": leaves.value, "kernels_per_call": k.value,
+                "p2p_ctas_per_sm": cps.value, "m2l_threads": th.value}
+
+    def direct_sampled(self, xy, gamma, targets, kernel=0, stream=None):
+        targets = targets.to(device=xy.device, dtype=torch.int64).contiguous()
+        out = torch.empty((targets.shape[0], 2), dtype=torch.float64, device=xy.device)
+        _check(self._lib.fmm2d_batch_direct_sampled(self._h, int(kernel), _ptr(xy), _ptr(gamma),
+                                                    targets.shape[0], _ptr(targets), _ptr(out),
+                                                    _stream(stream)), "batch_direct_sampled")
+        return out
+
+    def error_stats(self, xy, uv, targets, uv_ref, per_leaf=False, stream=None):
+        """(count, 4) float64: max|du|, max|u_ref|, sum|du|^2, sum|u_ref|^2 per
+        instance; plus per-leaf max |du| (global leaf order) when asked."""
+        targets = targets.to(device=uv.device, dtype=torch.int64).contiguous()
+        stats = torch.empty((len(self.instances), 4), dtype=torch.float64, device=uv.device)
+        leaf = None
+        if per_leaf:
+            nleaf = sum(1 << (2 * int(d["L"])) for d in self.instances)
+            leaf = torch.empty(nleaf, dtype=torch.float64, device=uv.device)
+        _check(self._lib.fmm2d_batch_error_stats(self._h, _ptr(xy), _ptr(uv), targets.shape[0],
+                                                 _ptr(targets), _ptr(uv_ref.contiguous()),
+                                                 _ptr(stats), _ptr(leaf), _stream(stream)),
+               "batch_error_stats")
+        return (stats, leaf) if per_leaf else stats

@@ -291,6 +291,7 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
         if (l <= g.L) acc += (int64_t)1 << (2 * l);
     }
     g.nboxes = acc;
+    g.scale = ldexp(1.0, g.L) / g.W;
 
     auto cleanup = [&](fmm2d_status s) {
         fmm2d_plan_destroy(pl);

@@ -150,7 +150,126 @@ __global__ void error_kernel(int64_t n, const R* __restrict__ xy, const R* __res
     }
 }
 
+__device__ inline int find_instance(const int64_t* __restrict__ offsets, int count, int64_t i) {
+    int lo = 0, hi = count;  // offsets[lo] <= i < offsets[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (offsets[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Batched direct sums: one warp per sampled target, over its own instance.
+__global__ void __launch_bounds__(256)
+batch_direct_kernel(const BatchInst* __restrict__ inst, const int64_t* __restrict__ offsets,
+                    int count, int kernel, const float* __restrict__ xy,
+                    const float* __restrict__ gamma, int64_t s_count,
+                    const int64_t* __restrict__ targets, double* __restrict__ uv_ref,
+                    int* status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (t >= s_count) return;
+    const int64_t i = targets[t];
+    if (i < 0 || i >= offsets[count]) {
+        if (lane == 0) atomicOr(status, kFlagInvalid);
+        return;
+    }
+    const BatchInst& b = inst[find_instance(offsets, count, i)];
+    const double top = ldexp(1.0, b.g.L) - 1.0;
+    const double xi = (double)xy[2 * i], yi = (double)xy[2 * i + 1];
+    const int li = leaf_index(xi, b.g.x0, b.g.scale, top), mi = leaf_index(yi, b.g.y0, b.g.scale, top);
+    const double inv2s2 = 1.0 / (2.0 * b.sigma * b.sigma);
+    double au = 0.0, av = 0.0;
+    for (int64_t j = b.offset + lane; j < b.offset + b.n; j += 32) {
+        if (j == i) continue;
+        const double x = (double)xy[2 * j], y = (double)xy[2 * j + 1];
+        const double dx = xi - x, dy = yi - y, r2 = dx * dx + dy * dy;
+        if (r2 == 0.0) continue;  // K_sigma(0) = 0 by its limit
+        bool near = kernel == 0;
+        if (!near) {
+            const int lj = leaf_index(x, b.g.x0, b.g.scale, top);
+            const int mj = leaf_index(y, b.g.y0, b.g.scale, top);
+            near = abs(lj - li) <= 1 && abs(mj - mi) <= 1;
+        }
+        const double f = near ? -expm1(-r2 * inv2s2) / r2 : 1.0 / r2;
+        const double w = (double)gamma[j] * f;
+        au = fma(-dy, w, au);
+        av = fma(dx, w, av);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        au += __shfl_xor_sync(0xffffffffu, au, o);
+        av += __shfl_xor_sync(0xffffffffu, av, o);
+    }
+    if (lane == 0) {
+        const double inv2pi = 1.0 / 6.283185307179586476925286766559;
+        uv_ref[2 * t] = au * inv2pi;
+        uv_ref[2 * t + 1] = av * inv2pi;
+    }
+}
+
+// Batched error statistics: 4 doubles per instance (max |du|, max |u_ref|,
+// sum |du|^2, sum |u_ref|^2) and the max |du| per global leaf.
+__global__ void batch_error_kernel(const BatchInst* __restrict__ inst,
+                                   const int64_t* __restrict__ offsets, int count,
+                                   const float* __restrict__ xy, const float* __restrict__ uv,
+                                   int64_t s_count, const int64_t* __restrict__ targets,
+                                   const double* __restrict__ uv_ref, double* stats,
+                                   double* leaf_err, int* status) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < s_count;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = targets[t];
+        if (i < 0 || i >= offsets[count]) {
+            atomicOr(status, kFlagInvalid);
+            continue;
+        }
+        const int k = find_instance(offsets, count, i);
+        const BatchInst& b = inst[k];
+        double ru = uv_ref[2 * t], rv = uv_ref[2 * t + 1];
+        double du = (double)uv[2 * i] - ru, dv = (double)uv[2 * i + 1] - rv;
+        double e = sqrt(du * du + dv * dv), r = sqrt(ru * ru + rv * rv);
+        if (!(e == e)) e = __longlong_as_double(0x7ff0000000000000LL);
+        atomic_max_nonneg(&stats[4 * k], e);
+        atomic_max_nonneg(&stats[4 * k + 1], r);
+        atomicAdd(&stats[4 * k + 2], e * e);
+        atomicAdd(&stats[4 * k + 3], r * r);
+        if (leaf_err) {
+            const double top = ldexp(1.0, b.g.L) - 1.0;
+            uint32_t lx = (uint32_t)leaf_index((double)xy[2 * i], b.g.x0, b.g.scale, top);
+            uint32_t ly = (uint32_t)leaf_index((double)xy[2 * i + 1], b.g.y0, b.g.scale, top);
+            atomic_max_nonneg(&leaf_err[b.leaf_base + morton_key(lx, ly)], e);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_batch_direct(const BatchInst* inst, const int64_t* dev_offsets, int count,
+                                int kernel, const float* xy, const float* gamma, int64_t s_count,
+                                const int64_t* targets, double* uv_ref, int* status,
+                                cudaStream_t s) {
+    if (s_count == 0) return cudaSuccess;
+    int64_t blocks = (s_count * 32 + 255) / 256;
+    batch_direct_kernel<<<(unsigned)blocks, 256, 0, s>>>(inst, dev_offsets, count, kernel, xy,
+                                                         gamma, s_count, targets, uv_ref, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_error(const BatchInst* inst, const int64_t* dev_offsets, int count,
+                               const float* xy, const float* uv, int64_t s_count,
+                               const int64_t* targets, const double* uv_ref, double* stats,
+                               double* leaf_err, uint32_t nleaf_total, int* status,
+                               cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(stats, 0, 4 * sizeof(double) * count, s);
+    if (e == cudaSuccess && leaf_err)
+        e = cudaMemsetAsync(leaf_err, 0, sizeof(double) * nleaf_total, s);
+    if (e != cudaSuccess || s_count == 0) return e;
+    int64_t blocks = (s_count + 255) / 256;
+    if (blocks > 2048) blocks = 2048;
+    batch_error_kernel<<<(unsigned)blocks, 256, 0, s>>>(inst, dev_offsets, count, xy, uv, s_count,
+                                                        targets, uv_ref, stats, leaf_err, status);
+    return cudaGetLastError();
+}
 
 template <typename R>
 cudaError_t launch_direct_sampled(const Geometry& g, double sigma, int kernel, int64_t n,

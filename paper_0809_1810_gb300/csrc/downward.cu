@@ -30,6 +30,7 @@ __device__ __forceinline__ void l2l_box(const Geometry& g, int level, int64_t sl
         C lk = cshfl(l_own, k, G);
         acc = cfma(tab[(q * G + k) * G + n], lk, acc);
     }
+    if (n >= g.p) acc = cmake<C>(R(0), R(0));  // coefficients >= p stay zero
     if (valid) {
         C* dst = reinterpret_cast<C*>(le + slot * (2 * g.P));
         C v = dst[n];
@@ -77,7 +78,37 @@ l2l_top_kernel(Geometry g, int lhi, const R* __restrict__ l2l, R* __restrict__ l
     }
 }
 
+// Batched L2L at one level: G lanes per box, boxes of the listed instances.
+template <int G>
+__global__ void __launch_bounds__(256)
+l2l_batch_kernel(const BatchInst* __restrict__ inst, const int32_t* __restrict__ list, int count,
+                 int level, const float* __restrict__ l2l, float* __restrict__ le) {
+    __shared__ float2 tab[4 * G * G];
+    stage_l2l_table<float, G>(l2l, tab);
+    const int64_t per = (int64_t)1 << (2 * level);
+    const int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    const bool valid = gid < per * count;
+    const int64_t g0 = valid ? gid : 0;
+    const BatchInst& b = inst[list[g0 / per]];
+    l2l_box<float, G>(b.g, level, b.g.level_base[level] + g0 % per, valid, tab, le + b.exp_off);
+}
+
 }  // namespace
+
+cudaError_t launch_batch_l2l(const BatchInst* inst, const BatchLists& bl, int P, int level,
+                             const float* l2l, float* le, cudaStream_t s) {
+    const int count = bl.l2l_count[level];
+    if (count == 0) return cudaSuccess;
+    const int64_t threads = ((int64_t)1 << (2 * level)) * count * P;
+    const int blocks = (int)((threads + 255) / 256);
+    if (P <= 16)
+        l2l_batch_kernel<16><<<blocks, 256, 0, s>>>(inst, bl.l2l_inst[level], count, level, l2l,
+                                                   le);
+    else
+        l2l_batch_kernel<32><<<blocks, 256, 0, s>>>(inst, bl.l2l_inst[level], count, level, l2l,
+                                                   le);
+    return cudaGetLastError();
+}
 
 template <typename R>
 cudaError_t launch_l2l(const Geometry& g, const Tables<R>& t, R* le, cudaStream_t s) {

@@ -60,6 +60,7 @@ struct Geometry {
     int P;             // padded terms per box in expansion arrays (16 or 32)
     int64_t level_base[kMaxL + 2];  // first box slot of level l (l >= 2)
     int64_t nboxes;    // box slots over levels 2..L
+    double scale;      // 2^L / W, inverse leaf width (formed on the host)
 };
 
 // Expansion-array slot of box (ix, iy) at level l >= 2.  Each level is
@@ -136,6 +137,72 @@ template <typename R>
 cudaError_t launch_p2p_l2p(const Geometry& g, double sigma, const void* particles,
                            const uint32_t* leaf_start, const R* le, const R* l2l, R* uv,
                            cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Batched evaluation: many instances in one packed problem.  Instance i owns
+// particles [offset, offset + n) of the packed arrays, leaves
+// [leaf_base, leaf_base + 4^L) of one global leaf index space (its keys are
+// leaf_base + Morton key, so one stable sort groups every instance), and the
+// expansion block starting at element exp_off of the ME and LE arrays.
+// ---------------------------------------------------------------------------
+struct BatchInst {
+    Geometry g;          // the instance's geometry; level_base relative to exp_off
+    int64_t offset;      // first particle in the packed arrays
+    int64_t n;           // particle count
+    int64_t exp_off;     // first element of its expansion block
+    uint32_t leaf_base;  // global index of its leaf 0
+    double sigma;        // core size
+};
+
+// Per-class work lists built on the host (class = expansion stride P, 16 or
+// 32): the instances that take part in a step, and flattened index spaces.
+struct BatchLists {
+    const int32_t* quad_inst;    // P2M: instance of every parent box (level L-1) of the class
+    const uint32_t* quad_local;  // its local index (Morton key at level L-1)
+    int64_t nquads;
+    const int32_t* m2l_inst;     // M2L: instances of the class ...
+    const int64_t* m2l_prefix;   // ... and the prefix of their box counts (levels 2..L)
+    int m2l_count;
+    int64_t m2l_total;
+    const int32_t* m2m_inst[kMaxL + 1];  // M2M at level l: instances with 2 <= l <= L - 2
+    int m2m_count[kMaxL + 1];
+    const int32_t* l2l_inst[kMaxL + 1];  // L2L at level l: instances with 3 <= l <= L - 1
+    int l2l_count[kMaxL + 1];
+};
+
+cudaError_t batch_key_params(const BatchInst* host_inst, int count, void* dev_params,
+                             cudaStream_t s);
+size_t batch_key_params_bytes(int count);
+cudaError_t launch_batch_tree(const void* dev_key_params, const int64_t* dev_offsets, int count,
+                              int64_t ntotal, int key_bits, uint32_t nleaf_total, const float* xy,
+                              const float* gamma, SortBuffers& sb, void* particles,
+                              cudaStream_t s);
+cudaError_t launch_batch_p2m(const BatchInst* inst, const BatchLists& bl, int P,
+                             const void* particles, const uint32_t* leaf_start, const float* m2m,
+                             float* me, cudaStream_t s);
+cudaError_t launch_batch_m2m(const BatchInst* inst, const BatchLists& bl, int P, int level,
+                             const float* m2m, float* me, cudaStream_t s);
+cudaError_t launch_batch_m2l(const BatchInst* inst, const BatchLists& bl, int P, int threads,
+                             const float* m2l, const float* me, float* le, cudaStream_t s);
+cudaError_t launch_batch_l2l(const BatchInst* inst, const BatchLists& bl, int P, int level,
+                             const float* l2l, float* le, cudaStream_t s);
+size_t batch_near_bytes(int count);
+cudaError_t batch_near_fill(const BatchInst* host_inst, int count, void* dev_near,
+                            cudaStream_t s);
+cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
+                             const int32_t* leaf_inst, const uint32_t* order, uint32_t nwork,
+                             uint32_t* counter, int ctas_per_sm, const void* particles,
+                             const uint32_t* leaf_start, const float* le, const float* l2l16,
+                             const float* l2l32, float* uv, cudaStream_t s);
+cudaError_t launch_batch_direct(const BatchInst* inst, const int64_t* dev_offsets, int count,
+                                int kernel, const float* xy, const float* gamma, int64_t s_count,
+                                const int64_t* targets, double* uv_ref, int* status,
+                                cudaStream_t s);
+cudaError_t launch_batch_error(const BatchInst* inst, const int64_t* dev_offsets, int count,
+                               const float* xy, const float* uv, int64_t s_count,
+                               const int64_t* targets, const double* uv_ref, double* stats,
+                               double* leaf_err, uint32_t nleaf_total, int* status,
+                               cudaStream_t s);
 
 // Tensor maps of the tensor-core M2L: multipole hi/lo parts per level (4D:
 // 2P reals x row x column x parity plane) and the real-ified offset matrices

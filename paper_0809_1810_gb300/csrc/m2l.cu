@@ -13,16 +13,15 @@
 namespace fmm2d {
 namespace {
 
+// One target box, G lanes (lane n computes L~_n).
 template <typename R, int G>
-__global__ void __launch_bounds__(128)
-m2l_kernel(Geometry g, const R* __restrict__ m2l, const R* __restrict__ me, R* __restrict__ le) {
-    using C = typename Cplx<R>::T;  // G = P lanes per target box (16 or 32)
+__device__ __forceinline__ void m2l_box(const Geometry& g, int64_t slot, bool valid,
+                                        const R* __restrict__ m2l, const R* __restrict__ me,
+                                        R* __restrict__ le) {
+    using C = typename Cplx<R>::T;
     int lane = threadIdx.x & 31;
     int n = lane % G;
     unsigned seg = segment_mask(G);
-    int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
-    bool valid = gid < g.nboxes;
-    int64_t slot = g.level_base[2] + (valid ? gid : 0);
     int l = slot_level(g.level_base, g.L, slot);
     uint32_t ix, iy;
     slot_box(g.level_base, l, slot, &ix, &iy);
@@ -47,7 +46,37 @@ m2l_kernel(Geometry g, const R* __restrict__ m2l, const R* __restrict__ me, R* _
             }
         }
     }
+    if (n >= g.p) acc = cmake<C>(R(0), R(0));  // coefficients >= p stay zero
     if (valid) reinterpret_cast<C*>(le + slot * (2 * g.P))[n] = acc;
+}
+
+template <typename R, int G>
+__global__ void __launch_bounds__(128)
+m2l_kernel(Geometry g, const R* __restrict__ m2l, const R* __restrict__ me, R* __restrict__ le) {
+    int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    bool valid = gid < g.nboxes;
+    m2l_box<R, G>(g, g.level_base[2] + (valid ? gid : 0), valid, m2l, me, le);
+}
+
+// Batched: every box of every listed instance (levels 2..L), G lanes each.
+template <int G>
+__global__ void __launch_bounds__(256)
+m2l_batch_kernel(const BatchInst* __restrict__ inst, const int32_t* __restrict__ list,
+                 const int64_t* __restrict__ prefix, int count, int64_t total,
+                 const float* __restrict__ m2l, const float* __restrict__ me,
+                 float* __restrict__ le) {
+    const int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    const bool valid = gid < total;
+    const int64_t g0 = valid ? gid : 0;
+    int lo = 0, hi = count;  // prefix[lo] <= g0 < prefix[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= g0) lo = mid;
+        else hi = mid;
+    }
+    const BatchInst& b = inst[list[lo]];
+    m2l_box<float, G>(b.g, b.g.level_base[2] + (g0 - prefix[lo]), valid, m2l, me + b.exp_off,
+                      le + b.exp_off);
 }
 
 }  // namespace
@@ -61,6 +90,20 @@ cudaError_t launch_m2l(const Geometry& g, const Tables<R>& t, const R* me, R* le
         m2l_kernel<R, 16><<<blocks, 128, 0, s>>>(g, t.m2l, me, le);
     else
         m2l_kernel<R, 32><<<blocks, 128, 0, s>>>(g, t.m2l, me, le);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_m2l(const BatchInst* inst, const BatchLists& bl, int P, int threads,
+                             const float* m2l, const float* me, float* le, cudaStream_t s) {
+    if (bl.m2l_count == 0) return cudaSuccess;
+    const int64_t lanes = bl.m2l_total * P;
+    const int blocks = (int)((lanes + threads - 1) / threads);
+    if (P <= 16)
+        m2l_batch_kernel<16><<<blocks, threads, 0, s>>>(inst, bl.m2l_inst, bl.m2l_prefix,
+                                                       bl.m2l_count, bl.m2l_total, m2l, me, le);
+    else
+        m2l_batch_kernel<32><<<blocks, threads, 0, s>>>(inst, bl.m2l_inst, bl.m2l_prefix,
+                                                       bl.m2l_count, bl.m2l_total, m2l, me, le);
     return cudaGetLastError();
 }
 

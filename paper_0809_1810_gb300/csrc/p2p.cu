@@ -335,31 +335,31 @@ __device__ __forceinline__ void gather_bands(const float4* __restrict__ sp, cons
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(kLeafWarps * 32, 8)
-p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
-                   Geometry g, NearF32v3 nm, const float* __restrict__ le,
-                   const float* __restrict__ l2l, float* __restrict__ uv) {
-    __shared__ float4 lists[kLeafWarps][kListCap];
-    __shared__ uint32_t ranges[kLeafWarps][20];
-    __shared__ float2 leaf_le[kLeafWarps][kMaxP];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t leaf = blockIdx.x * kLeafWarps + warp;
-    const uint32_t nleaf = 1u << (2 * g.L);
-    if (leaf >= nleaf) return;
+// One leaf's targets against its local list, by one warp.  `leaf` is the
+// leaf's Morton key; leaf_start is indexed by leaf_base + key (zero for a
+// single evaluation).  buf, ranges and leaf_le are this warp's shared memory.
+__device__ __forceinline__ void p2p_leaf_f32(const float4* __restrict__ sp,
+                                             const uint32_t* __restrict__ leaf_start,
+                                             uint32_t leaf_base, uint32_t leaf, const Geometry& g,
+                                             const NearF32v3& nm, const float* __restrict__ le,
+                                             const float* __restrict__ l2l,
+                                             float* __restrict__ uv, float4* buf,
+                                             uint32_t* ranges, float2* leaf_le) {
+    const int lane = threadIdx.x & 31;
     const int nl = 1 << g.L;
     const uint32_t lx = morton_compact(leaf), ly = morton_compact(leaf >> 1);
     LeafCtx c;
-    c.t0 = leaf_start[leaf];
-    c.nt = leaf_start[leaf + 1] - c.t0;
+    c.t0 = leaf_start[leaf_base + leaf];
+    c.nt = leaf_start[leaf_base + leaf + 1] - c.t0;
     if (c.nt == 0) return;
-    uint32_t* rbeg = ranges[warp];
-    uint32_t* rpre = ranges[warp] + 9;
+    uint32_t* rbeg = ranges;
+    uint32_t* rpre = ranges + 9;
     {  // lane r < 9 reads range r
         uint32_t b = 0, len = 0;
         if (lane < 9) {
             int sx = (int)lx + lane % 3 - 1, sy = (int)ly + lane / 3 - 1;
             if (sx >= 0 && sy >= 0 && sx < nl && sy < nl) {
-                uint32_t k = morton_key((uint32_t)sx, (uint32_t)sy);
+                uint32_t k = leaf_base + morton_key((uint32_t)sx, (uint32_t)sy);
                 b = leaf_start[k];
                 len = leaf_start[k + 1] - b;
             }
@@ -369,6 +369,7 @@ p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ l
             uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += t;
         }
+        __syncwarp();  // earlier readers of ranges are done
         if (lane < 9) {
             rbeg[lane] = b;
             rpre[lane + 1] = incl;
@@ -395,11 +396,12 @@ p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ l
                 if (lane < g.P) v = cfma(t[k * g.P + lane], pk, v);
             }
         }
-        if (lane < g.P) leaf_le[warp][lane] = v;
+        if (lane >= g.p) v = make_float2(0.f, 0.f);
+        __syncwarp();  // earlier readers of leaf_le are done
+        if (lane < g.P) leaf_le[lane] = v;
         __syncwarp();
-        c.le_leaf = reinterpret_cast<const float*>(leaf_le[warp]);
+        c.le_leaf = reinterpret_cast<const float*>(leaf_le);
     }
-    float4* buf = lists[warp];
     const uint32_t total = rpre[9];
     const bool one_chunk = total <= kListCap;
     uint32_t nn = 0, nf = 0;
@@ -445,6 +447,59 @@ p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ l
             uv[2 * (int64_t)idx] = u;
             uv[2 * (int64_t)idx + 1] = v;
         }
+    }
+    __syncwarp();  // the buffer may be reused by this warp's next leaf
+}
+
+__global__ void __launch_bounds__(kLeafWarps * 32, 8)
+p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
+                   Geometry g, NearF32v3 nm, const float* __restrict__ le,
+                   const float* __restrict__ l2l, float* __restrict__ uv) {
+    __shared__ float4 lists[kLeafWarps][kListCap];
+    __shared__ uint32_t ranges[kLeafWarps][20];
+    __shared__ float2 leaf_le[kLeafWarps][kMaxP];
+    const int warp = threadIdx.x >> 5;
+    const uint32_t leaf = blockIdx.x * kLeafWarps + warp;
+    if (leaf >= (1u << (2 * g.L))) return;
+    p2p_leaf_f32(sp, leaf_start, 0, leaf, g, nm, le, l2l, uv, lists[warp], ranges[warp],
+                 leaf_le[warp]);
+}
+
+// Per-instance near-field constants of a batched evaluation.
+struct NearInst {
+    float sc, kvel, kzeta, inv_s, half_leaf;
+};
+
+// Batched and persistent: warps pull global leaves from a work counter, in
+// the order of `order` (largest instances first).
+__global__ void __launch_bounds__(kLeafWarps * 32, 8)
+p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
+                 const BatchInst* __restrict__ inst, const NearInst* __restrict__ near_inst,
+                 const int32_t* __restrict__ leaf_inst, const uint32_t* __restrict__ order,
+                 uint32_t nwork, uint32_t* counter, NearF32v3 shared_nm,
+                 const float* __restrict__ le, const float* __restrict__ l2l16,
+                 const float* __restrict__ l2l32, float* __restrict__ uv) {
+    __shared__ float4 lists[kLeafWarps][kListCap];
+    __shared__ uint32_t ranges[kLeafWarps][20];
+    __shared__ float2 leaf_le[kLeafWarps][kMaxP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        uint32_t w = 0;
+        if (lane == 0) w = atomicAdd(counter, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= nwork) break;
+        const uint32_t gleaf = order[w];
+        const int i = leaf_inst[gleaf];
+        const BatchInst& b = inst[i];
+        NearF32v3 nm = shared_nm;
+        const NearInst ni = near_inst[i];
+        nm.sc = ni.sc;
+        nm.kvel = ni.kvel;
+        nm.kzeta = ni.kzeta;
+        nm.inv_s = ni.inv_s;
+        nm.half_leaf = ni.half_leaf;
+        p2p_leaf_f32(sp, leaf_start, b.leaf_base, gleaf - b.leaf_base, b.g, nm, le + b.exp_off,
+                     b.g.P <= 16 ? l2l16 : l2l32, uv, lists[warp], ranges[warp], leaf_le[warp]);
     }
 }
 
@@ -497,10 +552,8 @@ double fit_near_polynomial(double a, double* coef) {
 
 }  // namespace
 
-template <>
-cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, const void* particles,
-                                  const uint32_t* leaf_start, const float* le, const float* l2l,
-                                  float* uv, cudaStream_t s) {
+// Near-field constants of an evaluation (formed in double, rounded once).
+static NearF32v3 near_constants(double sigma, const Geometry& g, bool* ok) {
     const double ln2 = 0.69314718055994530942;
     const double pi = 3.14159265358979323846;
     NearF32v3 nm;
@@ -514,12 +567,67 @@ cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, const void* p
     nm.half_leaf = (float)(0.5 * box * (double)nm.sc);
     nm.band2 = (float)(qthr * 1.02);  // q < 1 needs |dX|^2 < 1/ln 2; 2% margin for rounding
     double coef[kF32Deg + 1];
-    if (fit_near_polynomial(qthr, coef) > 1e-8) return cudaErrorInvalidValue;
+    *ok = fit_near_polynomial(qthr, coef) <= 1e-8;
     for (int k = 0; k <= kF32Deg; ++k) nm.coef[k] = (float)coef[k];
+    return nm;
+}
+
+template <>
+cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, const void* particles,
+                                  const uint32_t* leaf_start, const float* le, const float* l2l,
+                                  float* uv, cudaStream_t s) {
+    bool ok;
+    NearF32v3 nm = near_constants(sigma, g, &ok);
+    if (!ok) return cudaErrorInvalidValue;
     unsigned nleaf = 1u << (2 * g.L);
     unsigned blocks = (nleaf + kLeafWarps - 1) / kLeafWarps;
     p2p_l2p_f32_kernel<<<blocks, kLeafWarps * 32, 0, s>>>(
         reinterpret_cast<const float4*>(particles), leaf_start, g, nm, le, l2l, uv);
+    return cudaGetLastError();
+}
+
+size_t batch_near_bytes(int count) { return sizeof(NearInst) * (size_t)count; }
+
+cudaError_t batch_near_fill(const BatchInst* host_inst, int count, void* dev_near,
+                            cudaStream_t s) {
+    NearInst* h = new NearInst[count];
+    bool ok = true;
+    for (int i = 0; i < count; ++i) {
+        bool oki;
+        NearF32v3 nm = near_constants(host_inst[i].sigma, host_inst[i].g, &oki);
+        ok = ok && oki;
+        h[i] = NearInst{nm.sc, nm.kvel, nm.kzeta, nm.inv_s, nm.half_leaf};
+    }
+    cudaError_t e = ok ? cudaMemcpyAsync(dev_near, h, sizeof(NearInst) * count,
+                                         cudaMemcpyHostToDevice, s)
+                       : cudaErrorInvalidValue;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    delete[] h;
+    return e;
+}
+
+cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
+                             const int32_t* leaf_inst, const uint32_t* order, uint32_t nwork,
+                             uint32_t* counter, int ctas_per_sm, const void* particles,
+                             const uint32_t* leaf_start, const float* le, const float* l2l16,
+                             const float* l2l32, float* uv, cudaStream_t s) {
+    if (nwork == 0) return cudaSuccess;
+    Geometry g1{};
+    g1.W = 2.0;
+    g1.L = 0;
+    bool ok;
+    NearF32v3 shared_nm = near_constants(1.0, g1, &ok);  // sigma-independent parts
+    if (!ok) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    unsigned blocks = (unsigned)(sms * ctas_per_sm);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    p2p_batch_kernel<<<blocks, kLeafWarps * 32, 0, s>>>(
+        reinterpret_cast<const float4*>(particles), leaf_start, inst,
+        static_cast<const NearInst*>(near_inst), leaf_inst, order, nwork, counter, shared_nm, le,
+        l2l16, l2l32, uv);
     return cudaGetLastError();
 }
 

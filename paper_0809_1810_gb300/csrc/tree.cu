@@ -344,6 +344,122 @@ template cudaError_t launch_tree_build<double>(const Geometry&, int64_t, const d
 
 
 // ---------------------------------------------------------------------------
+// Batched tree build: keys of all instances in one global leaf index space
+// (instance i's keys are leaf_base_i + its Morton keys), then the same stable
+// radix sort, record gather and leaf ranges as a single evaluation.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchKeyParams {
+    KeyParams kp;
+    uint32_t leaf_base;
+    int L;
+};
+
+__global__ void __launch_bounds__(kSortThreads)
+batch_keys_hist_kernel(int64_t n, const float* __restrict__ xy, const float* __restrict__ gamma,
+                       const BatchKeyParams* __restrict__ bkp, const int64_t* __restrict__ offsets,
+                       int count, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                       uint32_t* __restrict__ hist, int nblocks, int* status) {
+    __shared__ uint32_t cnt[kRadix];
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) cnt[d] = 0;
+    __syncthreads();
+    int flags = 0;
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int it = 0; it < kSortItems; ++it) {
+        int64_t i = base + it * kSortThreads + threadIdx.x;
+        if (i < n) {
+            int lo = 0, hi = count;  // offsets[lo] <= i < offsets[hi]
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (offsets[mid] <= i) lo = mid;
+                else hi = mid;
+            }
+            const BatchKeyParams& b = bkp[lo];
+            const KeyParams& kp = b.kp;
+            float x = xy[2 * i], y = xy[2 * i + 1];
+            if (!isfinite(gamma[i])) flags |= kFlagNonfinite;
+            uint32_t ix, iy;
+            if (kp.fast) {
+                ix = leaf_coord_f32(x, kp.lox, kp.hix, kp.x0f, kp.scalef, kp.margin, kp.x0,
+                                    kp.scale, kp.top, &flags);
+                iy = leaf_coord_f32(y, kp.loy, kp.hiy, kp.y0f, kp.scalef, kp.margin, kp.y0,
+                                    kp.scale, kp.top, &flags);
+            } else {
+                ix = leaf_coord((double)x, kp.x0, kp.x1, kp.scale, kp.top, &flags);
+                iy = leaf_coord((double)y, kp.y0, kp.y1, kp.scale, kp.top, &flags);
+            }
+            uint32_t k = b.leaf_base + morton_key(ix, iy);
+            keys[i] = k;
+            vals[i] = (uint32_t)i;
+            atomicAdd(&cnt[k & (kRadix - 1)], 1u);
+        }
+    }
+    if (flags) atomicOr(status, flags);
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+        hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
+}
+
+}  // namespace
+
+size_t batch_key_params_bytes(int count) { return sizeof(BatchKeyParams) * (size_t)count; }
+
+cudaError_t batch_key_params(const BatchInst* host_inst, int count, void* dev_params,
+                             cudaStream_t s) {
+    static_assert(sizeof(BatchKeyParams) % 8 == 0, "aligned records");
+    BatchKeyParams* h = new BatchKeyParams[count];
+    for (int i = 0; i < count; ++i) {
+        const Geometry& g = host_inst[i].g;
+        h[i].kp = make_key_params(g.x0, g.y0, g.W, g.L);
+        h[i].leaf_base = host_inst[i].leaf_base;
+        h[i].L = g.L;
+    }
+    cudaError_t e = cudaMemcpyAsync(dev_params, h, sizeof(BatchKeyParams) * count,
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    delete[] h;
+    return e;
+}
+
+cudaError_t launch_batch_tree(const void* dev_key_params, const int64_t* dev_offsets, int count,
+                              int64_t ntotal, int key_bits, uint32_t nleaf_total, const float* xy,
+                              const float* gamma, SortBuffers& sb, void* particles,
+                              cudaStream_t s) {
+    if (ntotal == 0) {
+        leaf_bounds_kernel<<<1, 32, 0, s>>>(0, sb.keys[0], nleaf_total, sb.leaf_start);
+        return cudaGetLastError();
+    }
+    int nblocks = (int)((ntotal + kSortTile - 1) / kSortTile);
+    int passes = key_bits <= kRadixBits ? 1 : (key_bits + kRadixBits - 1) / kRadixBits;
+    uint32_t* digit_total = sb.hist + (int64_t)kRadix * nblocks;
+    batch_keys_hist_kernel<<<nblocks, kSortThreads, 0, s>>>(
+        ntotal, xy, gamma, static_cast<const BatchKeyParams*>(dev_key_params), dev_offsets, count,
+        sb.keys[0], sb.vals[0], sb.hist, nblocks, sb.status);
+    for (int q = 0; q < passes; ++q) {
+        int src = q & 1, dst = src ^ 1;
+        int shift = q * kRadixBits;
+        if (q > 0)
+            hist_kernel<<<nblocks, kSortThreads, 0, s>>>(ntotal, sb.keys[src], shift, sb.hist,
+                                                         nblocks);
+        scan_digits_kernel<<<kRadix, 256, 0, s>>>(sb.hist, nblocks, digit_total);
+        if (q == passes - 1)
+            scatter_kernel<float, true><<<nblocks, kSortThreads, 0, s>>>(
+                ntotal, sb.keys[src], sb.vals[src], shift, sb.hist, digit_total, nblocks,
+                sb.keys[dst], sb.perm, xy, gamma, reinterpret_cast<float4*>(particles));
+        else
+            scatter_kernel<float, false><<<nblocks, kSortThreads, 0, s>>>(
+                ntotal, sb.keys[src], sb.vals[src], shift, sb.hist, digit_total, nblocks,
+                sb.keys[dst], sb.vals[dst], xy, gamma, reinterpret_cast<float4*>(particles));
+    }
+    const uint32_t* sorted = sb.keys[passes & 1];
+    int lb_blocks = (int)((ntotal + 1 + 255) / 256);
+    if (lb_blocks > 4096) lb_blocks = 4096;
+    leaf_bounds_kernel<<<lb_blocks, 256, 0, s>>>(ntotal, sorted, nleaf_total, sb.leaf_start);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Tree build without allocation (fmm2d_tree_build_noalloc).
 //
 // For callers that cannot allocate device memory.  The scratch the build

@@ -23,17 +23,21 @@ constexpr int kTopLevel = 4;  // levels <= kTopLevel run in the single-CTA kerne
 
 // One warp per leaf, four sibling leaves per CTA; lanes stride over the
 // leaf's particles, accumulate all coefficients, then reduce across the warp.
+// `quad` is the parent box (Morton key at level L-1); leaf keys are offset by
+// leaf_base in leaf_start (zero for a single evaluation).
 template <typename R, int PMAX>
-__global__ void __launch_bounds__(128)
-p2m_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
-           const uint32_t* __restrict__ leaf_start, Geometry g, double scale,
-           const R* __restrict__ m2m, bool fuse_parent, R* __restrict__ me) {
+__device__ __forceinline__ void p2m_quad(const typename ParticleOf<R>::type* __restrict__ sp,
+                                         const uint32_t* __restrict__ leaf_start,
+                                         uint32_t leaf_base, uint32_t quad, const Geometry& g,
+                                         const R* __restrict__ m2m, bool fuse_parent,
+                                         R* __restrict__ me,
+                                         typename Cplx<R>::T (*child_me)[PMAX]) {
     using C = typename Cplx<R>::T;
-    __shared__ C child_me[4][PMAX];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t leaf = (int64_t)blockIdx.x * 4 + warp;
-    const uint32_t ix = morton_compact((uint32_t)leaf), iy = morton_compact((uint32_t)leaf >> 1);
-    const uint32_t b = leaf_start[leaf], e = leaf_start[leaf + 1];
+    const uint32_t leaf = quad * 4 + warp;
+    const uint32_t ix = morton_compact(leaf), iy = morton_compact(leaf >> 1);
+    const uint32_t b = leaf_start[leaf_base + leaf], e = leaf_start[leaf_base + leaf + 1];
+    const double scale = g.scale;
     R cxh, cxl, cyh, cyl;
     if (sizeof(R) == 4) {
         float a0, a1, a2, a3;
@@ -81,7 +85,7 @@ p2m_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
             child_me[warp][m] = acc[m];
         }
     }
-    if (!fuse_parent) return;  // uniform over the grid
+    if (!fuse_parent) return;  // uniform over the CTA
     __syncthreads();
     if (warp == 0 && lane < g.P) {  // parent at level L-1; child quadrant q is warp q
         const C* tab = reinterpret_cast<const C*>(m2m);
@@ -92,9 +96,32 @@ p2m_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
             for (int k = 0; k < PMAX; ++k)
                 if (k < g.P) out = cfma(tq[k * g.P + lane], child_me[q][k], out);
         }
+        if (lane >= g.p) out = cmake<C>(R(0), R(0));
         reinterpret_cast<C*>(me + box_slot(g.level_base, g.L - 1, ix >> 1, iy >> 1) *
                                       (2 * g.P))[lane] = out;
     }
+}
+
+template <typename R, int PMAX>
+__global__ void __launch_bounds__(128)
+p2m_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
+           const uint32_t* __restrict__ leaf_start, Geometry g, const R* __restrict__ m2m,
+           bool fuse_parent, R* __restrict__ me) {
+    __shared__ typename Cplx<R>::T child_me[4][PMAX];
+    p2m_quad<R, PMAX>(sp, leaf_start, 0, blockIdx.x, g, m2m, fuse_parent, me, child_me);
+}
+
+// Batched: one CTA per parent box of any instance of the class.
+template <int PMAX>
+__global__ void __launch_bounds__(128)
+p2m_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
+                 const BatchInst* __restrict__ inst, const int32_t* __restrict__ quad_inst,
+                 const uint32_t* __restrict__ quad_local, const float* __restrict__ m2m,
+                 float* __restrict__ me) {
+    __shared__ float2 child_me[4][PMAX];
+    const BatchInst& b = inst[quad_inst[blockIdx.x]];
+    p2m_quad<float, PMAX>(sp, leaf_start, b.leaf_base, quad_local[blockIdx.x], b.g, m2m,
+                          b.g.L >= 3, me + b.exp_off, child_me);
 }
 
 // M2M of one box with G lanes (lane n computes b~_n); children read by lane k
@@ -119,6 +146,7 @@ __device__ __forceinline__ void m2m_box(const Geometry& g, int level, int64_t sl
             acc = cfma(tab[(q * G + k) * G + n], ak, acc);
         }
     }
+    if (n >= g.p) acc = cmake<C>(R(0), R(0));  // coefficients >= p stay zero
     if (valid) reinterpret_cast<C*>(me + slot * (2 * g.P))[n] = acc;
 }
 
@@ -161,7 +189,53 @@ m2m_top_kernel(Geometry g, int lhi, const R* __restrict__ m2m, R* __restrict__ m
     }
 }
 
+// Batched M2M at one level: G lanes per box, boxes of the listed instances.
+template <int G>
+__global__ void __launch_bounds__(256)
+m2m_batch_kernel(const BatchInst* __restrict__ inst, const int32_t* __restrict__ list, int count,
+                 int level, const float* __restrict__ m2m, float* __restrict__ me) {
+    __shared__ float2 tab[4 * G * G];
+    stage_table<float, G>(m2m, tab);
+    const int64_t per = (int64_t)1 << (2 * level);
+    const int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    const bool valid = gid < per * count;
+    const int64_t g0 = valid ? gid : 0;
+    const BatchInst& b = inst[list[g0 / per]];
+    m2m_box<float, G>(b.g, level, b.g.level_base[level] + g0 % per, valid, tab, me + b.exp_off);
+}
+
 }  // namespace
+
+cudaError_t launch_batch_p2m(const BatchInst* inst, const BatchLists& bl, int P,
+                             const void* particles, const uint32_t* leaf_start, const float* m2m,
+                             float* me, cudaStream_t s) {
+    if (bl.nquads == 0) return cudaSuccess;
+    const float4* sp = reinterpret_cast<const float4*>(particles);
+    if (P <= 16)
+        p2m_batch_kernel<16><<<(unsigned)bl.nquads, 128, 0, s>>>(sp, leaf_start, inst,
+                                                                bl.quad_inst, bl.quad_local, m2m,
+                                                                me);
+    else
+        p2m_batch_kernel<32><<<(unsigned)bl.nquads, 128, 0, s>>>(sp, leaf_start, inst,
+                                                                bl.quad_inst, bl.quad_local, m2m,
+                                                                me);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_m2m(const BatchInst* inst, const BatchLists& bl, int P, int level,
+                             const float* m2m, float* me, cudaStream_t s) {
+    const int count = bl.m2m_count[level];
+    if (count == 0) return cudaSuccess;
+    const int64_t threads = ((int64_t)1 << (2 * level)) * count * P;
+    const int blocks = (int)((threads + 255) / 256);
+    if (P <= 16)
+        m2m_batch_kernel<16><<<blocks, 256, 0, s>>>(inst, bl.m2m_inst[level], count, level, m2m,
+                                                   me);
+    else
+        m2m_batch_kernel<32><<<blocks, 256, 0, s>>>(inst, bl.m2m_inst[level], count, level, m2m,
+                                                   me);
+    return cudaGetLastError();
+}
 
 template <typename R>
 cudaError_t launch_p2m(const Geometry& g, const void* particles, const uint32_t* leaf_start,
@@ -169,14 +243,13 @@ cudaError_t launch_p2m(const Geometry& g, const void* particles, const uint32_t*
     using P = typename ParticleOf<R>::type;
     int64_t nleaf = (int64_t)1 << (2 * g.L);
     int blocks = (int)(nleaf / 4);
-    double scale = ldexp(1.0, g.L) / g.W;
     bool fuse = g.L >= 3;
     if (g.P <= 16)
         p2m_kernel<R, 16><<<blocks, 128, 0, s>>>(reinterpret_cast<const P*>(particles), leaf_start,
-                                                 g, scale, t.m2m, fuse, me);
+                                                 g, t.m2m, fuse, me);
     else
         p2m_kernel<R, 32><<<blocks, 128, 0, s>>>(reinterpret_cast<const P*>(particles), leaf_start,
-                                                 g, scale, t.m2m, fuse, me);
+                                                 g, t.m2m, fuse, me);
     return cudaGetLastError();
 }
 

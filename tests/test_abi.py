@@ -76,3 +76,23 @@ def test_oracle_and_cuda_path_share_nothing():
         if f.endswith(".c"):
             with open(p) as fh:
                 assert "fmm2d.h" not in fh.read()
+
+
+@pytest.mark.parametrize("field,value", [("n", -1), ("p", 0), ("p", 40), ("L", 13),
+                                         ("sigma", 0.0), ("W", 0.0)])
+def test_batch_rejects_invalid_instances(lib, field, value):
+    good = _native.Instance(100, 8, 3, 0.01, -1.0, -1.0, 2.0)
+    bad = _native.Instance(100, 8, 3, 0.01, -1.0, -1.0, 2.0)
+    setattr(bad, field, value)
+    arr = (_native.Instance * 2)(good, bad)
+    h = ctypes.c_void_p(99)
+    assert lib.fmm2d_batch_plan_create(ctypes.byref(h), 2, arr) == _native.INVALID_ARG
+    assert h.value is None
+    assert b"instance 1" in lib.fmm2d_batch_last_error()
+
+
+def test_batch_rejects_empty_and_oversized(lib):
+    h = ctypes.c_void_p()
+    assert lib.fmm2d_batch_plan_create(ctypes.byref(h), 0, None) == _native.INVALID_ARG
+    big = (_native.Instance * 300)(*[_native.Instance(10, 4, 12, 0.01, -1.0, -1.0, 2.0)] * 300)
+    assert lib.fmm2d_batch_plan_create(ctypes.byref(h), 300, big) == _native.INVALID_ARG
