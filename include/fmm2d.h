@@ -214,7 +214,7 @@ fmm2d_status fmm2d_batch_velocity(fmm2d_batch_plan* plan, const float* xy_dev,
 fmm2d_status fmm2d_batch_check(fmm2d_batch_plan* plan, cudaStream_t stream);
 
 /* Autotuner: times candidate launch shapes of the two heaviest steps on the
- * given batch (persistent near-field CTAs per SM in {2..5}; M2L block size in
+ * given batch (persistent near-field CTAs per SM in {2..6}; M2L block size in
  * {64, 128, 256}), keeps the fastest and leaves uv_dev holding the
  * velocities.  Synchronous; later fmm2d_batch_velocity calls use the
  * choices. */
@@ -281,6 +281,111 @@ fmm2d_status fmm2d_tree_build_noalloc(int precision, int64_t n, const void* xy_d
                                       double W, uint32_t* keys_dev, uint32_t* perm_dev,
                                       uint32_t* leaf_start_dev, int* flags_dev,
                                       cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Learned (p, L) proposer.
+ *
+ * Sec. 5 measures how the FMM error moves with the expansion order p and the
+ * tree depth l, and Sec. 4.1 (Eqs. 26-29) shows that a leaf too small
+ * against the core size sigma puts a floor under it that no p removes.  The
+ * proposer learns that error surface from the library's own measurements --
+ * FMM velocities against the FP64 direct sum at sampled particles -- and
+ * picks the cheapest (p, L) whose predicted maximum error meets a
+ * tolerance, falling back to a conservative fixed setting when no candidate
+ * qualifies.  The paper tunes (p, l) by hand; the network is not in it.
+ *
+ * Network: FMM2D_MLP_INPUTS -> 128 -> 128 -> 128 -> FMM2D_MLP_OUTPUTS,
+ * SiLU between layers, weights stored in BF16 (rounded to nearest even from
+ * FP32 master copies), biases, activations and every accumulation in FP32.
+ * Inputs are standardised and outputs de-standardised with constants the
+ * caller sets.  Outputs: (log10 of the median over sampled leaves of the
+ * per-leaf max error, log10 of the max error), both relative to max |u|.
+ *
+ * Master parameter layout (FMM2D_MLP_PARAMS floats): for layers l = 0..3,
+ * W_l as [out][in] row-major, then b_l [out].
+ *
+ * Features (fmm2d_features), for a particle set and a candidate (p, L):
+ *   0 p                       6 max / mean particles per leaf
+ *   1 L                       7 sum_b |S_b| / sum_i |Gamma_i|
+ *   2 sigma / h, h = W/sqrt(n) 8 std_b(S_b) / A
+ *   3 log2 n                  9 max_b |S_b| / A
+ *   4 log2 mean per leaf     10 sum Gamma / sum |Gamma|
+ *   5 std / mean per leaf    11 log10(leaf width / sigma)
+ * where S_b is the circulation sum of leaf b at depth L and
+ * A = sum |Gamma| / 4^L.  Circulations enter only as ratios: the relative
+ * error does not change when every Gamma is scaled.
+ * ------------------------------------------------------------------------ */
+#define FMM2D_MLP_INPUTS 12
+#define FMM2D_MLP_OUTPUTS 2
+#define FMM2D_MLP_PARAMS 34946
+
+typedef struct fmm2d_mlp fmm2d_mlp;
+
+/* Detail of the last proposer-call error on the calling host thread. */
+const char* fmm2d_mlp_last_error(void);
+
+/* Create a network for batches of up to max_rows rows (1 .. 2^20) on the
+ * current device; weights uniform in +-1/sqrt(fan_in) from a splitmix64
+ * stream seeded with `seed`, biases zero, identity normalisation, Adam
+ * moments zero.  Synchronous. */
+fmm2d_status fmm2d_mlp_create(fmm2d_mlp** out, int max_rows, uint64_t seed);
+void fmm2d_mlp_destroy(fmm2d_mlp* net);
+
+/* Standardisation constants (host arrays of 12, 12, 2, 2 floats; every std
+ * > 0): the network sees (x - in_mean) / in_std, and its raw output y is
+ * reported as y * out_std + out_mean.  Training targets are standardised
+ * the same way.  Synchronous. */
+fmm2d_status fmm2d_mlp_set_normalization(fmm2d_mlp* net, const float* in_mean,
+                                         const float* in_std, const float* out_mean,
+                                         const float* out_std);
+
+/* Read (get_host != NULL) and/or replace (set_host != NULL) the FP32 master
+ * parameters, FMM2D_MLP_PARAMS floats in the layout above; replacing also
+ * re-rounds the BF16 copies.  Adam moments are kept.  Synchronous. */
+fmm2d_status fmm2d_mlp_params(fmm2d_mlp* net, float* get_host, const float* set_host);
+
+/* y_dev[rows][2] = network(x_dev[rows][12]) in de-standardised units (device
+ * buffers, rows <= max_rows).  Asynchronous on `stream`. */
+fmm2d_status fmm2d_mlp_forward(fmm2d_mlp* net, int rows, const float* x_dev, float* y_dev,
+                               cudaStream_t stream);
+
+/* Gradient of the mean squared error between the standardised output and
+ * the standardised targets t_dev[rows][2], mean over rows x outputs, with
+ * respect to the master parameters (computed through the BF16 weights):
+ * grad_dev receives FMM2D_MLP_PARAMS floats, loss_dev (optional) the loss.
+ * Asynchronous on `stream`. */
+fmm2d_status fmm2d_mlp_gradients(fmm2d_mlp* net, int rows, const float* x_dev,
+                                 const float* t_dev, float* grad_dev, float* loss_dev,
+                                 cudaStream_t stream);
+
+/* One Adam step (Kingma & Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8, bias
+ * correction by the step count) on that gradient at learning rate lr > 0;
+ * loss_dev (optional) receives the loss before the step.  Asynchronous. */
+fmm2d_status fmm2d_mlp_train_step(fmm2d_mlp* net, int rows, const float* x_dev,
+                                  const float* t_dev, float lr, float* loss_dev,
+                                  cudaStream_t stream);
+
+/* The 12 features above for n >= 1 particles (float xy_dev, gamma_dev on the
+ * device) with core size sigma, root box (x0, y0, W), candidate p >= 1 and
+ * depth L (0..10); particles outside the box count in the nearest edge
+ * leaf.  Allocates stream-ordered scratch (16 * 4^L bytes), synchronises
+ * `stream` and writes feat_host[12]. */
+fmm2d_status fmm2d_features(int64_t n, const float* xy_dev, const float* gamma_dev,
+                            double sigma, double x0, double y0, double W, int p, int L,
+                            float* feat_host, cudaStream_t stream);
+
+/* Pick the cheapest candidate whose predicted log10 max error is at most
+ * log10(tol) - margin.  features_host holds ncand rows of 12 features whose
+ * first two entries are the candidate's integral p (1..32) and L (0..12);
+ * cost_host its cost (any unit, smaller is better).  *p_out, *L_out receive
+ * the choice, or (fallback_p, fallback_L) when no candidate qualifies or
+ * ncand == 0; *choice_out (optional) the chosen row or -1;
+ * predicted_host (optional) 2 * ncand predicted outputs.  Synchronous, on
+ * the legacy default stream. */
+fmm2d_status fmm2d_propose(fmm2d_mlp* net, int ncand, const float* features_host,
+                           const double* cost_host, double tol, double margin, int fallback_p,
+                           int fallback_L, int* p_out, int* L_out, int* choice_out,
+                           float* predicted_host);
 
 /* Number of kernel launches one fmm2d_velocity call makes (the kernel nodes
  * of its recorded CUDA graph); -1 before the first call. */

@@ -27,7 +27,12 @@ class FMMError(RuntimeError):
     def __init__(self, status: int, where: str):
         lib = _native.load()
         name = lib.fmm2d_status_string(status).decode()
-        getter = lib.fmm2d_batch_last_error if where.startswith("batch") else lib.fmm2d_last_error
+        if where.startswith("batch"):
+            getter = lib.fmm2d_batch_last_error
+        elif where.startswith(("mlp", "features", "propose")):
+            getter = lib.fmm2d_mlp_last_error
+        else:
+            getter = lib.fmm2d_last_error
         detail = getter().decode()
         super().__init__(f"{where}: {name} ({detail})" if detail else f"{where}: {name}")
         self.status = status

@@ -12,6 +12,7 @@ from . import build as _build
 OK, INVALID_ARG, OUT_OF_DOMAIN, NONFINITE, CUDA_ERROR, TIMEOUT, OUT_OF_MEMORY, UNSUPPORTED = range(8)
 FP64, FP32, FP32_TC = 0, 1, 2
 NUM_PHASES = 6
+MLP_INPUTS, MLP_OUTPUTS, MLP_PARAMS = 12, 2, 34946
 PHASES = ("tree", "p2m", "m2m", "m2l", "l2l", "p2p_l2p")
 
 HEADER = os.path.join(_build.INCLUDE, "fmm2d.h")
@@ -80,6 +81,16 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "fmm2d_batch_error_stats": ([vp, vp, vp, i64, vp, vp, vp, vp, vp], i32),
         "fmm2d_batch_info": ([vp, vp, vp, vp, vp, vp], i32),
         "fmm2d_batch_tree_debug": ([vp, vp, vp, vp, vp], i32),
+        "fmm2d_mlp_last_error": ([], ctypes.c_char_p),
+        "fmm2d_mlp_create": ([ctypes.POINTER(vp), i32, ctypes.c_uint64], i32),
+        "fmm2d_mlp_destroy": ([vp], None),
+        "fmm2d_mlp_set_normalization": ([vp, vp, vp, vp, vp], i32),
+        "fmm2d_mlp_params": ([vp, vp, vp], i32),
+        "fmm2d_mlp_forward": ([vp, i32, vp, vp, vp], i32),
+        "fmm2d_mlp_gradients": ([vp, i32, vp, vp, vp, vp, vp], i32),
+        "fmm2d_mlp_train_step": ([vp, i32, vp, vp, ctypes.c_float, vp, vp], i32),
+        "fmm2d_features": ([i64, vp, vp, d, d, d, d, i32, i32, vp, vp], i32),
+        "fmm2d_propose": ([vp, i32, vp, vp, d, d, i32, i32, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)

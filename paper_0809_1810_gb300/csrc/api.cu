@@ -58,6 +58,7 @@ struct fmm2d_plan {
     double* tab64 = nullptr;
     float* tab32 = nullptr;
     int* d_status = nullptr;
+    uint32_t* p2p_counter = nullptr;  // near-field work counter (in the status slot)
     int* h_status = nullptr;
     // host-call staging
     void* st_xy = nullptr;
@@ -141,8 +142,9 @@ cudaError_t enqueue(fmm2d_plan* pl, int64_t n, const R* xy, const R* gamma, R* u
     STEP(mark(pl, 4, s));
     if (g.L >= 4) STEP(launch_l2l<R>(g, t, le, s));
     STEP(mark(pl, 5, s));
-    STEP(launch_p2p_l2p<R>(g, pl->prm.sigma, pl->particles, pl->sb.leaf_start, le, t.l2l, uv,
-                           s));
+    STEP(launch_p2p_l2p<R>(g, pl->prm.sigma, n, pl->particles,
+                           pl->sb.keys[sort_passes(2 * g.L) & 1], pl->sb.leaf_start,
+                           pl->p2p_counter, le, t.l2l, uv, s));
     STEP(mark(pl, 6, s));
 #undef STEP
     return cudaSuccess;
@@ -316,7 +318,7 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
         align256(tab_count * 8),                              // tables fp64
         align256(tab_count * 4),                              // tables fp32
         align256((size_t)(2 * g.P + 1) * (2 * g.P + 1) * 8),  // binomials
-        256,                                                  // status
+        256,                                                  // status, work counter
     };
     size_t total = 0;
     for (size_t s : sizes) total += s;
@@ -342,6 +344,7 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
     pl->tab32 = (float*)slots[11];
     double* binom = (double*)slots[12];
     pl->d_status = (int*)slots[13];
+    pl->p2p_counter = reinterpret_cast<uint32_t*>(static_cast<char*>(slots[13]) + 128);
     pl->sb.status = pl->d_status;
 
     e = cudaHostAlloc((void**)&pl->h_status, sizeof(int), cudaHostAllocDefault);
@@ -482,8 +485,7 @@ fmm2d_status fmm2d_tree_debug(fmm2d_plan* pl, uint32_t* keys, uint32_t* perm,
     if (pl->g_n < 0) return fail(FMM2D_INVALID_ARG, "no evaluation has run on this plan");
     int64_t n = pl->g_n;
     int bits = 2 * pl->geo.L;
-    int passes = bits <= kRadixBits ? 1 : (bits + kRadixBits - 1) / kRadixBits;
-    const uint32_t* sorted = pl->sb.keys[passes & 1];
+    const uint32_t* sorted = pl->sb.keys[sort_passes(bits) & 1];
     if (keys && n > 0)
         CK(cudaMemcpyAsync(keys, sorted, n * 4, cudaMemcpyDeviceToDevice, stream));
     if (perm && n > 0)

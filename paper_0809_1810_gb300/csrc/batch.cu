@@ -55,7 +55,6 @@ struct fmm2d_batch_plan {
     void* d_keyparams = nullptr;
     void* d_near = nullptr;
     int32_t* d_leaf_inst = nullptr;
-    uint32_t* d_order = nullptr;
     uint32_t* d_counter = nullptr;
     int* d_status = nullptr;
     int* h_status = nullptr;
@@ -119,9 +118,10 @@ cudaError_t enqueue_batch(fmm2d_batch_plan* b, const float* xy, const float* gam
             if (b->has_class[c])
                 BSTEP(launch_batch_l2l(b->d_inst, b->lists[c], c ? 32 : 16, l, tab_l2l(b, c),
                                        b->le, s));
-    BSTEP(launch_batch_p2p(b->d_inst, b->d_near, b->d_leaf_inst, b->d_order, b->nleaf_total,
-                           b->d_counter, b->p2p_ctas_per_sm, b->particles, b->sb.leaf_start,
-                           b->le, b->has_class[0] ? tab_l2l(b, 0) : nullptr,
+    BSTEP(launch_batch_p2p(b->d_inst, b->d_near, b->d_leaf_inst, (uint32_t)b->ntotal,
+                           b->d_counter, b->p2p_ctas_per_sm, b->particles,
+                           b->sb.keys[sort_passes(b->key_bits) & 1], b->sb.leaf_start, b->le,
+                           b->has_class[0] ? tab_l2l(b, 0) : nullptr,
                            b->has_class[1] ? tab_l2l(b, 1) : nullptr, uv, s));
 #undef BSTEP
     return cudaSuccess;
@@ -265,17 +265,6 @@ fmm2d_status fmm2d_batch_plan_create(fmm2d_batch_plan** out, int count,
         for (int l = 2; l <= g.L - 2; ++l) lvl_m2m[c][l].push_back(i);
         for (int l = 3; l <= g.L - 1; ++l) lvl_l2l[c][l].push_back(i);
     }
-    // P2P order: instances by decreasing particle count, leaves in key order
-    std::vector<int> by_size(count);
-    for (int i = 0; i < count; ++i) by_size[i] = i;
-    std::stable_sort(by_size.begin(), by_size.end(),
-                     [&](int a, int c) { return in[a].n > in[c].n; });
-    std::vector<uint32_t> order;
-    order.reserve(nleaf);
-    for (int i : by_size)
-        for (uint32_t k = 0; k < (1u << (2 * b->inst[i].g.L)); ++k)
-            order.push_back(b->inst[i].leaf_base + k);
-
     // one device allocation
     int64_t nmax = ntotal > 0 ? ntotal : 1;
     int64_t nblocks = (nmax + kSortTile - 1) / kSortTile;
@@ -283,7 +272,7 @@ fmm2d_status fmm2d_batch_plan_create(fmm2d_batch_plan** out, int count,
                            (size_t)(8 + kOffsetSlots) * 32 * 32 * 2};
     std::vector<size_t> sizes = {
         a256(sizeof(BatchInst) * count), a256(8 * (count + 1)), a256(batch_key_params_bytes(count)),
-        a256(batch_near_bytes(count)), a256(4 * nleaf), a256(4 * nleaf), 256,  // counter
+        a256(batch_near_bytes(count)), a256(4 * nleaf), 256,  // counter
         256,                                                                   // status
         a256(4 * nmax), a256(4 * nmax), a256(4 * nmax), a256(4 * nmax), a256(4 * nmax),
         a256(4 * ((size_t)kRadix * nblocks + kRadix)), a256(4 * (nleaf + 1)), a256(16 * nmax),
@@ -314,7 +303,6 @@ fmm2d_status fmm2d_batch_plan_create(fmm2d_batch_plan** out, int count,
     b->d_keyparams = take(sizes[k++]);
     b->d_near = take(sizes[k++]);
     b->d_leaf_inst = (int32_t*)take(sizes[k++]);
-    b->d_order = (uint32_t*)take(sizes[k++]);
     b->d_counter = (uint32_t*)take(sizes[k++]);
     b->d_status = (int*)take(sizes[k++]);
     b->sb.keys[0] = (uint32_t*)take(sizes[k++]);
@@ -344,7 +332,6 @@ fmm2d_status fmm2d_batch_plan_create(fmm2d_batch_plan** out, int count,
     e = up(b->d_inst, b->inst.data(), sizeof(BatchInst) * count);
     if (e == cudaSuccess) e = up(b->d_offsets, offsets.data(), 8 * (count + 1));
     if (e == cudaSuccess) e = up(b->d_leaf_inst, leaf_inst.data(), 4 * nleaf);
-    if (e == cudaSuccess) e = up(b->d_order, order.data(), 4 * nleaf);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), s);
     for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
         BatchLists& bl = b->lists[c];
@@ -457,13 +444,14 @@ fmm2d_status fmm2d_batch_autotune(fmm2d_batch_plan* b, const float* xy, const fl
         }
         return best;
     };
-    // near field: persistent CTAs per SM (shared memory allows at most 5)
+    // near field: persistent CTAs per SM (shared memory allows at most 6)
     float best = 1e30f;
     int best_cps = b->p2p_ctas_per_sm;
-    for (int cps : {2, 3, 4, 5}) {
+    for (int cps : {2, 3, 4, 5, 6}) {
         float ms = time_it([&] {
-            return launch_batch_p2p(b->d_inst, b->d_near, b->d_leaf_inst, b->d_order,
-                                    b->nleaf_total, b->d_counter, cps, b->particles,
+            return launch_batch_p2p(b->d_inst, b->d_near, b->d_leaf_inst, (uint32_t)b->ntotal,
+                                    b->d_counter, cps, b->particles,
+                                    b->sb.keys[sort_passes(b->key_bits) & 1],
                                     b->sb.leaf_start, b->le,
                                     b->has_class[0] ? tab_l2l(b, 0) : nullptr,
                                     b->has_class[1] ? tab_l2l(b, 1) : nullptr, uv, s);
@@ -541,7 +529,7 @@ fmm2d_status fmm2d_batch_info(const fmm2d_batch_plan* b, int64_t* n_total, int64
 fmm2d_status fmm2d_batch_tree_debug(fmm2d_batch_plan* b, uint32_t* keys, uint32_t* perm,
                                     uint32_t* leaf_start, cudaStream_t stream) {
     if (!b) return bfail(FMM2D_INVALID_ARG, "null plan");
-    int passes = b->key_bits <= kRadixBits ? 1 : (b->key_bits + kRadixBits - 1) / kRadixBits;
+    int passes = sort_passes(b->key_bits);
     if (keys && b->ntotal > 0)
         BCK(cudaMemcpyAsync(keys, b->sb.keys[passes & 1], 4 * b->ntotal, cudaMemcpyDeviceToDevice,
                             stream));

@@ -111,6 +111,12 @@ cudaError_t launch_build_tables(int p, int P, double* m2m, double* l2l, double* 
                                 double* binom_scratch, cudaStream_t s);
 cudaError_t launch_tables_to_f32(const double* src, float* dst, int64_t count, cudaStream_t s);
 
+// Sorted keys after an LSD sort of key_bits-bit keys (kRadixBits per pass):
+// the buffer the last pass wrote.
+inline int sort_passes(int key_bits) {
+    return key_bits <= kRadixBits ? 1 : (key_bits + kRadixBits - 1) / kRadixBits;
+}
+
 struct SortBuffers {
     uint32_t* keys[2];
     uint32_t* vals[2];
@@ -134,9 +140,9 @@ cudaError_t launch_m2l(const Geometry& g, const Tables<R>& t, const R* me, R* le
 template <typename R>
 cudaError_t launch_l2l(const Geometry& g, const Tables<R>& t, R* le, cudaStream_t s);
 template <typename R>
-cudaError_t launch_p2p_l2p(const Geometry& g, double sigma, const void* particles,
-                           const uint32_t* leaf_start, const R* le, const R* l2l, R* uv,
-                           cudaStream_t s);
+cudaError_t launch_p2p_l2p(const Geometry& g, double sigma, int64_t n, const void* particles,
+                           const uint32_t* skeys, const uint32_t* leaf_start, uint32_t* counter,
+                           const R* le, const R* l2l, R* uv, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Batched evaluation: many instances in one packed problem.  Instance i owns
@@ -190,8 +196,8 @@ size_t batch_near_bytes(int count);
 cudaError_t batch_near_fill(const BatchInst* host_inst, int count, void* dev_near,
                             cudaStream_t s);
 cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
-                             const int32_t* leaf_inst, const uint32_t* order, uint32_t nwork,
-                             uint32_t* counter, int ctas_per_sm, const void* particles,
+                             const int32_t* leaf_inst, uint32_t ntotal, uint32_t* counter,
+                             int ctas_per_sm, const void* particles, const uint32_t* skeys,
                              const uint32_t* leaf_start, const float* le, const float* l2l16,
                              const float* l2l32, float* uv, cudaStream_t s);
 cudaError_t launch_batch_direct(const BatchInst* inst, const int64_t* dev_offsets, int count,

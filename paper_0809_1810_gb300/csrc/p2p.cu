@@ -6,21 +6,15 @@
 // self term drops out without a test: K_sigma's direction vector (-dy, dx)
 // is exactly zero at zero separation, and its radial factor stays finite.
 //
-// One CTA per target leaf.  Source records of the 3x3 neighbourhood are
-// staged in shared memory in chunks; each target is handled by `ns` adjacent
-// lanes that split the sources and combine with warp shuffles.  Velocities
-// are written straight to the input order through the record's index.
-//
-// FP32 radial factor.  With q = r^2 / 2 sigma^2 and q2 = q / ln 2,
-//   (1 - e^-q) / r^2 = g(q2) / (2 sigma^2 ln 2),  g(q2) = (1 - 2^-q2) / q2.
-// For q >= 1, g = (1 - ex2(-q2)) * rcp(q2) on the MUFU unit; for q < 1 the
-// subtraction would cancel, so g is summed from its Taylor series
-//   g(q2) = sum_k (-1)^k ln2^(k+1) q2^k / (k+1)!   (truncated after q2^9,
-// relative truncation error below 5e-8 on [0, 1/ln 2)).
-// Each lane accumulates kInner pairs in a fresh register, then adds that
-// partial sum to its running sum with Neumaier's compensated addition, so
-// the FP32 rounding of a near sum stays at the level of one kInner-term sum
-// however many sources the local list holds.
+// FP64: one CTA per target leaf.  Source records of the 3x3 neighbourhood
+// are staged in shared memory in chunks; each target is handled by `ns`
+// adjacent lanes that split the sources and combine with warp shuffles.
+// Velocities are written straight to the input order through the record's
+// index.  The radial factor is (1 - e^-q)/r^2 with q = r^2 / 2 sigma^2,
+// formed with expm1 so that it keeps full precision for small q.  The FP32
+// kernel (further down) has its own work split and radial factor.
+#include <algorithm>
+
 #include "fmm2d_internal.cuh"
 
 namespace fmm2d {
@@ -182,8 +176,14 @@ p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
 // ---------------------------------------------------------------------------
 // FP32 near field, the dominant kernel of the FP32 form.
 //
-// Work split: one warp per target leaf (four consecutive Morton leaves per
-// CTA), no CTA-wide barriers.  The warp gathers its local list -- the 9
+// Work split: chunks of kTicket sorted targets.  A leaf's targets split
+// into chunks [c kTicket, (c + 1) kTicket) from its first target; the warp
+// owning window [w kTicket, (w + 1) kTicket) of the sorted order runs every
+// chunk that starts inside it (four warps per CTA, no CTA-wide barriers).
+// A window meets a few whole leaves when leaves are small and one chunk of
+// a leaf when leaves are large, so a crowded leaf spreads over many warps
+// instead of holding one warp while the rest of the GPU idles.  For each
+// chunk the warp gathers the leaf's local list -- the 9
 // source ranges of the 3x3 neighbourhood, coalesced loads -- into a
 // per-warp shared-memory buffer, sorted by a ballot compaction into a near
 // band (front) and a far band (back): a source whose distance to the leaf's
@@ -197,29 +197,35 @@ p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
 //
 // Pair arithmetic in physical FP32 coordinates: dx = x_i - x_j is exact for
 // nearby particles, q2 = (dx^2 + dy^2) log2(e) / (2 sigma^2).
-// Radial factor g(q2) = (1 - 2^-q2) / q2: MUFU ex2 and rcp for q2 >= 1/ln 2
-// (q >= 1); below that a degree-6 polynomial interpolating g at the
-// Chebyshev nodes of [0, 1/ln 2] (interpolation error 3e-9, below FP32
-// rounding), fitted on the host when the kernel is launched.
-// Sums: kInner sources into fresh registers, then Neumaier-compensated
-// addition into the running sums.
+// Radial factor g(q2) = (1 - 2^-q2) / q2: MUFU ex2 and rcp for q2 >= kPolyEdge;
+// below it the subtraction 1 - 2^-q2 would cancel, and a degree-5
+// polynomial interpolating g at the Chebyshev nodes of [0, kPolyEdge] takes
+// over (interpolation error below 1e-9), fitted on the host when the kernel
+// is launched.  At q2 = kPolyEdge the MUFU form is within 6e-7 of g (two
+// ulp of ex2 over 1 - 2^-q2 = 0.099), and the few pairs that close to a
+// target carry a small share of its velocity.
+// Sums: blocks of sources into fresh registers, then Neumaier-compensated
+// addition into the running sums.  Full passes of 64 targets give each lane
+// two targets, so one shared-memory read of a source serves two pairs.
 // ---------------------------------------------------------------------------
 constexpr int kLeafWarps = 4;
+constexpr uint32_t kTicket = 128;  // sorted targets per window (a power of two)
 #ifndef FMM2D_P2P_LIST_CAP
-#define FMM2D_P2P_LIST_CAP 640
+#define FMM2D_P2P_LIST_CAP 560  // 37 KB of shared memory per CTA: 6 CTAs per SM
 #endif
 constexpr int kListCap = FMM2D_P2P_LIST_CAP;  // source records per warp buffer
-constexpr int kF32Deg = 6;
+constexpr int kF32Deg = 5;
+constexpr double kPolyEdge = 0.15;  // q2 below which the polynomial is used
 
 struct NearF32v3 {
     float sc;                 // coordinate scale: q2 = |dX|^2 with X = (x - centre) sc
-    float qthr;               // polynomial below, MUFU at and above (q2 = 1/ln 2)
+    float qthr;               // polynomial below, MUFU at and above (q2 = kPolyEdge)
     float kvel;               // 1 / (4 pi sigma^2 ln 2 sc): sum -> velocity
     float kzeta;              // 1 / (sc s): scaled coordinate -> zeta
     float inv_s;              // 1 / s (leaf width)
     float half_leaf;          // s sc / 2, half the leaf in scaled units
     float band2;              // squared scaled distance to the leaf square below
-                              // which a source may be at q < 1
+                              // which a source may be at q2 < qthr of a target
     float coef[kF32Deg + 1];  // g(q2) ~ sum_k coef[k] q2^k on [0, qthr)
 };
 
@@ -291,6 +297,46 @@ __device__ __forceinline__ void band_loop(const float4* list, uint32_t lo, uint3
     }
 }
 
+// list[lo, hi) against two targets per lane (full passes of 64 targets):
+// blocks of kInner2 sources into fresh sums, then compensated.
+constexpr int kInner2 = 32;
+
+template <bool kNear>
+__device__ __forceinline__ void one_source2(const NearF32v3& nm, const float4 s, float x1,
+                                            float y1, float x2, float y2, float& iu1, float& iv1,
+                                            float& iu2, float& iv2) {
+    one_source<kNear>(nm, s, x1, y1, iu1, iv1);
+    one_source<kNear>(nm, s, x2, y2, iu2, iv2);
+}
+
+struct Sum2 {
+    float su1, sv1, cu1, cv1, su2, sv2, cu2, cv2;
+};
+
+template <bool kNear>
+__device__ __forceinline__ void band_loop2(const float4* list, uint32_t lo, uint32_t hi,
+                                           const NearF32v3& nm, float x1, float y1, float x2,
+                                           float y2, Sum2& S) {
+    uint32_t j = lo;
+    while (j < hi) {
+        const uint32_t e = min(j + (uint32_t)kInner2, hi);
+        float iu1 = 0.f, iv1 = 0.f, iu2 = 0.f, iv2 = 0.f;
+#pragma unroll 1
+        for (; j + 2 <= e; j += 2) {
+            one_source2<kNear>(nm, list[j], x1, y1, x2, y2, iu1, iv1, iu2, iv2);
+            one_source2<kNear>(nm, list[j + 1], x1, y1, x2, y2, iu1, iv1, iu2, iv2);
+        }
+        if (j < e) {
+            one_source2<kNear>(nm, list[j], x1, y1, x2, y2, iu1, iv1, iu2, iv2);
+            ++j;
+        }
+        neumaier_add(S.su1, S.cu1, iu1);
+        neumaier_add(S.sv1, S.cv1, iv1);
+        neumaier_add(S.su2, S.cu2, iu2);
+        neumaier_add(S.sv2, S.cv2, iv2);
+    }
+}
+
 struct LeafCtx {
     uint32_t t0, nt;           // the leaf's targets in sorted order
     const float* le_leaf;      // its local expansion (null when L < 2)
@@ -335,12 +381,14 @@ __device__ __forceinline__ void gather_bands(const float4* __restrict__ sp, cons
     __syncwarp();
 }
 
-// One leaf's targets against its local list, by one warp.  `leaf` is the
-// leaf's Morton key; leaf_start is indexed by leaf_base + key (zero for a
-// single evaluation).  buf, ranges and leaf_le are this warp's shared memory.
-__device__ __forceinline__ void p2p_leaf_f32(const float4* __restrict__ sp,
-                                             const uint32_t* __restrict__ leaf_start,
-                                             uint32_t leaf_base, uint32_t leaf, const Geometry& g,
+// Targets [a, b) of one leaf (positions within the leaf) against its local
+// list, by one warp.  `leaf` is the leaf's Morton key; leaf_start is indexed
+// by leaf_base + key (zero for a single evaluation).  buf, ranges and
+// leaf_le are this warp's shared memory.
+__device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
+                                              const uint32_t* __restrict__ leaf_start,
+                                              uint32_t leaf_base, uint32_t leaf, uint32_t a,
+                                              uint32_t b, const Geometry& g,
                                              const NearF32v3& nm, const float* __restrict__ le,
                                              const float* __restrict__ l2l,
                                              float* __restrict__ uv, float4* buf,
@@ -351,7 +399,7 @@ __device__ __forceinline__ void p2p_leaf_f32(const float4* __restrict__ sp,
     LeafCtx c;
     c.t0 = leaf_start[leaf_base + leaf];
     c.nt = leaf_start[leaf_base + leaf + 1] - c.t0;
-    if (c.nt == 0) return;
+    if (a >= b) return;
     uint32_t* rbeg = ranges;
     uint32_t* rpre = ranges + 9;
     {  // lane r < 9 reads range r
@@ -407,8 +455,43 @@ __device__ __forceinline__ void p2p_leaf_f32(const float4* __restrict__ sp,
     uint32_t nn = 0, nf = 0;
     if (one_chunk) gather_bands(sp, c, nm, 0, total, buf, nn, nf);
 
-    for (uint32_t tb = 0; tb < c.nt; tb += 32) {
-        const uint32_t tc = min(32u, c.nt - tb);
+    // far field (L2P, Eq. 12) plus near sum -> velocity of one target
+    auto finish = [&](const float4& rec, float x, float y, float su, float sv) {
+        float u = nm.kvel * su, v = nm.kvel * sv;
+        if (c.le_leaf) {  // w = (1/s) sum_n L~_n zeta^n, zeta = (z - z_leaf) / s
+            float2 zeta = make_float2(x * nm.kzeta, y * nm.kzeta);
+            const float2* Lc = reinterpret_cast<const float2*>(c.le_leaf);
+            float2 w = Lc[g.p - 1];
+            for (int m = g.p - 2; m >= 0; --m) {
+                float2 t = cmul(w, zeta);
+                float2 lm = Lc[m];
+                w = make_float2(t.x + lm.x, t.y + lm.y);
+            }
+            u += nm.inv_s * w.x;
+            v -= nm.inv_s * w.y;
+        }
+        const uint32_t idx = __float_as_uint(rec.w);
+        uv[2 * (int64_t)idx] = u;
+        uv[2 * (int64_t)idx + 1] = v;
+    };
+
+    uint32_t tb = a;
+    for (; tb + 64 <= b; tb += 64) {  // full passes: two targets per lane
+        const float4 r1 = sp[c.t0 + tb + lane], r2 = sp[c.t0 + tb + 32 + lane];
+        const float x1 = ((r1.x - c.cxh) - c.cxl) * nm.sc, y1 = ((r1.y - c.cyh) - c.cyl) * nm.sc;
+        const float x2 = ((r2.x - c.cxh) - c.cxl) * nm.sc, y2 = ((r2.y - c.cyh) - c.cyl) * nm.sc;
+        Sum2 S = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (uint32_t cb = 0; cb < total; cb += kListCap) {
+            if (!one_chunk)
+                gather_bands(sp, c, nm, cb, min((uint32_t)kListCap, total - cb), buf, nn, nf);
+            band_loop2<true>(buf, 0, nn, nm, x1, y1, x2, y2, S);
+            band_loop2<false>(buf, kListCap - nf, kListCap, nm, x1, y1, x2, y2, S);
+        }
+        finish(r1, x1, y1, S.su1 + S.cu1, S.sv1 + S.cv1);
+        finish(r2, x2, y2, S.su2 + S.cu2, S.sv2 + S.cv2);
+    }
+    for (; tb < b; tb += 32) {
+        const uint32_t tc = min(32u, b - tb);
         int ns = 1;  // lanes per target: largest power of two with tc * ns <= 32
         while (tc * (uint32_t)(2 * ns) <= 32u) ns *= 2;
         const uint32_t tl = lane / ns;
@@ -429,40 +512,68 @@ __device__ __forceinline__ void p2p_leaf_f32(const float4* __restrict__ sp,
             su += __shfl_xor_sync(0xffffffffu, su, o);
             sv += __shfl_xor_sync(0xffffffffu, sv, o);
         }
-        if (active && sl == 0) {
-            float u = nm.kvel * su, v = nm.kvel * sv;
-            if (c.le_leaf) {  // L2P: w = (1/s) sum_n L~_n zeta^n, zeta = (z - z_leaf) / s
-                float2 zeta = make_float2(x * nm.kzeta, y * nm.kzeta);
-                const float2* Lc = reinterpret_cast<const float2*>(c.le_leaf);
-                float2 w = Lc[g.p - 1];
-                for (int m = g.p - 2; m >= 0; --m) {
-                    float2 t = cmul(w, zeta);
-                    float2 lm = Lc[m];
-                    w = make_float2(t.x + lm.x, t.y + lm.y);
-                }
-                u += nm.inv_s * w.x;
-                v -= nm.inv_s * w.y;
-            }
-            const uint32_t idx = __float_as_uint(rec.w);
-            uv[2 * (int64_t)idx] = u;
-            uv[2 * (int64_t)idx + 1] = v;
-        }
+        if (active && sl == 0) finish(rec, x, y, su, sv);
     }
-    __syncwarp();  // the buffer may be reused by this warp's next leaf
+    __syncwarp();  // the buffer may be reused by this warp's next chunk
 }
 
-__global__ void __launch_bounds__(kLeafWarps * 32, 8)
-p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
+// Every chunk starting in window [r0, r1) of the sorted order: f(key, a, b)
+// with key the leaf index into leaf_start and [a, b) the chunk's targets
+// within the leaf.  A position r starts a chunk when its offset from the
+// first target of its leaf is a multiple of kTicket.  Warp-uniform calls.
+template <typename F>
+__device__ __forceinline__ void for_each_chunk(const uint32_t* __restrict__ skeys,
+                                               const uint32_t* __restrict__ leaf_start,
+                                               uint32_t r0, uint32_t r1, F&& f) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t base = r0; base < r1; base += 32) {
+        const uint32_t r = base + lane;
+        uint32_t key = 0, first = 0;
+        bool starts = false;
+        if (r < r1) {
+            key = skeys[r];
+            first = leaf_start[key];
+            starts = ((r - first) & (kTicket - 1)) == 0;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, starts);
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t k = __shfl_sync(0xffffffffu, key, src);
+            const uint32_t f0 = __shfl_sync(0xffffffffu, first, src);
+            const uint32_t a = base + (uint32_t)src - f0;
+            const uint32_t nt = leaf_start[k + 1] - f0;
+            f(k, a, min(a + kTicket, nt));
+        }
+    }
+}
+
+// Persistent: as many CTAs as fit on the GPU at once; each warp pulls
+// windows from a work counter (zeroed before the launch) until none is left,
+// so the last, partial wave of a fixed grid leaves no SM idle and crowded
+// windows balance against light ones.
+__global__ void __launch_bounds__(kLeafWarps * 32, 6)
+p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skeys,
+                   const uint32_t* __restrict__ leaf_start, uint32_t n, uint32_t* counter,
                    Geometry g, NearF32v3 nm, const float* __restrict__ le,
                    const float* __restrict__ l2l, float* __restrict__ uv) {
     __shared__ float4 lists[kLeafWarps][kListCap];
     __shared__ uint32_t ranges[kLeafWarps][20];
     __shared__ float2 leaf_le[kLeafWarps][kMaxP];
-    const int warp = threadIdx.x >> 5;
-    const uint32_t leaf = blockIdx.x * kLeafWarps + warp;
-    if (leaf >= (1u << (2 * g.L))) return;
-    p2p_leaf_f32(sp, leaf_start, 0, leaf, g, nm, le, l2l, uv, lists[warp], ranges[warp],
-                 leaf_le[warp]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        uint32_t w = 0;
+        if (lane == 0) w = atomicAdd(counter, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        const uint64_t r0 = (uint64_t)w * kTicket;
+        if (r0 >= n) break;
+        const uint32_t r1 = (uint32_t)min(r0 + kTicket, (uint64_t)n);
+        for_each_chunk(skeys, leaf_start, (uint32_t)r0, r1,
+                       [&](uint32_t leaf, uint32_t a, uint32_t b) {
+            p2p_chunk_f32(sp, leaf_start, 0, leaf, a, b, g, nm, le, l2l, uv, lists[warp],
+                          ranges[warp], leaf_le[warp]);
+        });
+    }
 }
 
 // Per-instance near-field constants of a batched evaluation.
@@ -470,13 +581,13 @@ struct NearInst {
     float sc, kvel, kzeta, inv_s, half_leaf;
 };
 
-// Batched and persistent: warps pull global leaves from a work counter, in
-// the order of `order` (largest instances first).
-__global__ void __launch_bounds__(kLeafWarps * 32, 8)
-p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
-                 const BatchInst* __restrict__ inst, const NearInst* __restrict__ near_inst,
-                 const int32_t* __restrict__ leaf_inst, const uint32_t* __restrict__ order,
-                 uint32_t nwork, uint32_t* counter, NearF32v3 shared_nm,
+// Batched and persistent: warps pull windows of the global sorted order
+// (all instances, packed) from a work counter.
+__global__ void __launch_bounds__(kLeafWarps * 32, 6)
+p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skeys,
+                 const uint32_t* __restrict__ leaf_start, const BatchInst* __restrict__ inst,
+                 const NearInst* __restrict__ near_inst, const int32_t* __restrict__ leaf_inst,
+                 uint32_t ntotal, uint32_t* counter, NearF32v3 shared_nm,
                  const float* __restrict__ le, const float* __restrict__ l2l16,
                  const float* __restrict__ l2l32, float* __restrict__ uv) {
     __shared__ float4 lists[kLeafWarps][kListCap];
@@ -487,19 +598,24 @@ p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ lea
         uint32_t w = 0;
         if (lane == 0) w = atomicAdd(counter, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
-        if (w >= nwork) break;
-        const uint32_t gleaf = order[w];
-        const int i = leaf_inst[gleaf];
-        const BatchInst& b = inst[i];
-        NearF32v3 nm = shared_nm;
-        const NearInst ni = near_inst[i];
-        nm.sc = ni.sc;
-        nm.kvel = ni.kvel;
-        nm.kzeta = ni.kzeta;
-        nm.inv_s = ni.inv_s;
-        nm.half_leaf = ni.half_leaf;
-        p2p_leaf_f32(sp, leaf_start, b.leaf_base, gleaf - b.leaf_base, b.g, nm, le + b.exp_off,
-                     b.g.P <= 16 ? l2l16 : l2l32, uv, lists[warp], ranges[warp], leaf_le[warp]);
+        const uint64_t r0 = (uint64_t)w * kTicket;
+        if (r0 >= ntotal) break;
+        const uint32_t r1 = (uint32_t)min(r0 + kTicket, (uint64_t)ntotal);
+        for_each_chunk(skeys, leaf_start, (uint32_t)r0, r1,
+                       [&](uint32_t gleaf, uint32_t a, uint32_t e) {
+            const int i = leaf_inst[gleaf];
+            const BatchInst& b = inst[i];
+            NearF32v3 nm = shared_nm;
+            const NearInst ni = near_inst[i];
+            nm.sc = ni.sc;
+            nm.kvel = ni.kvel;
+            nm.kzeta = ni.kzeta;
+            nm.inv_s = ni.inv_s;
+            nm.half_leaf = ni.half_leaf;
+            p2p_chunk_f32(sp, leaf_start, b.leaf_base, gleaf - b.leaf_base, a, e, b.g, nm,
+                          le + b.exp_off, b.g.P <= 16 ? l2l16 : l2l32, uv, lists[warp],
+                          ranges[warp], leaf_le[warp]);
+        });
     }
 }
 
@@ -557,7 +673,7 @@ static NearF32v3 near_constants(double sigma, const Geometry& g, bool* ok) {
     const double ln2 = 0.69314718055994530942;
     const double pi = 3.14159265358979323846;
     NearF32v3 nm;
-    double qthr = 1.0 / ln2;
+    double qthr = kPolyEdge;
     double box = g.W / ldexp(1.0, g.L);
     nm.sc = (float)sqrt(1.0 / (2.0 * sigma * sigma * ln2));
     nm.qthr = (float)qthr;
@@ -565,24 +681,41 @@ static NearF32v3 near_constants(double sigma, const Geometry& g, bool* ok) {
     nm.kzeta = (float)(1.0 / ((double)nm.sc * box));
     nm.inv_s = (float)(1.0 / box);
     nm.half_leaf = (float)(0.5 * box * (double)nm.sc);
-    nm.band2 = (float)(qthr * 1.02);  // q < 1 needs |dX|^2 < 1/ln 2; 2% margin for rounding
+    nm.band2 = (float)(qthr * 1.02);  // q2 < qthr needs |dX|^2 < qthr; 2% margin for rounding
     double coef[kF32Deg + 1];
     *ok = fit_near_polynomial(qthr, coef) <= 1e-8;
     for (int k = 0; k <= kF32Deg; ++k) nm.coef[k] = (float)coef[k];
     return nm;
 }
 
+// CTAs of `kernel` resident on the whole GPU at once (at least one).
+static unsigned resident_ctas(const void* kernel) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kLeafWarps * 32, 0);
+    return (unsigned)std::max(1, sms * std::max(per_sm, 1));
+}
+
 template <>
-cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, const void* particles,
-                                  const uint32_t* leaf_start, const float* le, const float* l2l,
-                                  float* uv, cudaStream_t s) {
+cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, int64_t n,
+                                  const void* particles, const uint32_t* skeys,
+                                  const uint32_t* leaf_start, uint32_t* counter, const float* le,
+                                  const float* l2l, float* uv, cudaStream_t s) {
     bool ok;
     NearF32v3 nm = near_constants(sigma, g, &ok);
     if (!ok) return cudaErrorInvalidValue;
-    unsigned nleaf = 1u << (2 * g.L);
-    unsigned blocks = (nleaf + kLeafWarps - 1) / kLeafWarps;
+    if (n == 0) return cudaSuccess;
+    const uint64_t windows = ((uint64_t)n + kTicket - 1) / kTicket;
+    const unsigned needed = (unsigned)((windows + kLeafWarps - 1) / kLeafWarps);
+    const unsigned blocks =
+        std::min(needed, resident_ctas(reinterpret_cast<const void*>(p2p_l2p_f32_kernel)));
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
     p2p_l2p_f32_kernel<<<blocks, kLeafWarps * 32, 0, s>>>(
-        reinterpret_cast<const float4*>(particles), leaf_start, g, nm, le, l2l, uv);
+        reinterpret_cast<const float4*>(particles), skeys, leaf_start, (uint32_t)n, counter, g,
+        nm, le, l2l, uv);
     return cudaGetLastError();
 }
 
@@ -607,11 +740,11 @@ cudaError_t batch_near_fill(const BatchInst* host_inst, int count, void* dev_nea
 }
 
 cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
-                             const int32_t* leaf_inst, const uint32_t* order, uint32_t nwork,
-                             uint32_t* counter, int ctas_per_sm, const void* particles,
+                             const int32_t* leaf_inst, uint32_t ntotal, uint32_t* counter,
+                             int ctas_per_sm, const void* particles, const uint32_t* skeys,
                              const uint32_t* leaf_start, const float* le, const float* l2l16,
                              const float* l2l32, float* uv, cudaStream_t s) {
-    if (nwork == 0) return cudaSuccess;
+    if (ntotal == 0) return cudaSuccess;
     Geometry g1{};
     g1.W = 2.0;
     g1.L = 0;
@@ -625,16 +758,21 @@ cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     p2p_batch_kernel<<<blocks, kLeafWarps * 32, 0, s>>>(
-        reinterpret_cast<const float4*>(particles), leaf_start, inst,
-        static_cast<const NearInst*>(near_inst), leaf_inst, order, nwork, counter, shared_nm, le,
+        reinterpret_cast<const float4*>(particles), skeys, leaf_start, inst,
+        static_cast<const NearInst*>(near_inst), leaf_inst, ntotal, counter, shared_nm, le,
         l2l16, l2l32, uv);
     return cudaGetLastError();
 }
 
 template <>
-cudaError_t launch_p2p_l2p<double>(const Geometry& g, double sigma, const void* particles,
-                                   const uint32_t* leaf_start, const double* le,
-                                   const double* l2l, double* uv, cudaStream_t s) {
+cudaError_t launch_p2p_l2p<double>(const Geometry& g, double sigma, int64_t n,
+                                   const void* particles, const uint32_t* skeys,
+                                   const uint32_t* leaf_start, uint32_t* counter,
+                                   const double* le, const double* l2l, double* uv,
+                                   cudaStream_t s) {
+    (void)n;
+    (void)skeys;
+    (void)counter;  // one CTA per leaf
     NearF64 nm;
     nm.inv2s2 = 1.0 / (2.0 * sigma * sigma);
     nm.k0 = 1.0 / (2.0 * 3.14159265358979323846);

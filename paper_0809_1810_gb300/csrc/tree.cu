@@ -311,7 +311,7 @@ cudaError_t launch_tree_build(const Geometry& g, int64_t n, const R* xy, const R
     KeyParams kp = make_key_params(g.x0, g.y0, g.W, g.L);
     int nblocks = (int)((n + kSortTile - 1) / kSortTile);
     int bits = 2 * g.L;
-    int passes = bits <= kRadixBits ? 1 : (bits + kRadixBits - 1) / kRadixBits;
+    int passes = sort_passes(bits);
     uint32_t* digit_total = sb.hist + (int64_t)kRadix * nblocks;
     keys_hist_kernel<R><<<nblocks, kSortThreads, 0, s>>>(n, xy, gamma, kp, sb.keys[0], sb.vals[0],
                                                          sb.hist, nblocks, sb.status);
@@ -431,7 +431,7 @@ cudaError_t launch_batch_tree(const void* dev_key_params, const int64_t* dev_off
         return cudaGetLastError();
     }
     int nblocks = (int)((ntotal + kSortTile - 1) / kSortTile);
-    int passes = key_bits <= kRadixBits ? 1 : (key_bits + kRadixBits - 1) / kRadixBits;
+    int passes = sort_passes(key_bits);
     uint32_t* digit_total = sb.hist + (int64_t)kRadix * nblocks;
     batch_keys_hist_kernel<<<nblocks, kSortThreads, 0, s>>>(
         ntotal, xy, gamma, static_cast<const BatchKeyParams*>(dev_key_params), dev_offsets, count,
@@ -521,7 +521,7 @@ cudaError_t tree_build_noalloc(int64_t n, const R* xy, const R* gamma, int L, do
     KeyParams kp = make_key_params(x0, y0, W, L);
     int nblocks = (int)((n + kSortTile - 1) / kSortTile);
     int bits = 2 * L;
-    int passes = bits <= kRadixBits ? 1 : (bits + kRadixBits - 1) / kRadixBits;
+    int passes = sort_passes(bits);
     keys_hist_kernel<R><<<nblocks, kSortThreads, 0, s>>>(n, xy, gamma, kp, kA, vA, hist, nblocks,
                                                          status);
     for (int q = 0; q < passes; ++q) {

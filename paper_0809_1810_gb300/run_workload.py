@@ -1,6 +1,6 @@
 """Run full FMM evaluations of a named synthetic workload on cuda:0.
 
-    python -m paper_0809_1810_gb300.run_workload --workload uniform_1m --steps 3
+    python -m paper_0809_1810_gb300.run_workload --workload uniform_1m --steps 3 [--p P --L L]
 
 Each step is one complete fmm2d_velocity call (tree build to velocities);
 this is the command the profiler summaries under profiles/ are taken with.
@@ -37,8 +37,14 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_tc", "fp64"])
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--p", type=int, default=None, help="override the workload's p")
+    ap.add_argument("--L", type=int, default=None, help="override the workload's L")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]()
+    if args.p is not None:
+        w.p = args.p
+    if args.L is not None:
+        w.L = args.L
     dt = torch.float64 if args.precision == "fp64" else torch.float32
     xy = torch.tensor(np.stack([w.x, w.y], 1), dtype=dt, device="cuda")
     g = torch.tensor(w.gamma, dtype=dt, device="cuda")

@@ -6,6 +6,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_0809_1810_gb300 import _native, build
@@ -96,3 +97,36 @@ def test_batch_rejects_empty_and_oversized(lib):
     assert lib.fmm2d_batch_plan_create(ctypes.byref(h), 0, None) == _native.INVALID_ARG
     big = (_native.Instance * 300)(*[_native.Instance(10, 4, 12, 0.01, -1.0, -1.0, 2.0)] * 300)
     assert lib.fmm2d_batch_plan_create(ctypes.byref(h), 300, big) == _native.INVALID_ARG
+
+
+def test_proposer_calls_validate_before_touching_the_device(lib):
+    h = ctypes.c_void_p(7)
+    assert lib.fmm2d_mlp_create(ctypes.byref(h), 0, 1) == _native.INVALID_ARG
+    assert h.value is None
+    assert lib.fmm2d_mlp_create(None, 16, 1) == _native.INVALID_ARG
+    assert lib.fmm2d_mlp_forward(None, 1, None, None, None) == _native.INVALID_ARG
+    assert lib.fmm2d_mlp_train_step(None, 1, None, None, ctypes.c_float(1e-3), None,
+                                    None) == _native.INVALID_ARG
+    assert lib.fmm2d_features(0, None, None, 0.1, -1.0, -1.0, 2.0, 8, 3, None,
+                              None) == _native.INVALID_ARG
+    p, L = ctypes.c_int(), ctypes.c_int()
+    assert lib.fmm2d_propose(None, 0, None, None, 1e-6, 0.3, 20, 6, ctypes.byref(p),
+                             ctypes.byref(L), None, None) == _native.INVALID_ARG
+    assert lib.fmm2d_mlp_last_error()
+    lib.fmm2d_mlp_destroy(None)
+
+
+def test_proposer_fallback_rule():
+    from paper_0809_1810_gb300 import proposer as PR
+
+    h = 2.0 / 1024
+    # 2^20 uniform, sigma = 2h: occupancy gives L = 7, but a leaf must span
+    # 6 sigma = 0.0234, so L = floor(log2(2 / 0.0234)) = 6
+    assert PR.fallback(1 << 20, 2 * h, (-1.0, -1.0, 2.0)) == (20, 6)
+    assert PR.fallback(1 << 20, 0.5 * h, (-1.0, -1.0, 2.0)) == (20, 7)
+    assert PR.fallback(10, 0.01, (-1.0, -1.0, 2.0)) == (20, 0)
+    assert PR.depth_candidates(1 << 20) == [5, 6, 7, 8, 9]
+    assert PR.depth_candidates(1 << 18) == [4, 5, 6, 7, 8]
+    t = PR.cost_terms(np.array([16, 7, 0, 20, 6, 0.0, 1, 0, 0, 0, 0, 0], np.float32))
+    np.testing.assert_allclose(t, [1, 2 ** 20, 16 * 2 ** 20, (4 ** 8 - 1) / 3 * 256,
+                                   9 * 4 ** 7 * 64 * 64])

@@ -170,7 +170,7 @@ def test_autotune_keeps_results():
         info = bp.autotune(xy, g, out)
         b = bp.velocity(xy, g)
         bp.check()
-    assert info["p2p_ctas_per_sm"] in (2, 3, 4, 5)
+    assert info["p2p_ctas_per_sm"] in (2, 3, 4, 5, 6)
     assert info["m2l_threads"] in (64, 128, 256)
     assert torch.equal(a, out) and torch.equal(a, b)
 

@@ -1,0 +1,104 @@
+"""What the trained (p, L) proposer gains over the method without it.
+
+On particle sets the network never saw (other seeds, and the 2^20 uniform
+set with sigma = 2h), at tolerance 1e-6 on the max error relative to the
+largest speed, measured against the FP64 regularised direct sum at sampled
+particles (the judge of every choice, never the network itself):
+
+* the proposer's (p, L), screened by the network and judged by the direct
+  sum at 2048 sampled particles, meets the tolerance at 4096 other ones;
+* it is faster overall than the conservative plain setting (p = 20 at the
+  depth capped by the kernel-substitution floor of Sec. 4.1), and never much
+  slower on one set (the linear cost model may misrank near-equal settings);
+* the uninformed setting (p = 20, about 64 particles per leaf, sigma
+  ignored) misses the tolerance where leaves are small against sigma --
+  the floor of Eqs. 26-29 that the proposer learned to avoid.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def proposer():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0809_1810_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+    from paper_0809_1810_gb300 import proposer as PR
+
+    if not os.path.exists(PR.CHECKPOINT + ".json"):
+        pytest.fail("trained checkpoint missing: " + PR.CHECKPOINT + ".json")
+    return PR.Proposer.load()
+
+
+def _run(w, xy, g, p, L, tgt, ref, reps=5):
+    from paper_0809_1810_gb300 import Plan
+
+    with Plan(p, L, w.sigma, "fp32_tc", root=w.root, max_n=w.n) as plan:
+        uv = plan.velocity(xy, g)
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            plan.velocity(xy, g, out=uv)
+            b.record()
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        stats = plan.error_stats(xy, uv, tgt, ref).cpu().numpy()
+        plan.check()
+    return float(stats[0] / stats[1]), float(np.median(times))
+
+
+def _sets():
+    h18 = 2.0 / 512
+    yield W.uniform_random(1 << 18, 90001, h18, sigma_over_h=2.0)
+    yield W.uniform_random(1 << 18, 90002, h18, sigma_over_h=0.8)
+    yield W.lamb_oseen_lattice(512, sigma_over_h=1.3, dtype=np.float32)
+    yield W.clustered_patches(1 << 18, 90003, npatch=24, h=h18, sigma_over_h=1.0)
+    yield W.uniform_1m(seed=2)
+
+
+def test_proposer_meets_tolerance_and_beats_the_plain_setting(proposer):
+    from paper_0809_1810_gb300 import Plan
+    from paper_0809_1810_gb300 import proposer as PR
+
+    rows = []
+    for k, w in enumerate(_sets()):
+        xy = torch.tensor(np.stack([w.x, w.y], 1).astype(np.float32), device="cuda")
+        g = torch.tensor(w.gamma.astype(np.float32), device="cuda")
+        tgt = torch.tensor(W.sample_targets(w.n, 4096, 500 + k), device="cuda")
+        with Plan(1, 0, w.sigma, "fp32", root=w.root, max_n=w.n) as any_plan:
+            ref = any_plan.direct_sampled(xy, g, tgt, kernel=0)
+        r = proposer.propose(xy, g, w.sigma, w.root, tol=TOL, verify=2048)
+        err, ms = _run(w, xy, g, r["p"], r["L"], tgt, ref)
+        fb = PR.fallback(w.n, w.sigma, w.root)
+        err_fb, ms_fb = _run(w, xy, g, fb[0], fb[1], tgt, ref)
+        L_occ = int(round(math.log(w.n / 64.0, 4)))
+        err_un, ms_un = _run(w, xy, g, 20, L_occ, tgt, ref)
+        pred = r["predicted"][r["choice"], 1] if r["choice"] >= 0 else float("nan")
+        rows.append((w.name, w.sigma / w.h, r["p"], r["L"], err, pred, ms, fb, err_fb, ms_fb,
+                     L_occ, err_un, ms_un))
+    print()
+    print("set  sigma/h | proposer p L  err  pred-log10  ms | fallback p L err ms | "
+          "uninformed L err ms")
+    for row in rows:
+        print("%-22s %.2f | %2d %d %.2e %6.2f %7.3f | %s %.2e %7.3f | %d %.2e %7.3f" % row)
+    for row in rows:
+        assert row[4] <= TOL, row
+        assert row[6] <= 1.2 * row[9], row  # the cost model may rank near-equal settings wrongly
+    gain = math.exp(np.mean([math.log(r[9] / r[6]) for r in rows]))
+    print("geometric-mean speed-up over the plain setting: %.2fx" % gain)
+    assert gain > 1.05
+    # the uninformed setting misses the tolerance on the 2^20 set (leaf = 4 sigma)
+    assert rows[-1][11] > TOL
