@@ -51,6 +51,25 @@ FLUSH_BYTES = 512 << 20  # > 129 MB L2
 P2P_FLOPS_PER_PAIR = 20  # algorithmic work per near pair
 
 
+# DRAM traffic of one near-field launch (dram__bytes_read.sum +
+# dram__bytes_write.sum) from the ncu capture summarised in
+# profiles/p2p_l2p_f32_uniform_1m_p15_L6.md; reported only while the kernel
+# source is the one captured and the setting matches.
+P2P_TRAFFIC = {"sha256_p2p_cu": "d7d71da744a4a0fa9c0cdfe073332f84967fdfca0f4bd56331169e3514cb2dd9", "p": 15, "L": 6,
+               "bytes": 21738240}
+
+
+def p2p_traffic(p, L):
+    import hashlib
+
+    if P2P_TRAFFIC["bytes"] is None or (p, L) != (P2P_TRAFFIC["p"], P2P_TRAFFIC["L"]):
+        return None
+    src = os.path.join(ROOT, "paper_0809_1810_gb300", "csrc", "p2p.cu")
+    with open(src, "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()
+    return P2P_TRAFFIC["bytes"] if digest == P2P_TRAFFIC["sha256_p2p_cu"] else None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -295,6 +314,36 @@ def run_batch_sweep(torch, dev, flush, rank, pg, steps=10):
             "precision": "fp32 (M2L on CUDA cores)"}
 
 
+def run_clustered(torch, dev, flush, steps=5):
+    """The large clustered workload: N = 2^24 from 64 Gaussian patches,
+    sigma = h = 2/4096, p = 20, L = 9 (leaves span 8 sigma), FP32_TC; its
+    error against the FP64 direct sum at 16384 seeded particles."""
+    from paper_0809_1810_gb300 import Plan
+
+    w = W.clustered_16m()
+    n = w.n
+    xy = torch.tensor(np.stack([w.x, w.y], 1), dtype=torch.float32, device=dev)
+    g = torch.tensor(w.gamma, dtype=torch.float32, device=dev)
+    uv = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    with Plan(w.p, w.L, w.sigma, "fp32_tc", root=w.root, max_n=n) as plan:
+        plan.set_timing(steps)
+        for _ in range(3):
+            plan.velocity(xy, g, out=uv)
+        plan.check()
+        ms = float(np.mean(_time_steps(torch, plan, xy, g, uv, steps, flush)))
+        phases = [plan.phase_ms(a) for a in range(steps)]
+        t = torch.tensor(W.sample_targets(n, 16384, 4321), device=dev)
+        ref = plan.direct_sampled(xy, g, t, kernel=0)
+        st = plan.error_stats(xy, uv, t, ref).cpu().numpy()
+        plan.check()
+    return {"workload": "clustered_16m: N=2^24, 64 Gaussian patches (std 0.02-0.2), signed "
+                        "patch circulations h^2 N(0,1), sigma=h=2/4096, p=20, L=9, fp32_tc",
+            "value": n / (ms * 1e-3), "unit": "particles/s", "ms_per_step": ms, "steps": steps,
+            "phase_ms": {k: float(np.mean([q[k] for q in phases])) for k in phases[0]},
+            "max_rel_err_vs_fp64_direct": float(st[0] / st[1]), "targets": 16384,
+            "meets_tolerance": bool(st[0] / st[1] <= TOL)}
+
+
 def choose_setting(args, w, xy, g):
     """(p, L, info): the trained proposer's choice for tolerance TOL (the
     default), the workload's configured setting, or the plain fallback."""
@@ -417,7 +466,8 @@ def run_ours(args):
                        f"16 MUFU lanes / 2 ops) per SM per clock x 152 SMs x "
                        f"{sm_max:.0f} MHz ({peak_kind} sm_max_mhz)",
         "pairs_per_launch": pairs, "avg_launch_ms": p2p_ms,
-        "traffic": None,
+        "traffic": p2p_traffic(p, L),
+        "traffic_unit": "bytes per launch (ncu DRAM read + write)",
         "phase_ms": phase_avg,
     }
 
@@ -472,6 +522,7 @@ def run_ours(args):
                   "speedup_of_value": fp64_ms / ms_per_step}
 
     batch = None if args.no_batch else run_batch_sweep(torch, dev, flush, rank, pg)
+    large = None if args.no_large else run_clustered(torch, dev, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -492,6 +543,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "accuracy": accuracy, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "as_configured": configured, "plain_fp64": plain_fp64, "batch_sweep": batch,
+            "clustered_16m": large,
             "gpu_launches": int(launches_per_step * args.steps),
             "launches_per_step": launches_per_step, "clocks": clk,
         }))
@@ -508,6 +560,8 @@ def main():
     ap.add_argument("--precision", default="fp32_tc", choices=["fp32", "fp32_tc", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep line item")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 2^24-particle clustered line item")
     ap.add_argument("--setting", default="proposer", choices=["proposer", "configured", "fallback"],
                     help="(p, L): the trained proposer's choice for 1e-6 (default), the "
                          "workload's stated p=16, L=7, or the plain fallback")

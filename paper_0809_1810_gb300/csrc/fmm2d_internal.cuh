@@ -259,9 +259,14 @@ __host__ __device__ inline T cmake(decltype(T().x) re, decltype(T().x) im) {
     r.y = im;
     return r;
 }
+// Products the compiler may not fuse into a neighbouring addition: with the
+// fused steps spelled out, every kernel that inlines a routine rounds it the
+// same way (batched and single evaluations agree bit for bit).
+__device__ inline float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ inline double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 template <typename T>
 __device__ inline T cmul(T a, T b) {
-    return cmake<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return cmake<T>(fma(a.x, b.x, -mul_rn(a.y, b.y)), fma(a.x, b.y, mul_rn(a.y, b.x)));
 }
 // acc + a * b
 template <typename T>

@@ -14,6 +14,7 @@
 // formed with expm1 so that it keeps full precision for small q.  The FP32
 // kernel (further down) has its own work split and radial factor.
 #include <algorithm>
+#include <type_traits>
 
 #include "fmm2d_internal.cuh"
 
@@ -205,8 +206,10 @@ p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
 // ulp of ex2 over 1 - 2^-q2 = 0.099), and the few pairs that close to a
 // target carry a small share of its velocity.
 // Sums: blocks of sources into fresh registers, then Neumaier-compensated
-// addition into the running sums.  Full passes of 64 targets give each lane
-// two targets, so one shared-memory read of a source serves two pairs.
+// addition into the running sums.  A whole chunk (128 targets) gives each
+// lane four targets and gathers each part of the local list once; full
+// passes of 64 targets give each lane two; one shared-memory read of a
+// source serves that many pairs.
 // ---------------------------------------------------------------------------
 constexpr int kLeafWarps = 4;
 constexpr uint32_t kTicket = 128;  // sorted targets per window (a power of two)
@@ -249,91 +252,75 @@ __device__ __forceinline__ void one_source(const NearF32v3& nm, const float4 s, 
     iv = fmaf(dx, w, iv);
 }
 
-// list[lo, hi) against the lane's target, ns lanes per target (sl = this
-// lane's slot): blocks of kInner sources into fresh sums, then compensated.
+// list[lo, hi) against the lane's target when ns > 1 lanes share a target
+// (sl = this lane's slot; a leaf's last round of at most 16 targets): blocks
+// of kInner sources into fresh sums, then compensated.
 template <bool kNear>
-__device__ __forceinline__ void band_loop(const float4* list, uint32_t lo, uint32_t hi, int ns,
-                                          int sl, const NearF32v3& nm, float x, float y,
-                                          float& su, float& sv, float& cu, float& cv) {
-    if (ns == 1) {
-        uint32_t j = lo;
-        for (; j + kInner <= hi; j += kInner) {
-            float iu = 0.f, iv = 0.f;
+__device__ __forceinline__ void band_loop_split(const float4* list, uint32_t lo, uint32_t hi,
+                                                int ns, int sl, const NearF32v3& nm, float x,
+                                                float y, float& su, float& sv, float& cu,
+                                                float& cv) {
+    float iu = 0.f, iv = 0.f;
+    int cnt = 0;
 #pragma unroll 1
-            for (int q = 0; q < kInner; q += 4) {
-                one_source<kNear>(nm, list[j + q], x, y, iu, iv);
-                one_source<kNear>(nm, list[j + q + 1], x, y, iu, iv);
-                one_source<kNear>(nm, list[j + q + 2], x, y, iu, iv);
-                one_source<kNear>(nm, list[j + q + 3], x, y, iu, iv);
-            }
+    for (uint32_t jj = lo; jj < hi; jj += ns) {
+        const uint32_t j = jj + sl;
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);  // past the end: zero circulation
+        if (j < hi) r = list[j];
+        one_source<kNear>(nm, r, x, y, iu, iv);
+        if (++cnt == kInner) {
             neumaier_add(su, cu, iu);
             neumaier_add(sv, cv, iv);
+            iu = iv = 0.f;
+            cnt = 0;
         }
-        if (j < hi) {
-            float iu = 0.f, iv = 0.f;
-#pragma unroll 1
-            for (; j < hi; ++j) one_source<kNear>(nm, list[j], x, y, iu, iv);
-            neumaier_add(su, cu, iu);
-            neumaier_add(sv, cv, iv);
-        }
-    } else {
-        float iu = 0.f, iv = 0.f;
-        int cnt = 0;
-#pragma unroll 1
-        for (uint32_t jj = lo; jj < hi; jj += ns) {
-            const uint32_t j = jj + sl;
-            float4 r = make_float4(0.f, 0.f, 0.f, 0.f);  // past the end: zero circulation
-            if (j < hi) r = list[j];
-            one_source<kNear>(nm, r, x, y, iu, iv);
-            if (++cnt == kInner) {
-                neumaier_add(su, cu, iu);
-                neumaier_add(sv, cv, iv);
-                iu = iv = 0.f;
-                cnt = 0;
-            }
-        }
-        neumaier_add(su, cu, iu);
-        neumaier_add(sv, cv, iv);
     }
+    neumaier_add(su, cu, iu);
+    neumaier_add(sv, cv, iv);
 }
 
-// list[lo, hi) against two targets per lane (full passes of 64 targets):
-// blocks of kInner2 sources into fresh sums, then compensated.
-constexpr int kInner2 = 32;
+// list[lo, hi) against T targets per lane (passes of 32 T targets):
+// blocks of kInnerT sources into fresh sums, then compensated.  One
+// shared-memory read of a source serves T pairs.  Each target sees the same
+// sequence of operations whatever T is, so a target's velocity does not
+// depend on how its rounds were grouped into passes.
+constexpr int kInnerT = 32;
 
-template <bool kNear>
-__device__ __forceinline__ void one_source2(const NearF32v3& nm, const float4 s, float x1,
-                                            float y1, float x2, float y2, float& iu1, float& iv1,
-                                            float& iu2, float& iv2) {
-    one_source<kNear>(nm, s, x1, y1, iu1, iv1);
-    one_source<kNear>(nm, s, x2, y2, iu2, iv2);
-}
-
-struct Sum2 {
-    float su1, sv1, cu1, cv1, su2, sv2, cu2, cv2;
+template <int T>
+struct SumT {
+    float su[T], sv[T], cu[T], cv[T];
 };
 
-template <bool kNear>
-__device__ __forceinline__ void band_loop2(const float4* list, uint32_t lo, uint32_t hi,
-                                           const NearF32v3& nm, float x1, float y1, float x2,
-                                           float y2, Sum2& S) {
+template <bool kNear, int T>
+__device__ __forceinline__ void band_loopT(const float4* list, uint32_t lo, uint32_t hi,
+                                           const NearF32v3& nm, const float (&x)[T],
+                                           const float (&y)[T], SumT<T>& S) {
+    constexpr int kUnroll = 4 / T;  // sources per iteration: four pairs in flight
     uint32_t j = lo;
     while (j < hi) {
-        const uint32_t e = min(j + (uint32_t)kInner2, hi);
-        float iu1 = 0.f, iv1 = 0.f, iu2 = 0.f, iv2 = 0.f;
+        const uint32_t e = min(j + (uint32_t)kInnerT, hi);
+        float iu[T], iv[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) iu[t] = iv[t] = 0.f;
 #pragma unroll 1
-        for (; j + 2 <= e; j += 2) {
-            one_source2<kNear>(nm, list[j], x1, y1, x2, y2, iu1, iv1, iu2, iv2);
-            one_source2<kNear>(nm, list[j + 1], x1, y1, x2, y2, iu1, iv1, iu2, iv2);
+        for (; j + kUnroll <= e; j += kUnroll) {
+#pragma unroll
+            for (int q = 0; q < kUnroll; ++q) {
+                const float4 src = list[j + q];
+#pragma unroll
+                for (int t = 0; t < T; ++t) one_source<kNear>(nm, src, x[t], y[t], iu[t], iv[t]);
+            }
         }
-        if (j < e) {
-            one_source2<kNear>(nm, list[j], x1, y1, x2, y2, iu1, iv1, iu2, iv2);
-            ++j;
+        for (; j < e; ++j) {
+            const float4 src = list[j];
+#pragma unroll
+            for (int t = 0; t < T; ++t) one_source<kNear>(nm, src, x[t], y[t], iu[t], iv[t]);
         }
-        neumaier_add(S.su1, S.cu1, iu1);
-        neumaier_add(S.sv1, S.cv1, iv1);
-        neumaier_add(S.su2, S.cu2, iu2);
-        neumaier_add(S.sv2, S.cv2, iv2);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            neumaier_add(S.su[t], S.cu[t], iu[t]);
+            neumaier_add(S.sv[t], S.cv[t], iv[t]);
+        }
     }
 }
 
@@ -457,7 +444,7 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
 
     // far field (L2P, Eq. 12) plus near sum -> velocity of one target
     auto finish = [&](const float4& rec, float x, float y, float su, float sv) {
-        float u = nm.kvel * su, v = nm.kvel * sv;
+        float u = __fmul_rn(nm.kvel, su), v = __fmul_rn(nm.kvel, sv);
         if (c.le_leaf) {  // w = (1/s) sum_n L~_n zeta^n, zeta = (z - z_leaf) / s
             float2 zeta = make_float2(x * nm.kzeta, y * nm.kzeta);
             const float2* Lc = reinterpret_cast<const float2*>(c.le_leaf);
@@ -467,32 +454,51 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
                 float2 lm = Lc[m];
                 w = make_float2(t.x + lm.x, t.y + lm.y);
             }
-            u += nm.inv_s * w.x;
-            v -= nm.inv_s * w.y;
+            u = fmaf(nm.inv_s, w.x, u);
+            v = fmaf(-nm.inv_s, w.y, v);
         }
         const uint32_t idx = __float_as_uint(rec.w);
         uv[2 * (int64_t)idx] = u;
         uv[2 * (int64_t)idx + 1] = v;
     };
 
-    uint32_t tb = a;
-    for (; tb + 64 <= b; tb += 64) {  // full passes: two targets per lane
-        const float4 r1 = sp[c.t0 + tb + lane], r2 = sp[c.t0 + tb + 32 + lane];
-        const float x1 = ((r1.x - c.cxh) - c.cxl) * nm.sc, y1 = ((r1.y - c.cyh) - c.cyl) * nm.sc;
-        const float x2 = ((r2.x - c.cxh) - c.cxl) * nm.sc, y2 = ((r2.y - c.cyh) - c.cyl) * nm.sc;
-        Sum2 S = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    // passes of 32 T targets, T per lane (targets tb + lane + 32 t); in a
+    // leaf's last round fewer than 32 targets may be active
+    auto pass = [&](auto tag, uint32_t tb, uint32_t active) {
+        constexpr int T = decltype(tag)::value;
+        float4 rec[T];
+        float x[T], y[T];
+        SumT<T> S;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const uint32_t k = 32 * t + lane;
+            rec[t] = sp[c.t0 + tb + (k < active ? k : 0)];
+            x[t] = ((rec[t].x - c.cxh) - c.cxl) * nm.sc;
+            y[t] = ((rec[t].y - c.cyh) - c.cyl) * nm.sc;
+            S.su[t] = S.sv[t] = S.cu[t] = S.cv[t] = 0.f;
+        }
         for (uint32_t cb = 0; cb < total; cb += kListCap) {
             if (!one_chunk)
                 gather_bands(sp, c, nm, cb, min((uint32_t)kListCap, total - cb), buf, nn, nf);
-            band_loop2<true>(buf, 0, nn, nm, x1, y1, x2, y2, S);
-            band_loop2<false>(buf, kListCap - nf, kListCap, nm, x1, y1, x2, y2, S);
+            band_loopT<true, T>(buf, 0, nn, nm, x, y, S);
+            band_loopT<false, T>(buf, kListCap - nf, kListCap, nm, x, y, S);
         }
-        finish(r1, x1, y1, S.su1 + S.cu1, S.sv1 + S.cv1);
-        finish(r2, x2, y2, S.su2 + S.cu2, S.sv2 + S.cv2);
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+            if (32 * t + lane < active)
+                finish(rec[t], x[t], y[t], S.su[t] + S.cu[t], S.sv[t] + S.cv[t]);
+    };
+    uint32_t tb = a;
+    if (b - tb == kTicket) {  // a whole chunk: four targets per lane, the list gathered once
+        pass(std::integral_constant<int, 4>{}, tb, kTicket);
+        tb = b;
     }
-    for (; tb < b; tb += 32) {
-        const uint32_t tc = min(32u, b - tb);
-        int ns = 1;  // lanes per target: largest power of two with tc * ns <= 32
+    for (; tb + 64 <= b; tb += 64) pass(std::integral_constant<int, 2>{}, tb, 64u);
+    for (; tb + 16 < b; tb += 32)  // rounds of 17..32 targets, one per lane
+        pass(std::integral_constant<int, 1>{}, tb, min(32u, b - tb));
+    if (tb < b) {  // a leaf's last round of at most 16 targets: ns lanes per target
+        const uint32_t tc = b - tb;
+        int ns = 2;  // lanes per target: largest power of two with tc * ns <= 32
         while (tc * (uint32_t)(2 * ns) <= 32u) ns *= 2;
         const uint32_t tl = lane / ns;
         const int sl = lane % ns;
@@ -503,8 +509,9 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
         for (uint32_t cb = 0; cb < total; cb += kListCap) {
             if (!one_chunk)
                 gather_bands(sp, c, nm, cb, min((uint32_t)kListCap, total - cb), buf, nn, nf);
-            band_loop<true>(buf, 0, nn, ns, sl, nm, x, y, su, sv, cu, cv);
-            band_loop<false>(buf, kListCap - nf, kListCap, ns, sl, nm, x, y, su, sv, cu, cv);
+            band_loop_split<true>(buf, 0, nn, ns, sl, nm, x, y, su, sv, cu, cv);
+            band_loop_split<false>(buf, kListCap - nf, kListCap, ns, sl, nm, x, y, su, sv, cu,
+                                   cv);
         }
         su += cu;
         sv += cv;
@@ -517,15 +524,41 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
     __syncwarp();  // the buffer may be reused by this warp's next chunk
 }
 
-// Every chunk starting in window [r0, r1) of the sorted order: f(key, a, b)
-// with key the leaf index into leaf_start and [a, b) the chunk's targets
-// within the leaf.  A position r starts a chunk when its offset from the
-// first target of its leaf is a multiple of kTicket.  Warp-uniform calls.
+// Work items of one near-field pass over n sorted targets.  Items
+// [0, nbig) are windows of kTicket positions, [0, nbig kTicket); the rest are
+// windows of 32 positions covering [nbig kTicket, n).  A big window runs every
+// chunk (kTicket targets from a multiple of kTicket past its leaf's first
+// target) that starts inside it; a small window runs every round (32
+// targets from a multiple of 32 past the leaf's first target) that starts
+// inside it and whose chunk starts at or after nbig kTicket (earlier chunks
+// are a big window's).  Small items at the end keep the last warps' work
+// short; the split changes only how rounds are grouped, not a target's
+// arithmetic.
+struct WorkSplit {
+    uint32_t n, nbig, items;
+};
+
+// The small items cover about half a window per resident warp (the spread
+// of the warps' finishing times), at most a quarter of the windows.
+static WorkSplit work_split(uint64_t n, uint64_t warps) {
+    const uint64_t windows = (n + kTicket - 1) / kTicket;
+    const uint64_t nbig = windows - std::min(windows / 4, warps / 2 + 1);
+    const uint64_t rest = n - std::min<uint64_t>(n, nbig * kTicket);
+    return WorkSplit{(uint32_t)n, (uint32_t)nbig, (uint32_t)(nbig + (rest + 31) / 32)};
+}
+
+// f(key, a, b) for every chunk or round that item w owns: key the leaf index
+// into leaf_start, [a, b) its targets within the leaf.  Warp-uniform calls.
 template <typename F>
-__device__ __forceinline__ void for_each_chunk(const uint32_t* __restrict__ skeys,
+__device__ __forceinline__ void for_each_piece(const uint32_t* __restrict__ skeys,
                                                const uint32_t* __restrict__ leaf_start,
-                                               uint32_t r0, uint32_t r1, F&& f) {
+                                               const WorkSplit& ws, uint32_t w, F&& f) {
     const int lane = threadIdx.x & 31;
+    const bool big = w < ws.nbig;
+    const uint32_t split = ws.nbig * kTicket;
+    const uint32_t r0 = big ? w * kTicket : split + (w - ws.nbig) * 32u;
+    const uint32_t r1 = min(r0 + (big ? kTicket : 32u), ws.n);
+    const uint32_t span = big ? kTicket : 32u;
     for (uint32_t base = r0; base < r1; base += 32) {
         const uint32_t r = base + lane;
         uint32_t key = 0, first = 0;
@@ -533,7 +566,9 @@ __device__ __forceinline__ void for_each_chunk(const uint32_t* __restrict__ skey
         if (r < r1) {
             key = skeys[r];
             first = leaf_start[key];
-            starts = ((r - first) & (kTicket - 1)) == 0;
+            const uint32_t off = r - first;
+            starts = (off & (span - 1)) == 0 &&
+                     (big || first + (off & ~(kTicket - 1)) >= split);
         }
         unsigned m = __ballot_sync(0xffffffffu, starts);
         while (m) {
@@ -543,18 +578,18 @@ __device__ __forceinline__ void for_each_chunk(const uint32_t* __restrict__ skey
             const uint32_t f0 = __shfl_sync(0xffffffffu, first, src);
             const uint32_t a = base + (uint32_t)src - f0;
             const uint32_t nt = leaf_start[k + 1] - f0;
-            f(k, a, min(a + kTicket, nt));
+            f(k, a, min(a + span, nt));
         }
     }
 }
 
-// Persistent: as many CTAs as fit on the GPU at once; each warp pulls
-// windows from a work counter (zeroed before the launch) until none is left,
-// so the last, partial wave of a fixed grid leaves no SM idle and crowded
-// windows balance against light ones.
+// Persistent: as many CTAs as fit on the GPU at once; each warp pulls work
+// items from a counter (zeroed before the launch) until none is left, so
+// crowded windows balance against light ones and no SM idles behind a
+// partial last wave.
 __global__ void __launch_bounds__(kLeafWarps * 32, 6)
 p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skeys,
-                   const uint32_t* __restrict__ leaf_start, uint32_t n, uint32_t* counter,
+                   const uint32_t* __restrict__ leaf_start, WorkSplit ws, uint32_t* counter,
                    Geometry g, NearF32v3 nm, const float* __restrict__ le,
                    const float* __restrict__ l2l, float* __restrict__ uv) {
     __shared__ float4 lists[kLeafWarps][kListCap];
@@ -565,11 +600,8 @@ p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ s
         uint32_t w = 0;
         if (lane == 0) w = atomicAdd(counter, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
-        const uint64_t r0 = (uint64_t)w * kTicket;
-        if (r0 >= n) break;
-        const uint32_t r1 = (uint32_t)min(r0 + kTicket, (uint64_t)n);
-        for_each_chunk(skeys, leaf_start, (uint32_t)r0, r1,
-                       [&](uint32_t leaf, uint32_t a, uint32_t b) {
+        if (w >= ws.items) break;
+        for_each_piece(skeys, leaf_start, ws, w, [&](uint32_t leaf, uint32_t a, uint32_t b) {
             p2p_chunk_f32(sp, leaf_start, 0, leaf, a, b, g, nm, le, l2l, uv, lists[warp],
                           ranges[warp], leaf_le[warp]);
         });
@@ -581,13 +613,13 @@ struct NearInst {
     float sc, kvel, kzeta, inv_s, half_leaf;
 };
 
-// Batched and persistent: warps pull windows of the global sorted order
+// Batched and persistent: warps pull work items over the global sorted order
 // (all instances, packed) from a work counter.
 __global__ void __launch_bounds__(kLeafWarps * 32, 6)
 p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skeys,
                  const uint32_t* __restrict__ leaf_start, const BatchInst* __restrict__ inst,
                  const NearInst* __restrict__ near_inst, const int32_t* __restrict__ leaf_inst,
-                 uint32_t ntotal, uint32_t* counter, NearF32v3 shared_nm,
+                 WorkSplit ws, uint32_t* counter, NearF32v3 shared_nm,
                  const float* __restrict__ le, const float* __restrict__ l2l16,
                  const float* __restrict__ l2l32, float* __restrict__ uv) {
     __shared__ float4 lists[kLeafWarps][kListCap];
@@ -598,11 +630,8 @@ p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ ske
         uint32_t w = 0;
         if (lane == 0) w = atomicAdd(counter, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
-        const uint64_t r0 = (uint64_t)w * kTicket;
-        if (r0 >= ntotal) break;
-        const uint32_t r1 = (uint32_t)min(r0 + kTicket, (uint64_t)ntotal);
-        for_each_chunk(skeys, leaf_start, (uint32_t)r0, r1,
-                       [&](uint32_t gleaf, uint32_t a, uint32_t e) {
+        if (w >= ws.items) break;
+        for_each_piece(skeys, leaf_start, ws, w, [&](uint32_t gleaf, uint32_t a, uint32_t e) {
             const int i = leaf_inst[gleaf];
             const BatchInst& b = inst[i];
             NearF32v3 nm = shared_nm;
@@ -707,15 +736,15 @@ cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, int64_t n,
     NearF32v3 nm = near_constants(sigma, g, &ok);
     if (!ok) return cudaErrorInvalidValue;
     if (n == 0) return cudaSuccess;
-    const uint64_t windows = ((uint64_t)n + kTicket - 1) / kTicket;
-    const unsigned needed = (unsigned)((windows + kLeafWarps - 1) / kLeafWarps);
-    const unsigned blocks =
-        std::min(needed, resident_ctas(reinterpret_cast<const void*>(p2p_l2p_f32_kernel)));
+    const unsigned resident = resident_ctas(reinterpret_cast<const void*>(p2p_l2p_f32_kernel));
+    const WorkSplit ws = work_split((uint64_t)n, (uint64_t)resident * kLeafWarps);
+    const unsigned needed = (ws.items + kLeafWarps - 1) / kLeafWarps;
+    const unsigned blocks = std::min(needed, resident);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     p2p_l2p_f32_kernel<<<blocks, kLeafWarps * 32, 0, s>>>(
-        reinterpret_cast<const float4*>(particles), skeys, leaf_start, (uint32_t)n, counter, g,
-        nm, le, l2l, uv);
+        reinterpret_cast<const float4*>(particles), skeys, leaf_start, ws, counter, g, nm, le,
+        l2l, uv);
     return cudaGetLastError();
 }
 
@@ -759,8 +788,9 @@ cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
     if (e != cudaSuccess) return e;
     p2p_batch_kernel<<<blocks, kLeafWarps * 32, 0, s>>>(
         reinterpret_cast<const float4*>(particles), skeys, leaf_start, inst,
-        static_cast<const NearInst*>(near_inst), leaf_inst, ntotal, counter, shared_nm, le,
-        l2l16, l2l32, uv);
+        static_cast<const NearInst*>(near_inst), leaf_inst,
+        work_split(ntotal, (uint64_t)blocks * kLeafWarps), counter,
+        shared_nm, le, l2l16, l2l32, uv);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--p", type=int, default=None, help="override the workload's p")
     ap.add_argument("--L", type=int, default=None, help="override the workload's L")
+    ap.add_argument("--phases", action="store_true",
+                    help="also print the mean per-phase times (events inside the graph)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]()
     if args.p is not None:
@@ -50,6 +52,8 @@ def main():
     g = torch.tensor(w.gamma, dtype=dt, device="cuda")
     uv = torch.empty((w.n, 2), dtype=dt, device="cuda")
     with Plan(w.p, w.L, w.sigma, args.precision, root=w.root, max_n=w.n) as plan:
+        if args.phases:
+            plan.set_timing(max(args.steps, 1))
         for _ in range(args.warmup):
             plan.velocity(xy, g, out=uv)
         plan.check()
@@ -63,6 +67,10 @@ def main():
         print(f"{args.workload} {args.precision}: n={w.n} p={w.p} L={w.L} "
               f"{a.elapsed_time(b) / max(args.steps, 1):.4f} ms/step, "
               f"{plan.kernels_per_call()} kernels/step")
+        if args.phases:
+            ph = [plan.phase_ms(a) for a in range(max(args.steps, 1))]
+            print("  phases (ms): " + ", ".join(
+                f"{k} {np.mean([q[k] for q in ph]):.4f}" for k in ph[0]))
 
 
 if __name__ == "__main__":

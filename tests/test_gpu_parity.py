@@ -51,6 +51,11 @@ def _rel(a, b):
     return np.abs(a - b).max() / scale if scale > 0 else np.abs(a - b).max()
 
 
+def _rel_speed(uv, ref):
+    """The error metric of Sec. 5.1: max_i |du_i| / max_i |u_ref,i| (2-norms)."""
+    return np.linalg.norm(uv - ref, axis=1).max() / np.linalg.norm(ref, axis=1).max()
+
+
 def _edge_lattice(L, m=7):
     """Points exactly on leaf edges and on the root's upper edge."""
     k = np.arange(0, (1 << L) + 1, max(1, (1 << L) // m))
@@ -149,6 +154,41 @@ def test_uniform_1m_full_size(prec):
     o2 = oracle.hybrid(w.x, w.y, w.gamma, w.sigma, w.root, w.L, targets=t)
     assert _rel(d0, o1) <= FP64_TOL
     assert _rel(d1, o2) <= FP64_TOL
+
+
+def test_uniform_1m_benchmark_setting():
+    """The benchmark's timed configuration: the 2^20-particle workload at the
+    proposer's verified setting (p = 15, L = 6, leaves of 8 sigma), FP32_TC.
+    Every output against the oracle FMM at the same (p, L), and the metric's
+    bar -- max |du| <= 1e-6 max |u| against the oracle's regularised direct
+    sum -- at 256 seeded particles."""
+    w = W.uniform_1m()
+    w.p, w.L = 15, 6
+    xy, g = _dev(w, torch.float32)
+    with _plan(w, "fp32_tc") as plan:
+        uv = plan.velocity(xy, g, check=True).double().cpu().numpy()
+    ref = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.p, w.L, w.root)
+    assert _rel(uv, ref) <= FP32_TOL, _rel(uv, ref)
+    t = W.sample_targets(w.n, 256, 12)
+    o1 = oracle.direct(w.x, w.y, w.gamma, w.sigma, targets=t)
+    assert _rel_speed(uv[t], o1) <= 1e-6, _rel_speed(uv[t], o1)
+
+
+def test_clustered_16m_against_direct_sum():
+    """The large clustered workload (2^24 particles in 64 Gaussian patches,
+    sigma = h, p = 20, L = 9, uneven leaf occupancy) in FP32_TC: the GPU FP64
+    direct sum against the oracle's at 48 seeded particles (1e-13), and the
+    FMM within 1e-6 of max |u| there."""
+    w = W.clustered_16m()
+    xy, g = _dev(w, torch.float32)
+    t = W.sample_targets(w.n, 48, 13)
+    with _plan(w, "fp32_tc") as plan:
+        uv = plan.velocity(xy, g, check=True).double().cpu().numpy()
+        d0 = plan.direct_sampled(xy, g, torch.tensor(t, device="cuda"), kernel=0).cpu().numpy()
+        plan.check()
+    o1 = oracle.direct(w.x, w.y, w.gamma, w.sigma, targets=t)
+    assert _rel(d0, o1) <= FP64_TOL, _rel(d0, o1)
+    assert _rel_speed(uv[t], o1) <= 1e-6, _rel_speed(uv[t], o1)
 
 
 # ---------------------------------------------------------------------------
