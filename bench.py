@@ -59,6 +59,33 @@ P2P_TRAFFIC = {"sha256_p2p_cu": "d7d71da744a4a0fa9c0cdfe073332f84967fdfca0f4bd56
                "bytes": 21738240}
 
 
+def m2l_pairs(L):
+    """Box pairs of the M2L step summed over levels 2..L: each box against the
+    children of its parent's neighbours that are not its own neighbours (the
+    interaction list of Sec. 3.3.1, 27 for an interior box)."""
+    total = 0
+    for lev in range(2, L + 1):
+        side = 1 << lev
+        i = np.arange(side)
+        # per axis: source index j with parent(j) within 1 of parent(i)
+        pi = i >> 1
+        cnt = np.zeros((side, 5), dtype=np.int64)  # per |i - j| class
+        js = np.arange(side)
+        near = np.abs(pi[:, None] - (js >> 1)[None, :]) <= 1      # parent neighbours (1D)
+        adj = np.abs(i[:, None] - js[None, :]) <= 1                # own neighbours (1D)
+        a = near.sum(1)            # 1D candidates per target index
+        b = (near & adj).sum(1)    # of which adjacent
+        # 2D: candidates a_x a_y minus the adjacent block b_x b_y
+        total += int((a[:, None] * a[None, :] - b[:, None] * b[None, :]).sum())
+    return total
+
+
+def tf32_peak_tflops(peaks):
+    """Dense TF32 tensor peak: the measured bf16 figure times the nominal
+    TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s dense)."""
+    return float(peaks.get("bf16_tflops", 1900.0)) * 1.1 / 2.25
+
+
 def p2p_traffic(p, L):
     import hashlib
 
@@ -336,10 +363,22 @@ def run_clustered(torch, dev, flush, steps=5):
         ref = plan.direct_sampled(xy, g, t, kernel=0)
         st = plan.error_stats(xy, uv, t, ref).cpu().numpy()
         plan.check()
+    ph = {k: float(np.mean([q[k] for q in phases])) for k in phases[0]}
+    peaks, peak_kind = _peaks()
+    m2l_flops = 8.0 * w.p * w.p * m2l_pairs(w.L)
+    tf32 = tf32_peak_tflops(peaks)
+    P = 16 if w.p <= 16 else 32
+    m2l = {"bound": "tensor", "unit": "TFLOP/s", "peak": tf32,
+           "achieved": m2l_flops / (ph["m2l"] * 1e-3) / 1e12,
+           "frac": m2l_flops / (ph["m2l"] * 1e-3) / 1e12 / tf32,
+           "executed_frac": 3.0 * (P / w.p) ** 2 * m2l_flops / (ph["m2l"] * 1e-3) / 1e12 / tf32,
+           "note": "achieved counts useful flops (8 p^2 per box pair); executed_frac adds the "
+                   "3xTF32 split and the zero padding of p to P"}
     return {"workload": "clustered_16m: N=2^24, 64 Gaussian patches (std 0.02-0.2), signed "
                         "patch circulations h^2 N(0,1), sigma=h=2/4096, p=20, L=9, fp32_tc",
+            "roofline_m2l": m2l,
             "value": n / (ms * 1e-3), "unit": "particles/s", "ms_per_step": ms, "steps": steps,
-            "phase_ms": {k: float(np.mean([q[k] for q in phases])) for k in phases[0]},
+            "phase_ms": ph,
             "max_rel_err_vs_fp64_direct": float(st[0] / st[1]), "targets": 16384,
             "meets_tolerance": bool(st[0] / st[1] <= TOL)}
 
@@ -471,6 +510,22 @@ def run_ours(args):
         "phase_ms": phase_avg,
     }
 
+    m2l_ms = phase_avg["m2l"]
+    m2l_flops = 8.0 * p * p * m2l_pairs(L)
+    tf32 = tf32_peak_tflops(peaks)
+    roofline_m2l = {
+        "kernel": "m2l_split_kernel + m2l_tc_kernel (tcgen05 3xTF32)",
+        "bound": "tensor", "unit": "TFLOP/s",
+        "achieved": m2l_flops / (m2l_ms * 1e-3) / 1e12, "peak": tf32,
+        "frac": m2l_flops / (m2l_ms * 1e-3) / 1e12 / tf32,
+        "peak_source": f"{peak_kind} bf16 {float(peaks.get('bf16_tflops', 1900.0)):.0f} TFLOP/s "
+                       "x nominal TF32/BF16 1.1/2.25",
+        "flops_per_launch": m2l_flops,
+        "flops_counted": "8 p^2 per interaction-list box pair, levels 2..L (useful complex "
+                         "MACs; the 3xTF32 split and the zero padding to P = 16/32 run more)",
+        "avg_launch_ms": m2l_ms,
+    }
+
     # end to end through the host-buffer entry point
     hxy = xy.cpu().pin_memory()
     hg = g.cpu().pin_memory()
@@ -541,7 +596,8 @@ def run_ours(args):
                        "precision": args.precision,
                        "l2": "flushed between timed steps (512 MiB write outside the events)",
                        "parallelism": f"replicas x{world}"},
-            "accuracy": accuracy, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "accuracy": accuracy, "roofline": roofline, "roofline_m2l": roofline_m2l,
+            "cpu_baseline": cpu, "e2e": e2e,
             "as_configured": configured, "plain_fp64": plain_fp64, "batch_sweep": batch,
             "clustered_16m": large,
             "gpu_launches": int(launches_per_step * args.steps),

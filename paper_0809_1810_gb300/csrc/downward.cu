@@ -11,7 +11,7 @@
 namespace fmm2d {
 namespace {
 
-constexpr int kTopLevel = 4;
+constexpr int kTopLevel = 2;  // levels 3.. run one launch per level (a single CTA serialises them)
 
 template <typename R, int G>
 __device__ __forceinline__ void l2l_box(const Geometry& g, int level, int64_t slot, bool valid,

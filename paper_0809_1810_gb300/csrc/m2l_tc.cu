@@ -129,11 +129,15 @@ __host__ __device__ constexpr uint32_t idesc_tf32(uint32_t n) {
 constexpr int kAccs = 8;       // accumulators in tensor memory
 constexpr int kMainAccs = 7;   // for A_hi B_hi; the last one takes the corrections
 
-template <int KC>
+// KC K-chunks of 32 floats (2P = 32 KC), ST pipeline stages.  At 2P = 32 a
+// stage is 40 KB: two stages let two CTAs share an SM (many tiles), four
+// keep more loads in flight for one CTA per SM (fewer tiles than SMs).  At
+// 2P = 64 a stage is 96 KB and two fit.
+template <int KC, int ST>
 struct TcShape {
     static constexpr int kN = 32 * KC;                    // 2P columns
     static constexpr int kTmemCols = kAccs * kN;          // 256 or 512 (power of two)
-    static constexpr int kStages = 2;  // 2 CTAs per SM at 2P = 32
+    static constexpr int kStages = ST;
     static constexpr int kABytes = 128 * 128;             // one 128 x 32-float K chunk
     static constexpr int kBBytes = kN * 128;              // one kN x 32-float K chunk
     static constexpr int kStageBytes = 2 * KC * (kABytes + kBBytes);
@@ -173,11 +177,11 @@ __global__ void m2l_tc_tables_kernel(const double* __restrict__ m2l64, int P,
     }
 }
 
-template <int KC>
+template <int KC, int ST>
 __global__ void __launch_bounds__(128, 1)
 m2l_tc_kernel(const __grid_constant__ M2LTcMaps maps, const int4* __restrict__ tiles, Geometry g,
               float* __restrict__ le, int* status) {
-    using S = TcShape<KC>;
+    using S = TcShape<KC, ST>;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[S::kStages], empty[S::kStages], done;
     __shared__ uint32_t tmem_base;
@@ -358,7 +362,7 @@ EncodeTiledFn encoder() {
 
 }  // namespace
 
-int m2l_tc_smem_bytes(int P) { return P <= 16 ? TcShape<1>::kSmem : TcShape<2>::kSmem; }
+int m2l_tc_smem_bytes(int P) { return P <= 16 ? TcShape<1, 4>::kSmem : TcShape<2, 2>::kSmem; }
 
 cudaError_t m2l_tc_prepare(const Geometry& g, const double* m2l64, float* me_hi, float* me_lo,
                            float* bhi, float* blo, M2LTcMaps* maps, int4* tiles_host,
@@ -425,20 +429,28 @@ cudaError_t launch_m2l_tc(const Geometry& g, const M2LTcMaps& maps, const int4* 
     int blocks = (int)((count + 255) / 256);
     if (blocks > 8192) blocks = 8192;
     m2l_split_kernel<<<blocks, 256, 0, s>>>(me, me_hi, me_lo, count);
-    if (g.P <= 16)
-        m2l_tc_kernel<1><<<ntiles, 128, TcShape<1>::kSmem, s>>>(maps, tiles, g, le, status);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g.P > 16)
+        m2l_tc_kernel<2, 2><<<ntiles, 128, TcShape<2, 2>::kSmem, s>>>(maps, tiles, g, le, status);
+    else if (ntiles <= sms)
+        m2l_tc_kernel<1, 4><<<ntiles, 128, TcShape<1, 4>::kSmem, s>>>(maps, tiles, g, le, status);
     else
-        m2l_tc_kernel<2><<<ntiles, 128, TcShape<2>::kSmem, s>>>(maps, tiles, g, le, status);
+        m2l_tc_kernel<1, 2><<<ntiles, 128, TcShape<1, 2>::kSmem, s>>>(maps, tiles, g, le, status);
     return cudaGetLastError();
 }
 
 cudaError_t m2l_tc_configure() {
-    cudaError_t e = cudaFuncSetAttribute(m2l_tc_kernel<1>,
+    cudaError_t e = cudaFuncSetAttribute(m2l_tc_kernel<1, 4>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TcShape<1>::kSmem);
+                                         TcShape<1, 4>::kSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(m2l_tc_kernel<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 TcShape<1, 2>::kSmem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(m2l_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                TcShape<2>::kSmem);
+    return cudaFuncSetAttribute(m2l_tc_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TcShape<2, 2>::kSmem);
 }
 
 }  // namespace fmm2d

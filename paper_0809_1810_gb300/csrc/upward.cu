@@ -19,7 +19,7 @@ namespace fmm2d {
 namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
-constexpr int kTopLevel = 4;  // levels <= kTopLevel run in the single-CTA kernel
+constexpr int kTopLevel = 2;  // levels <= kTopLevel run in the single-CTA kernel
 
 // One warp per leaf, four sibling leaves per CTA; lanes stride over the
 // leaf's particles, accumulate all coefficients, then reduce across the warp.
@@ -69,21 +69,37 @@ __device__ __forceinline__ void p2m_quad(const typename ParticleOf<R>::type* __r
             }
         }
     }
+    // Butterfly reduce-scatter of the warp's 2 PMAX partial sums: at each of
+    // five steps a lane keeps half of its live values and adds its partner's
+    // copy of that half.  Lane l ends with the warp totals of reals
+    // [l W, (l + 1) W), W = 2 PMAX / 32: one real for PMAX = 16, one complex
+    // coefficient for PMAX = 32.
+    constexpr int N = 2 * PMAX;
+    R v[N];
 #pragma unroll
     for (int m = 0; m < PMAX; ++m) {
+        v[2 * m] = acc[m].x;
+        v[2 * m + 1] = acc[m].y;
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            acc[m].x += __shfl_xor_sync(0xffffffffu, acc[m].x, o);
-            acc[m].y += __shfl_xor_sync(0xffffffffu, acc[m].y, o);
+    for (int step = 0; step < 5; ++step) {
+        const int o = 16 >> step;
+        const int half = (N >> step) >> 1;
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const R send = upper ? v[i] : v[i + half];
+            const R keep = upper ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
         }
     }
-    C* dst = reinterpret_cast<C*>(me + box_slot(g.level_base, g.L, ix, iy) * (2 * g.P));
+    constexpr int W = N / 32;
+    R* dst = me + box_slot(g.level_base, g.L, ix, iy) * (2 * g.P);
+    R* kid = reinterpret_cast<R*>(child_me[warp]);
 #pragma unroll
-    for (int m = 0; m < PMAX; ++m) {
-        if ((m & 31) == lane && m < g.P) {
-            dst[m] = acc[m];
-            child_me[warp][m] = acc[m];
-        }
+    for (int j = 0; j < W; ++j) {
+        dst[lane * W + j] = v[j];
+        kid[lane * W + j] = v[j];
     }
     if (!fuse_parent) return;  // uniform over the CTA
     __syncthreads();
