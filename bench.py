@@ -55,8 +55,8 @@ P2P_FLOPS_PER_PAIR = 20  # algorithmic work per near pair
 # dram__bytes_write.sum) from the ncu capture summarised in
 # profiles/p2p_l2p_f32_uniform_1m_p15_L6.md; reported only while the kernel
 # source is the one captured and the setting matches.
-P2P_TRAFFIC = {"sha256_p2p_cu": "d7d71da744a4a0fa9c0cdfe073332f84967fdfca0f4bd56331169e3514cb2dd9", "p": 15, "L": 6,
-               "bytes": 21738240}
+P2P_TRAFFIC = {"sha256_p2p_cu": "ef22e7c96a7725ea6ce68e53cf350314ea948d3150eaa4c10a9f86f04d6481ae", "p": 15, "L": 6,
+               "bytes": 21734144}
 
 
 def m2l_pairs(L):

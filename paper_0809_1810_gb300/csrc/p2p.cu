@@ -177,27 +177,25 @@ p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
 // ---------------------------------------------------------------------------
 // FP32 near field, the dominant kernel of the FP32 form.
 //
-// Work split: chunks of kTicket sorted targets.  A leaf's targets split
-// into chunks [c kTicket, (c + 1) kTicket) from its first target; the warp
-// owning window [w kTicket, (w + 1) kTicket) of the sorted order runs every
-// chunk that starts inside it (four warps per CTA, no CTA-wide barriers).
-// A window meets a few whole leaves when leaves are small and one chunk of
-// a leaf when leaves are large, so a crowded leaf spreads over many warps
-// instead of holding one warp while the rest of the GPU idles.  For each
-// chunk the warp gathers the leaf's local list -- the 9
+// Work split: targets in sorted (leaf) order.  A leaf's targets form rounds
+// of 32 and chunks of 64 or 128 from its first target; persistent warps pull
+// windows of the sorted order from a counter and run every chunk that starts
+// inside (see WorkSplit), so a crowded leaf spreads over many warps instead
+// of holding one warp while the rest of the GPU idles, and the last items are
+// short.  For each chunk the warp gathers the leaf's local list -- the 9
 // source ranges of the 3x3 neighbourhood, coalesced loads -- into a
 // per-warp shared-memory buffer, sorted by a ballot compaction into a near
-// band (front) and a far band (back): a source whose distance to the leaf's
-// square is at least sqrt(2) sigma (q = 1) is at q >= 1 from every target of
+// band (front) and a far band (back): a source farther than sqrt(qthr)
+// scaled units from the leaf's square is at q2 >= qthr from every target of
 // the leaf, so the far band never needs the polynomial.
-// Targets go in rounds of 32, one per lane; all lanes read the same source
-// (a shared-memory broadcast).  In a leaf's last, partial round, ns adjacent
-// lanes share a target and split its sources (combined by shuffles).  Both
-// band loops are straight-line code (4 sources unrolled, no per-pair
-// branches).  Lists longer than the buffer are processed in chunks.
+// Targets go in passes of 32 T (T = 4, 2, 1 per lane); all lanes read the
+// same source (a shared-memory broadcast).  In a leaf's last round of at
+// most 16 targets, ns adjacent lanes share a target and split its sources
+// (combined by shuffles).  Band loops are straight-line code (no per-pair
+// branches).  Lists longer than the buffer are processed in parts.
 //
-// Pair arithmetic in physical FP32 coordinates: dx = x_i - x_j is exact for
-// nearby particles, q2 = (dx^2 + dy^2) log2(e) / (2 sigma^2).
+// Pair arithmetic in scaled leaf-relative FP32 coordinates X = (x - centre)
+// sc, so that q2 = |X_i - X_j|^2 = r^2 / (2 sigma^2 ln 2).
 // Radial factor g(q2) = (1 - 2^-q2) / q2: MUFU ex2 and rcp for q2 >= kPolyEdge;
 // below it the subtraction 1 - 2^-q2 would cancel, and a degree-5
 // polynomial interpolating g at the Chebyshev nodes of [0, kPolyEdge] takes
@@ -212,7 +210,7 @@ p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
 // source serves that many pairs.
 // ---------------------------------------------------------------------------
 constexpr int kLeafWarps = 4;
-constexpr uint32_t kTicket = 128;  // sorted targets per window (a power of two)
+constexpr uint32_t kTicket = 128;  // largest sorted-target window (a power of two)
 #ifndef FMM2D_P2P_LIST_CAP
 #define FMM2D_P2P_LIST_CAP 560  // 37 KB of shared memory per CTA: 6 CTAs per SM
 #endif
@@ -489,8 +487,8 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
                 finish(rec[t], x[t], y[t], S.su[t] + S.cu[t], S.sv[t] + S.cv[t]);
     };
     uint32_t tb = a;
-    if (b - tb == kTicket) {  // a whole chunk: four targets per lane, the list gathered once
-        pass(std::integral_constant<int, 4>{}, tb, kTicket);
+    if (b - tb == 128) {  // 128 targets: four per lane, the list gathered once
+        pass(std::integral_constant<int, 4>{}, tb, 128u);
         tb = b;
     }
     for (; tb + 64 <= b; tb += 64) pass(std::integral_constant<int, 2>{}, tb, 64u);
@@ -525,26 +523,30 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
 }
 
 // Work items of one near-field pass over n sorted targets.  Items
-// [0, nbig) are windows of kTicket positions, [0, nbig kTicket); the rest are
-// windows of 32 positions covering [nbig kTicket, n).  A big window runs every
-// chunk (kTicket targets from a multiple of kTicket past its leaf's first
-// target) that starts inside it; a small window runs every round (32
-// targets from a multiple of 32 past the leaf's first target) that starts
-// inside it and whose chunk starts at or after nbig kTicket (earlier chunks
-// are a big window's).  Small items at the end keep the last warps' work
-// short; the split changes only how rounds are grouped, not a target's
-// arithmetic.
+// [0, nbig) are windows of `span` positions (128, or 64 when there are few
+// windows per resident warp), covering [0, nbig span); the rest are windows of
+// 32 positions covering [nbig span, n).  A big window runs every chunk (span
+// targets from a multiple of span past its leaf's first target) that starts
+// inside it; a small window runs every round (32 targets from a multiple of
+// 32 past the leaf's first target) that starts inside it and whose chunk
+// starts at or after nbig span (earlier chunks are a big window's).  Small
+// items at the end keep the last warps' work short; neither the window size
+// nor the split changes a target's arithmetic, only how rounds are grouped.
 struct WorkSplit {
-    uint32_t n, nbig, items;
+    uint32_t n, span, nbig, items;
 };
 
 // The small items cover about half a window per resident warp (the spread
-// of the warps' finishing times), at most a quarter of the windows.
+// of the warps' finishing times), at most a quarter of the windows.  Windows
+// of 128 targets give each lane four targets but take a warp long to finish;
+// with fewer than 8 of them per warp the tail would dominate, and windows of
+// 64 are used.
 static WorkSplit work_split(uint64_t n, uint64_t warps) {
-    const uint64_t windows = (n + kTicket - 1) / kTicket;
+    const uint32_t span = (n + kTicket - 1) / kTicket >= 8 * warps ? kTicket : kTicket / 2;
+    const uint64_t windows = (n + span - 1) / span;
     const uint64_t nbig = windows - std::min(windows / 4, warps / 2 + 1);
-    const uint64_t rest = n - std::min<uint64_t>(n, nbig * kTicket);
-    return WorkSplit{(uint32_t)n, (uint32_t)nbig, (uint32_t)(nbig + (rest + 31) / 32)};
+    const uint64_t rest = n - std::min<uint64_t>(n, nbig * span);
+    return WorkSplit{(uint32_t)n, span, (uint32_t)nbig, (uint32_t)(nbig + (rest + 31) / 32)};
 }
 
 // f(key, a, b) for every chunk or round that item w owns: key the leaf index
@@ -555,10 +557,10 @@ __device__ __forceinline__ void for_each_piece(const uint32_t* __restrict__ skey
                                                const WorkSplit& ws, uint32_t w, F&& f) {
     const int lane = threadIdx.x & 31;
     const bool big = w < ws.nbig;
-    const uint32_t split = ws.nbig * kTicket;
-    const uint32_t r0 = big ? w * kTicket : split + (w - ws.nbig) * 32u;
-    const uint32_t r1 = min(r0 + (big ? kTicket : 32u), ws.n);
-    const uint32_t span = big ? kTicket : 32u;
+    const uint32_t split = ws.nbig * ws.span;
+    const uint32_t r0 = big ? w * ws.span : split + (w - ws.nbig) * 32u;
+    const uint32_t span = big ? ws.span : 32u;
+    const uint32_t r1 = min(r0 + span, ws.n);
     for (uint32_t base = r0; base < r1; base += 32) {
         const uint32_t r = base + lane;
         uint32_t key = 0, first = 0;
@@ -568,7 +570,7 @@ __device__ __forceinline__ void for_each_piece(const uint32_t* __restrict__ skey
             first = leaf_start[key];
             const uint32_t off = r - first;
             starts = (off & (span - 1)) == 0 &&
-                     (big || first + (off & ~(kTicket - 1)) >= split);
+                     (big || first + (off & ~(ws.span - 1)) >= split);
         }
         unsigned m = __ballot_sync(0xffffffffu, starts);
         while (m) {
