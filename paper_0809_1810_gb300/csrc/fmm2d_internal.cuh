@@ -15,7 +15,9 @@ constexpr int kMaxL = 12;      // deepest quadtree level served
 constexpr int kRadixBits = 8;  // radix sort digit width
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;  // keys per thread per tile
+// keys per thread per tile: 2048-key tiles sort 2^24 keys 10-15% faster than
+// 4096-key ones (more CTAs in flight) and 2^20 keys as fast
+constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 
 // Device-side status flags (bitwise OR of 1 << fmm2d_status).

@@ -230,14 +230,18 @@ struct NearF32v3 {
     float coef[kF32Deg + 1];  // g(q2) ~ sum_k coef[k] q2^k on [0, qthr)
 };
 
-__device__ __forceinline__ float g_far(float q2) {
-    return (1.0f - ex2_approx(-q2)) * rcp_approx(q2);
+// Gamma_j g(q2) with the circulation folded into the subtraction:
+// Gamma (1 - e) / q2 = fma(-Gamma, e, Gamma) rcp(q2), e = 2^-q2 (one
+// instruction fewer than forming 1 - e first, and one rounding fewer).
+__device__ __forceinline__ float wg_far(float gamma, float q2) {
+    return fmaf(-gamma, ex2_approx(-q2), gamma) * rcp_approx(q2);
 }
-__device__ __forceinline__ float g_near(const NearF32v3& nm, float q2) {
+__device__ __forceinline__ float wg_near(const NearF32v3& nm, float gamma, float q2) {
     float poly = nm.coef[kF32Deg];
 #pragma unroll
     for (int k = kF32Deg - 1; k >= 0; --k) poly = fmaf(poly, q2, nm.coef[k]);
-    return q2 < nm.qthr ? poly : g_far(q2);
+    const float far = wg_far(gamma, q2);
+    return q2 < nm.qthr ? gamma * poly : far;
 }
 
 template <bool kNear>
@@ -245,7 +249,7 @@ __device__ __forceinline__ void one_source(const NearF32v3& nm, const float4 s, 
                                            float& iu, float& iv) {
     const float dx = x - s.x, dy = y - s.y;
     const float q2 = fmaf(dx, dx, dy * dy);
-    const float w = s.z * (kNear ? g_near(nm, q2) : g_far(q2));
+    const float w = kNear ? wg_near(nm, s.z, q2) : wg_far(s.z, q2);
     iu = fmaf(-dy, w, iu);
     iv = fmaf(dx, w, iv);
 }

@@ -466,7 +466,7 @@ cudaError_t launch_batch_tree(const void* dev_key_params, const int64_t* dev_off
 // needs (two key/value ping-pong buffers, the digit counts and a status
 // word) lives in one file-scope device array of fixed size, so the call
 // itself allocates nothing.  Every GPU that loads the library holds this
-// array (about 4.07 MB) until the process exits.
+// array (about 4.3 MB) until the process exits.
 // ---------------------------------------------------------------------------
 namespace {
 
