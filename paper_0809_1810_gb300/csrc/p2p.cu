@@ -197,10 +197,9 @@ p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
 // Pair arithmetic in scaled leaf-relative FP32 coordinates X = (x - centre)
 // sc, so that q2 = |X_i - X_j|^2 = r^2 / (2 sigma^2 ln 2).
 // Radial factor g(q2) = (1 - 2^-q2) / q2: MUFU ex2 and rcp for q2 >= kPolyEdge;
-// below it the subtraction 1 - 2^-q2 would cancel, and a degree-5
-// polynomial interpolating g at the Chebyshev nodes of [0, kPolyEdge] takes
-// over (interpolation error below 1e-9), fitted on the host when the kernel
-// is launched.  At q2 = kPolyEdge the MUFU form is within 6e-7 of g (two
+// below it the subtraction 1 - 2^-q2 would cancel, and a cubic interpolating
+// g at the Chebyshev nodes of [0, kPolyEdge] takes over (interpolation error
+// 8e-9, below FP32 rounding), fitted on the host when the kernel is launched.  At q2 = kPolyEdge the MUFU form is within 6e-7 of g (two
 // ulp of ex2 over 1 - 2^-q2 = 0.099), and the few pairs that close to a
 // target carry a small share of its velocity.
 // Sums: blocks of sources into fresh registers, then Neumaier-compensated
@@ -215,7 +214,7 @@ constexpr uint32_t kTicket = 128;  // largest sorted-target window (a power of t
 #define FMM2D_P2P_LIST_CAP 560  // 37 KB of shared memory per CTA: 6 CTAs per SM
 #endif
 constexpr int kListCap = FMM2D_P2P_LIST_CAP;  // source records per warp buffer
-constexpr int kF32Deg = 5;
+constexpr int kF32Deg = 3;
 constexpr double kPolyEdge = 0.15;  // q2 below which the polynomial is used
 
 struct NearF32v3 {
