@@ -296,7 +296,10 @@ template <bool kNear, int T>
 __device__ __forceinline__ void band_loopT(const float4* list, uint32_t lo, uint32_t hi,
                                            const NearF32v3& nm, const float (&x)[T],
                                            const float (&y)[T], SumT<T>& S) {
-    constexpr int kUnroll = 4 / T;  // sources per iteration: four pairs in flight
+    // sources per iteration (measured: eight pairs in flight at two targets
+    // per lane, four at one and at four; longer bodies cost more in
+    // instruction fetch than they save in loop overhead)
+    constexpr int kUnroll = T >= 4 ? 1 : 4;
     uint32_t j = lo;
     while (j < hi) {
         const uint32_t e = min(j + (uint32_t)kInnerT, hi);

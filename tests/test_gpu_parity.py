@@ -108,6 +108,20 @@ def _cases():
                    n, n + p, 2.0 / np.sqrt(n), sigma_over_h=soh, p=p, L=L, dtype=dt))
     yield "clustered_20000", lambda dt: W.clustered_patches(20000, 4, npatch=6, h=2.0 / 140,
                                                              p=14, L=5, dtype=dt)
+    # a deep, sparse tree: 262,144 leaves for 20,000 particles, most empty
+    yield "uniform_n20000_p4_L9", lambda dt: W.uniform_random(20000, 77, 2.0 / np.sqrt(20000),
+                                                              sigma_over_h=1.0, p=4, L=9,
+                                                              dtype=dt)
+    yield "one_leaf_3000", _one_leaf
+
+
+def _one_leaf(dt):
+    """Every particle inside one leaf of a depth-4 tree (the box
+    [0.25, 0.375)^2): one dense leaf, every other leaf empty."""
+    w = W.uniform_random(3000, 78, 0.125 / np.sqrt(3000), sigma_over_h=1.5, p=9, L=4, dtype=dt)
+    w.x = (0.25 + (w.x.astype(np.float64) + 1.0) * 0.0625 * 0.999).astype(dt)
+    w.y = (0.25 + (w.y.astype(np.float64) + 1.0) * 0.0625 * 0.999).astype(dt)
+    return w
 
 
 CASES = list(_cases())
