@@ -196,12 +196,13 @@ p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
 //
 // Pair arithmetic in scaled leaf-relative FP32 coordinates X = (x - centre)
 // sc, so that q2 = |X_i - X_j|^2 = r^2 / (2 sigma^2 ln 2).
-// Radial factor g(q2) = (1 - 2^-q2) / q2: MUFU ex2 and rcp for q2 >= kPolyEdge;
-// below it the subtraction 1 - 2^-q2 would cancel, and a cubic interpolating
-// g at the Chebyshev nodes of [0, kPolyEdge] takes over (interpolation error
-// 8e-9, below FP32 rounding), fitted on the host when the kernel is launched.  At q2 = kPolyEdge the MUFU form is within 6e-7 of g (two
-// ulp of ex2 over 1 - 2^-q2 = 0.099), and the few pairs that close to a
-// target carry a small share of its velocity.
+// Radial factor g(q2) = (1 - 2^-q2) / q2: MUFU ex2 and rcp for
+// q2 >= kPolyEdge; below it the subtraction 1 - 2^-q2 would cancel, and a
+// cubic interpolating g at the Chebyshev nodes of [0, kPolyEdge] takes over
+// (interpolation error 8e-9, below FP32 rounding), fitted on the host when
+// the kernel is launched.  At q2 = kPolyEdge the MUFU form is within 6e-7
+// of g (two ulp of ex2 over 1 - 2^-q2 = 0.099), and the few pairs that close
+// to a target carry a small share of its velocity.
 // Sums: blocks of sources into fresh registers, then Neumaier-compensated
 // addition into the running sums.  A whole chunk (128 targets) gives each
 // lane four targets and gathers each part of the local list once; full
