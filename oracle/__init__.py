@@ -11,9 +11,11 @@ Functions and the paper passage each follows:
 * :func:`morton_keys`, :func:`sort_by_key` -- uniform quadtree, Sec. 3.3 / Fig. 6.
 * :func:`direct` -- O1, the discrete Biot-Savart sum of Eq. 7 with Eq. 6 and
   the self term excluded (Eq. 9).
-* :func:`hybrid` -- O2, regularised kernel inside the 3x3 leaf neighbourhood,
-  singular kernel (Eq. 27) elsewhere: the FMM's limit as p grows (Eq. 10, Sec. 4.1).
-* :func:`fmm` -- O3, the plain FMM in the order of Sec. 3.1 / Fig. 3.
+* :func:`hybrid` -- O2, regularised kernel inside the 3x3 leaf neighbourhood
+  (and, with a cutoff a > 0, for every pair closer than a: Sec. 4.1, Eq. 29),
+  singular kernel (Eq. 27) elsewhere: the FMM's limit as p grows (Eq. 10).
+* :func:`fmm` -- O3, the plain FMM in the order of Sec. 3.1 / Fig. 3, with the
+  same optional cutoff.
 * ``op_*`` -- single expansions and translations: Eqs. 20-22, Secs. 3.3.2-3.3.3.
 * :func:`kernel_error_estimate` -- Eq. 29 (squared-distance reading).
 * :func:`truncation_bound` -- Eqs. 30-31 (geometric-tail reading).
@@ -78,6 +80,10 @@ def _load():
         lib.orc_hybrid.restype = i32
         lib.orc_fmm.argtypes = [i64, vp, vp, vp, d, i32, i32, d, d, d, vp, vp]
         lib.orc_fmm.restype = i32
+        lib.orc_hybrid_cut.argtypes = [i64, vp, vp, vp, d, d, d, d, i32, d, i64, vp, vp, vp]
+        lib.orc_hybrid_cut.restype = i32
+        lib.orc_fmm_cut.argtypes = [i64, vp, vp, vp, d, i32, i32, d, d, d, d, vp, vp]
+        lib.orc_fmm_cut.restype = i32
         lib.orc_op_p2m.argtypes = [i64, vp, vp, vp, d, d, i32, vp]
         lib.orc_op_m2m.argtypes = [i32, vp, d, d, d, d, vp]
         lib.orc_op_m2l.argtypes = [i32, vp, d, d, d, d, vp]
@@ -153,27 +159,40 @@ def direct(x, y, gamma, sigma, targets=None):
     return np.stack([u, v], axis=1)
 
 
-def hybrid(x, y, gamma, sigma, root, L, targets=None):
-    """O2: regularised kernel in the 3x3 leaf neighbourhood, singular elsewhere."""
+def hybrid(x, y, gamma, sigma, root, L, targets=None, a=0.0):
+    """O2: regularised kernel in the 3x3 leaf neighbourhood and for every pair
+    closer than the cutoff a (Sec. 4.1), singular elsewhere."""
     lib = _load()
     x, y, g = _f64(x), _f64(y), _f64(gamma)
     t = _targets(x.shape[0], targets)
     u = np.empty(t.shape[0])
     v = np.empty(t.shape[0])
-    _check(lib.orc_hybrid(x.shape[0], _ptr(x), _ptr(y), _ptr(g), sigma, root[0], root[1],
-                          root[2], L, t.shape[0], _ptr(t), _ptr(u), _ptr(v)), "hybrid")
+    if a == 0.0:
+        st = lib.orc_hybrid(x.shape[0], _ptr(x), _ptr(y), _ptr(g), sigma, root[0], root[1],
+                            root[2], L, t.shape[0], _ptr(t), _ptr(u), _ptr(v))
+    else:
+        st = lib.orc_hybrid_cut(x.shape[0], _ptr(x), _ptr(y), _ptr(g), sigma, root[0], root[1],
+                                root[2], L, float(a), t.shape[0], _ptr(t), _ptr(u), _ptr(v))
+    _check(st, "hybrid")
     return np.stack([u, v], axis=1)
 
 
-def fmm(x, y, gamma, sigma, p, L, root):
-    """O3: plain FP64 FMM velocity at every particle -> (n, 2)."""
+def fmm(x, y, gamma, sigma, p, L, root, a=0.0):
+    """O3: plain FP64 FMM velocity at every particle -> (n, 2); with a > 0,
+    pairs closer than a in non-neighbour leaves keep the regularised kernel
+    (Sec. 4.1)."""
     lib = _load()
     x, y, g = _f64(x), _f64(y), _f64(gamma)
     n = x.shape[0]
     u = np.empty(n)
     v = np.empty(n)
-    _check(lib.orc_fmm(n, _ptr(x), _ptr(y), _ptr(g), sigma, p, L, root[0], root[1], root[2],
-                       _ptr(u), _ptr(v)), "fmm")
+    if a == 0.0:
+        st = lib.orc_fmm(n, _ptr(x), _ptr(y), _ptr(g), sigma, p, L, root[0], root[1], root[2],
+                         _ptr(u), _ptr(v))
+    else:
+        st = lib.orc_fmm_cut(n, _ptr(x), _ptr(y), _ptr(g), sigma, p, L, root[0], root[1],
+                             root[2], float(a), _ptr(u), _ptr(v))
+    _check(st, "fmm")
     return np.stack([u, v], axis=1)
 
 

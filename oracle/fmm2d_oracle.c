@@ -19,6 +19,8 @@
  *   velocity (u_x, u_y) = (Re w, -Im w)
  *   near field: regularised kernel K_sigma (Eq. 6) over the local list, i != j
  *   (Eq. 9, Eq. 10).
+ *   cutoff a (Sec. 4.1, Eq. 29): a pair closer than a keeps K_sigma even when
+ *   its leaves are not neighbours; a = 0 is the plain 3x3 rule.
  *
  * Parity status of each function is stated beside it; the pins live in the
  * test suite.
@@ -163,12 +165,14 @@ int orc_direct(int64_t n, const double* x, const double* y, const double* gamma,
 
 /* O2: the sum the FMM converges to as p grows.  Pairs whose leaves are in
  * each other's local list (the 3x3 leaf neighbourhood, Sec. 3.3.1) use the
- * regularised kernel; every other pair uses the singular kernel, as the far
- * field does (Eq. 10, Sec. 4.1). */
-int orc_hybrid(int64_t n, const double* x, const double* y, const double* gamma, double sigma,
-               double x0, double y0, double W, int L, int64_t ntarg, const int64_t* targets,
-               double* u, double* v) {
-    if (n < 0 || ntarg < 0 || !(sigma > 0.0) || !(W > 0.0) || L < 0 || L > 15)
+ * regularised kernel, and so does every pair closer than the cutoff a
+ * (Sec. 4.1: below the distance a the regularised kernel is kept); every
+ * other pair uses the singular kernel, as the far field does (Eq. 10,
+ * Sec. 4.1).  a = 0 gives the plain 3x3 rule. */
+int orc_hybrid_cut(int64_t n, const double* x, const double* y, const double* gamma,
+                   double sigma, double x0, double y0, double W, int L, double a, int64_t ntarg,
+                   const int64_t* targets, double* u, double* v) {
+    if (n < 0 || ntarg < 0 || !(sigma > 0.0) || !(W > 0.0) || L < 0 || L > 15 || !(a >= 0.0))
         return ORC_INVALID_ARG;
     uint32_t* lx = (uint32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(uint32_t));
     uint32_t* ly = (uint32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(uint32_t));
@@ -186,11 +190,13 @@ int orc_hybrid(int64_t n, const double* x, const double* y, const double* gamma,
                 if (j == i) continue;
                 int64_t ddx = (int64_t)lx[i] - (int64_t)lx[j];
                 int64_t ddy = (int64_t)ly[i] - (int64_t)ly[j];
-                int near = ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1;
+                double dx = x[i] - x[j], dy = y[i] - y[j];
+                int near = (ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1) ||
+                           dx * dx + dy * dy < a * a;
                 if (near)
-                    k_sigma(x[i] - x[j], y[i] - y[j], gamma[j], sigma, &su, &sv);
+                    k_sigma(dx, dy, gamma[j], sigma, &su, &sv);
                 else
-                    k_singular(x[i] - x[j], y[i] - y[j], gamma[j], &su, &sv);
+                    k_singular(dx, dy, gamma[j], &su, &sv);
             }
             u[t] = su;
             v[t] = sv;
@@ -199,6 +205,12 @@ int orc_hybrid(int64_t n, const double* x, const double* y, const double* gamma,
     free(lx);
     free(ly);
     return status;
+}
+
+int orc_hybrid(int64_t n, const double* x, const double* y, const double* gamma, double sigma,
+               double x0, double y0, double W, int L, int64_t ntarg, const int64_t* targets,
+               double* u, double* v) {
+    return orc_hybrid_cut(n, x, y, gamma, sigma, x0, y0, W, L, 0.0, ntarg, targets, u, v);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -373,9 +385,16 @@ static double complex box_centre(double x0, double y0, double W, int l, int64_t 
     return (x0 + (ix + 0.5) * w) + I * (y0 + (iy + 0.5) * w);
 }
 
-int orc_fmm(int64_t n, const double* x, const double* y, const double* gamma, double sigma,
-            int p, int L, double x0, double y0, double W, double* u, double* v) {
-    if (n < 0 || p < 1 || p > 64 || L < 0 || L > 12 || !(sigma > 0.0) || !(W > 0.0))
+/* O3 with the cutoff a of Sec. 4.1: the FMM of Sec. 3.1 (far field through
+ * the expansions with the singular kernel, near field over the 3x3 local
+ * list with K_sigma), plus, for every pair closer than a whose leaves are not
+ * neighbours, the difference K_sigma - K' that turns the singular kernel the
+ * far field applied to it back into the regularised one.  a = 0 is the plain
+ * FMM. */
+int orc_fmm_cut(int64_t n, const double* x, const double* y, const double* gamma, double sigma,
+                int p, int L, double x0, double y0, double W, double a, double* u, double* v) {
+    if (n < 0 || p < 1 || p > 64 || L < 0 || L > 12 || !(sigma > 0.0) || !(W > 0.0) ||
+        !(a >= 0.0) || !isfinite(a))
         return ORC_INVALID_ARG;
     int64_t nl = (int64_t)1 << L; /* leaves per side */
     uint32_t* key = (uint32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(uint32_t));
@@ -485,6 +504,26 @@ int orc_fmm(int64_t n, const double* x, const double* y, const double* gamma, do
                         k_sigma(x[i] - x[j], y[i] - y[j], gamma[j], sigma, &su, &sv);
                     }
                 }
+            /* cutoff: non-neighbour leaves that can hold a source closer than
+             * a (leaves at Chebyshev distance d >= 2 are at least (d - 1)
+             * leaf widths away) */
+            if (a > 0.0) {
+                double w = W / ldexp(1.0, L);
+                int64_t R = 1 + (int64_t)ceil(a / w);
+                for (int64_t qy = iy - R; qy <= iy + R; ++qy)
+                    for (int64_t qx = ix - R; qx <= ix + R; ++qx) {
+                        if (qx < 0 || qy < 0 || qx >= nl || qy >= nl) continue;
+                        if (llabs(qx - ix) <= 1 && llabs(qy - iy) <= 1) continue;
+                        int64_t q = qy * nl + qx;
+                        for (uint32_t s = start[q]; s < start[q + 1]; ++s) {
+                            int64_t j = plist[s];
+                            double dx = x[i] - x[j], dy = y[i] - y[j];
+                            if (!(dx * dx + dy * dy < a * a)) continue;
+                            k_sigma(dx, dy, gamma[j], sigma, &su, &sv);
+                            k_singular(dx, dy, -gamma[j], &su, &sv);
+                        }
+                    }
+            }
             u[i] = su;
             v[i] = sv;
         }
@@ -501,6 +540,11 @@ int orc_fmm(int64_t n, const double* x, const double* y, const double* gamma, do
     free(rowkey);
     free(key);
     return ORC_OK;
+}
+
+int orc_fmm(int64_t n, const double* x, const double* y, const double* gamma, double sigma,
+            int p, int L, double x0, double y0, double W, double* u, double* v) {
+    return orc_fmm_cut(n, x, y, gamma, sigma, p, L, x0, y0, W, 0.0, u, v);
 }
 
 /* ------------------------------------------------------------------------ */
