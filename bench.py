@@ -3,11 +3,13 @@
 Workload (one "step" = one full FMM evaluation, tree build to velocities):
 uniform positions in [-1, 1]^2, circulations h^2 N(0,1) with h = 2/1024,
 sigma = 2h, float32 inputs and arithmetic, M2L as a 3xTF32 tensor-core
-contraction (the FP32_TC form; --precision selects another).  The
-expansion order p and depth L are the trained proposer's choice for a max
-error of 1e-6 relative to the largest speed against the FP64 direct sum
-(--setting selects the stated p = 16, L = 7 or the plain fallback); the
-stated setting, whose leaves span only 4 sigma, is reported beside it.
+contraction (the FP32_TC form; --precision selects another), at the stated
+p = 16, L = 7.  Its leaves span only 4 sigma, so pairs closer than the
+cutoff a of Sec. 4.1 keep the regularised kernel: a = sigma sqrt(2 ln(1/tol))
+bounds the kernel error of every pair left on the singular kernel by the
+tolerance 1e-6 (Eq. 29).  --setting selects instead the trained proposer's
+choice, the stated setting without the cutoff, or the plain fallback; the
+first two are reported beside the headline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -42,8 +44,8 @@ import workloads as W  # noqa: E402
 
 METRIC = "FMM particles/sec at ≤1e-6 max rel err vs FP64 direct; % roofline; vs plain FP64"
 WORKLOAD = ("uniform_1m: N=2^20 uniform in [-1,1]^2, Gamma=h^2 N(0,1), h=2/1024, sigma=2h; "
-            "(p, L) for max rel err <= 1e-6 vs the FP64 direct sum (stated p=16, L=7 reported "
-            "beside it)")
+            "stated p=16, L=7 with the Sec. 4.1 cutoff a=sigma sqrt(2 ln(1/tol)) for max rel "
+            "err <= 1e-6 vs the FP64 direct sum (the proposer's choice reported beside it)")
 TOL = 1e-6
 VERIFY_TARGETS = 2048  # particles at which the proposal is judged (other seed than ACC_TARGETS)
 ACC_TARGETS = 8192
@@ -59,8 +61,7 @@ P2P_FLOPS_PER_PAIR = 20
 # dram__bytes_write.sum) from one ncu capture of the kernel on the benchmark
 # workload and setting; reported only while the kernel source is the one
 # captured (its SHA-256) and the setting matches.
-P2P_TRAFFIC = {"sha256_p2p_cu": "5b07cd375d027fdf35866b1d555092c8ef4fda8297af10cfc0f6eb510cb752c1", "p": 15, "L": 6,
-               "bytes": 21732608}
+P2P_TRAFFIC = {"sha256_p2p_cu": None, "p": 16, "L": 7, "cutoff": True, "bytes": None}
 
 
 def m2l_pairs(L):
@@ -90,10 +91,11 @@ def tf32_peak_tflops(peaks):
     return float(peaks.get("bf16_tflops", 1900.0)) * 1.1 / 2.25
 
 
-def p2p_traffic(p, L):
+def p2p_traffic(p, L, cutoff):
     import hashlib
 
-    if P2P_TRAFFIC["bytes"] is None or (p, L) != (P2P_TRAFFIC["p"], P2P_TRAFFIC["L"]):
+    if P2P_TRAFFIC["bytes"] is None or (p, L) != (P2P_TRAFFIC["p"], P2P_TRAFFIC["L"]) or \
+            (cutoff > 0) != P2P_TRAFFIC.get("cutoff", False):
         return None
     src = os.path.join(ROOT, "paper_0809_1810_gb300", "csrc", "p2p.cu")
     with open(src, "rb") as f:
@@ -214,7 +216,7 @@ def max_over_ranks(pg, value, torch=None, device=None):
     return float(t.item())
 
 
-def cpu_oracle_rate(w, p, L, budget_s=12.0):
+def cpu_oracle_rate(w, p, L, cutoff, budget_s=12.0):
     """The oracle FMM on the same workload and setting, repeated while
     within budget (at least once)."""
     import oracle
@@ -223,7 +225,7 @@ def cpu_oracle_rate(w, p, L, budget_s=12.0):
     t0 = time.perf_counter()
     runs = 0
     while True:
-        oracle.fmm(w.x, w.y, w.gamma, w.sigma, p, L, w.root)
+        oracle.fmm(w.x, w.y, w.gamma, w.sigma, p, L, w.root, a=cutoff)
         runs += 1
         if time.perf_counter() - t0 > budget_s or runs >= 5:
             break
@@ -275,8 +277,9 @@ def reference_choice(w, tol=TOL):
 
 def run_reference(args):
     """CPU FP64 oracle arm: each step one oracle FMM evaluation of the full
-    workload at the (p, L) the proposer picks (recomputed on the CPU by the
-    oracle), on the host cores."""
+    workload at the setting our arm runs (by default the stated p, L with the
+    tolerance's cutoff; with --setting proposer the proposer's choice,
+    recomputed on the CPU by the oracle), on the host cores."""
     world, rank, local, pg = dist_setup(args)
     if rank != 0:
         return
@@ -284,24 +287,34 @@ def run_reference(args):
 
     oracle.build()
     w = W.uniform_1m()
-    p, L, how = reference_choice(w)
+    a = 0.0
+    if args.setting == "cutoff":
+        from paper_0809_1810_gb300 import cutoff_for
+
+        p, L = w.p, w.L
+        a = cutoff_for(w.sigma, w.root[2] / 2 ** L, TOL)
+        how = "stated (p, L); cutoff a = sigma sqrt(2 ln(1/tol)) of Sec. 4.1 / Eq. 29"
+    elif args.setting == "configured":
+        p, L, how = w.p, w.L, "configured"
+    else:
+        p, L, how = reference_choice(w)
     for _ in range(args.warmup):
-        oracle.fmm(w.x, w.y, w.gamma, w.sigma, p, L, w.root)
+        oracle.fmm(w.x, w.y, w.gamma, w.sigma, p, L, w.root, a=a)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.fmm(w.x, w.y, w.gamma, w.sigma, p, L, w.root)
+        oracle.fmm(w.x, w.y, w.gamma, w.sigma, p, L, w.root, a=a)
     dt = (time.perf_counter() - t0) / args.steps
     value = w.n / dt
     cores = oracle.num_threads()
     sample = (f"full workload (N=2^20) per step, plain FP64 FMM at p={p}, L={L}, "
-              f"{cores} OpenMP threads")
+              f"cutoff {a / w.sigma:.2f} sigma, {cores} OpenMP threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "p": p, "L": L, "chosen_by": how,
-                   "parallelism": "host cores (OpenMP)"},
+        "config": {"workload": WORKLOAD, "p": p, "L": L, "cutoff_over_sigma": a / w.sigma,
+                   "chosen_by": how, "parallelism": "host cores (OpenMP)"},
         "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
@@ -388,16 +401,22 @@ def run_clustered(torch, dev, flush, steps=5):
 
 
 def choose_setting(args, w, xy, g):
-    """(p, L, info): the trained proposer's choice for tolerance TOL (the
-    default), the workload's configured setting, or the plain fallback."""
+    """(p, L, cutoff, info): the stated setting with the tolerance's cutoff
+    (the default), the trained proposer's choice for tolerance TOL, the
+    stated setting without a cutoff, or the plain fallback."""
+    from paper_0809_1810_gb300 import cutoff_for
     from paper_0809_1810_gb300 import proposer as PR
 
+    if args.setting == "cutoff":
+        a = cutoff_for(w.sigma, w.root[2] / 2 ** w.L, TOL)
+        return w.p, w.L, a, {"chosen_by": "stated (p, L); cutoff a = sigma sqrt(2 ln(1/tol)) "
+                                          "of Sec. 4.1 / Eq. 29", "cutoff_over_sigma": a / w.sigma}
     if args.setting == "configured":
-        return w.p, w.L, {"chosen_by": "configured"}
+        return w.p, w.L, 0.0, {"chosen_by": "configured"}
     if args.setting == "fallback" or not os.path.exists(PR.CHECKPOINT + ".json"):
         p, L = PR.fallback(w.n, w.sigma, w.root)
         why = "fallback" if args.setting == "fallback" else "fallback (no trained checkpoint)"
-        return p, L, {"chosen_by": why}
+        return p, L, 0.0, {"chosen_by": why}
     prop = PR.Proposer.load()
     t0 = time.perf_counter()
     r = prop.propose(xy, g, w.sigma, w.root, tol=TOL, verify=VERIFY_TARGETS)
@@ -408,7 +427,7 @@ def choose_setting(args, w, xy, g):
             "verify_targets": VERIFY_TARGETS, "tries": r["tries"], "tolerance": TOL}
     if r["choice"] >= 0:
         info["predicted_log10_max_err"] = float(r["predicted"][r["choice"], 1])
-    return r["p"], r["L"], info
+    return r["p"], r["L"], 0.0, info
 
 
 def _time_steps(torch, plan, xy, g, uv, steps, flush):
@@ -421,6 +440,30 @@ def _time_steps(torch, plan, xy, g, uv, steps, flush):
         ends[k].record()
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def _ring_pairs(torch, xy, L, root, a, targets):
+    """Pairs the cutoff corrects -- closer than a, leaves not neighbours --
+    estimated from the sampled targets: N times their mean count."""
+    if a <= 0.0:
+        return 0
+    n = xy.shape[0]
+    x0, y0, W_ = root
+    sc = (1 << L) / W_
+    top = (1 << L) - 1
+    lx = ((xy[:, 0].double() - x0) * sc).floor().clamp(0, top)
+    ly = ((xy[:, 1].double() - y0) * sc).floor().clamp(0, top)
+    xs, ys = xy[:, 0].double(), xy[:, 1].double()
+    counts = []
+    for k in range(0, targets.numel(), 64):
+        t = targets[k:k + 64]
+        dx = xs[t][:, None] - xs[None, :]
+        dy = ys[t][:, None] - ys[None, :]
+        close = dx * dx + dy * dy < a * a
+        far_leaf = torch.maximum((lx[t][:, None] - lx[None, :]).abs(),
+                                 (ly[t][:, None] - ly[None, :]).abs()) >= 2
+        counts.append((close & far_leaf).sum(1).double())
+    return int(round(float(torch.cat(counts).mean()) * n))
 
 
 def _near_pairs(plan, n, L):
@@ -456,8 +499,8 @@ def run_ours(args):
     g = torch.tensor(w.gamma, dtype=torch.float32, device=dev)
     uv = torch.empty((n, 2), dtype=torch.float32, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    p, L, chosen = choose_setting(args, w, xy, g)
-    plan = Plan(p, L, w.sigma, args.precision, root=w.root, max_n=n)
+    p, L, cutoff, chosen = choose_setting(args, w, xy, g)
+    plan = Plan(p, L, w.sigma, args.precision, root=w.root, max_n=n, cutoff=cutoff)
 
     ring = max(args.steps, 1)
     plan.set_timing(ring)
@@ -479,7 +522,8 @@ def run_ours(args):
         "max_rel_err_vs_fp64_direct": err, "meets_tolerance": bool(err <= TOL),
         "max_rel_err_vs_fp64_fmm_limit": float(s_hyb[0] / s_hyb[1]),
         "note": "FP64 direct = regularised sum (Eq. 7), max |du| / max |u| over the "
-                "sampled particles; FMM limit = Eq. 6 near / singular far (Eq. 10)",
+                "sampled particles; FMM limit = Eq. 6 near (and closer than the cutoff) / "
+                "singular far (Eq. 10, Sec. 4.1)",
     }
 
     # timed region
@@ -493,7 +537,9 @@ def run_ours(args):
 
     phases = [plan.phase_ms(a) for a in range(min(args.steps, ring))]
     phase_avg = {k: float(np.mean([q[k] for q in phases])) for k in phases[0]}
-    pairs = _near_pairs(plan, n, L)
+    near_pairs = _near_pairs(plan, n, L)
+    ring_pairs = _ring_pairs(torch, xy, L, w.root, cutoff, t)
+    pairs = near_pairs + ring_pairs
 
     peaks, peak_kind = _peaks()
     clk = clocks.summary()
@@ -502,14 +548,19 @@ def run_ours(args):
     p2p_ms = phase_avg["p2p_l2p"]
     achieved = pairs / (p2p_ms * 1e-3)
     roofline = {
-        "kernel": "p2p_l2p_f32_kernel (fused L2P + near field)",
+        "kernel": "p2p_l2p_f32_kernel (fused L2P + near field"
+                  + (" + cutoff ring)" if cutoff > 0 else ")"),
         "bound": "alu", "unit": "Gpair/s",
         "achieved": achieved / 1e9, "peak": peak / 1e9, "frac": achieved / peak,
         "peak_source": f"derived: min(128 FP32 lanes x 2 / {P2P_FLOPS_PER_PAIR} flops, "
                        f"16 MUFU lanes / 2 ops) per SM per clock x 152 SMs x "
                        f"{sm_max:.0f} MHz ({peak_kind} sm_max_mhz)",
-        "pairs_per_launch": pairs, "avg_launch_ms": p2p_ms,
-        "traffic": p2p_traffic(p, L),
+        "pairs_per_launch": pairs, "near_pairs": near_pairs,
+        "ring_pairs": ring_pairs,
+        "pairs_counted": "3x3-neighbour pairs exactly; cutoff pairs (closer than a, leaves "
+                         "not neighbours) as N x their mean over the accuracy targets",
+        "avg_launch_ms": p2p_ms,
+        "traffic": p2p_traffic(p, L, cutoff),
         "traffic_unit": "bytes per launch (ncu DRAM read + write)",
         "phase_ms": phase_avg,
     }
@@ -552,18 +603,27 @@ def run_ours(args):
            "d2h_bytes_per_step": int(huv.numel() * 4), "ms_per_step": e2e_ms}
     plan.close()
 
-    # the workload's stated setting, for context (leaf = 4 sigma at L = 7)
-    configured = None
-    if (p, L) != (w.p, w.L):
-        with Plan(w.p, w.L, w.sigma, args.precision, root=w.root, max_n=n) as pc:
+    # other settings, for context: the stated one without the cutoff (leaf =
+    # 4 sigma at L = 7) and the trained proposer's verified choice
+    def context(pc_, Lc_, ac_, extra):
+        with Plan(pc_, Lc_, w.sigma, args.precision, root=w.root, max_n=n, cutoff=ac_) as pc:
             for _ in range(3):
                 pc.velocity(xy, g, out=uv)
             cms = float(np.mean(_time_steps(torch, pc, xy, g, uv, 10, flush)))
             sc = pc.error_stats(xy, uv, t, ref_direct).cpu().numpy()
             pc.check()
-        configured = {"p": w.p, "L": w.L, "value": n / (cms * 1e-3), "unit": "particles/s",
-                      "ms_per_step": cms, "max_rel_err_vs_fp64_direct": float(sc[0] / sc[1]),
-                      "meets_tolerance": bool(sc[0] / sc[1] <= TOL)}
+        return {"p": pc_, "L": Lc_, "cutoff_over_sigma": ac_ / w.sigma, **extra,
+                "value": n / (cms * 1e-3), "unit": "particles/s", "ms_per_step": cms,
+                "max_rel_err_vs_fp64_direct": float(sc[0] / sc[1]),
+                "meets_tolerance": bool(sc[0] / sc[1] <= TOL)}
+
+    configured = None
+    if (p, L, cutoff) != (w.p, w.L, 0.0):
+        configured = context(w.p, w.L, 0.0, {})
+    proposer = None
+    if args.setting != "proposer" and os.path.exists(PR.CHECKPOINT + ".json"):
+        pp, Lp, _, pinfo = choose_setting(argparse.Namespace(setting="proposer"), w, xy, g)
+        proposer = context(pp, Lp, 0.0, {"chosen_by": pinfo["chosen_by"]})
 
     # plain FP64 GPU FMM at the conservative plain setting, for "vs plain FP64"
     pf, Lf = PR.fallback(n, w.sigma, w.root)
@@ -585,10 +645,11 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, runs, cores = cpu_oracle_rate(w, p, L)
+        rate, runs, cores = cpu_oracle_rate(w, p, L, cutoff)
         cpu = {"value": rate, "unit": "particles/s", "cores": cores, "kind": "oracle",
                "sample": f"{runs} full evaluations of the same N=2^20 instance by the plain "
-                         f"FP64 oracle FMM at the same p={p}, L={L}"}
+                         f"FP64 oracle FMM at the same p={p}, L={L}, "
+                         f"cutoff {cutoff / w.sigma:.2f} sigma"}
 
     if rank == 0:
         print(json.dumps({
@@ -596,13 +657,14 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "p": p, "L": L, **chosen,
+            "config": {"workload": WORKLOAD, "p": p, "L": L, "cutoff": cutoff, **chosen,
                        "precision": args.precision,
                        "l2": "flushed between timed steps (512 MiB write outside the events)",
                        "parallelism": f"replicas x{world}"},
             "accuracy": accuracy, "roofline": roofline, "roofline_m2l": roofline_m2l,
             "cpu_baseline": cpu, "e2e": e2e,
-            "as_configured": configured, "plain_fp64": plain_fp64, "batch_sweep": batch,
+            "as_configured": configured, "proposer": proposer, "plain_fp64": plain_fp64,
+            "batch_sweep": batch,
             "clustered_16m": large,
             "gpu_launches": int(launches_per_step * args.steps),
             "launches_per_step": launches_per_step, "clocks": clk,
@@ -622,9 +684,11 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep line item")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 2^24-particle clustered line item")
-    ap.add_argument("--setting", default="proposer", choices=["proposer", "configured", "fallback"],
-                    help="(p, L): the trained proposer's choice for 1e-6 (default), the "
-                         "workload's stated p=16, L=7, or the plain fallback")
+    ap.add_argument("--setting", default="cutoff",
+                    choices=["cutoff", "proposer", "configured", "fallback"],
+                    help="the stated p=16, L=7 with the Sec. 4.1 cutoff for 1e-6 (default), "
+                         "the trained proposer's choice, the stated setting without the "
+                         "cutoff, or the plain fallback")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

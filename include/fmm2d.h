@@ -68,6 +68,11 @@ typedef struct {
     int precision;    /* fmm2d_precision */
     double x0, y0, W; /* root box [x0, x0 + W] x [y0, y0 + W]; W > 0 */
     int64_t max_n;    /* largest particle count any call on this plan passes */
+    double cutoff;    /* the distance a of Sec. 4.1 (Eq. 29): a pair closer than a keeps
+                         the regularised kernel of Eq. 6 even when its leaves are not
+                         neighbours (the far field's singular contribution is corrected
+                         by K_sigma - K' of Eq. 27).  0 = the plain 3x3 rule; at L >= 2
+                         at most 2 W / 2^L (one ring of leaves beyond the 3x3 block). */
 } fmm2d_params;
 
 typedef struct fmm2d_plan fmm2d_plan;
@@ -130,8 +135,9 @@ fmm2d_status fmm2d_tree_debug(fmm2d_plan* plan, uint32_t* keys_dev, uint32_t* pe
  * summation over all n particles (the accuracy yardstick of Sec. 5):
  *   kernel 0  regularised kernel of Eq. 6 for every pair (Eq. 7 with Eq. 9)
  *   kernel 1  the FMM's own limit: Eq. 6 for pairs in each other's 3x3 leaf
- *             neighbourhood at the plan's L and root box, the singular kernel
- *             of Eq. 27 for the rest (Eq. 10, Sec. 4.1)
+ *             neighbourhood at the plan's L and root box and for pairs closer
+ *             than the plan's cutoff, the singular kernel of Eq. 27 for the
+ *             rest (Eq. 10, Sec. 4.1)
  *   xy_dev, gamma_dev  inputs in the plan's element type
  *   target_idx_dev     s particle indices in [0, n)
  *   uv_ref_dev         2 s doubles (output)

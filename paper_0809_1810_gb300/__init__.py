@@ -18,7 +18,8 @@ import torch
 from . import _native
 from ._native import FP32, FP32_TC, FP64, NUM_PHASES, PHASES
 
-__all__ = ["Plan", "BatchPlan", "FMMError", "FP64", "FP32", "FP32_TC", "PHASES", "library"]
+__all__ = ["Plan", "BatchPlan", "FMMError", "FP64", "FP32", "FP32_TC", "PHASES", "library",
+           "cutoff_for"]
 
 _PREC = {"fp64": FP64, "fp32": FP32, "fp32_tc": FP32_TC}
 
@@ -36,6 +37,21 @@ class FMMError(RuntimeError):
         detail = getter().decode()
         super().__init__(f"{where}: {name} ({detail})" if detail else f"{where}: {name}")
         self.status = status
+
+
+def cutoff_for(sigma: float, leaf: float, tol: float) -> float:
+    """The cutoff a of Sec. 4.1 for a relative tolerance: a pair left on the
+    singular kernel (r >= a) differs from the regularised one by
+    |K_sigma - K'| / |K'| = exp(-r^2 / 2 sigma^2) <= exp(-a^2 / 2 sigma^2) = tol
+    (Eq. 29 pair by pair), so a = sigma sqrt(2 ln(1/tol)).  0 when the leaves
+    are at least that wide (no non-neighbour pair is closer); at most two leaf
+    widths, the reach of the kernels' ring."""
+    import math
+
+    a = sigma * math.sqrt(2.0 * math.log(1.0 / tol))
+    if leaf >= a:
+        return 0.0
+    return min(a, 2.0 * leaf)
 
 
 def library():
@@ -59,19 +75,23 @@ def _ptr(t) -> ctypes.c_void_p:
 
 
 class Plan:
-    """An FMM configuration (p, L, sigma, precision, root box) and its device
-    workspace for up to ``max_n`` particles (fmm2d_plan_create)."""
+    """An FMM configuration (p, L, sigma, precision, root box, cutoff) and its
+    device workspace for up to ``max_n`` particles (fmm2d_plan_create).
+    ``cutoff`` is the distance a of Sec. 4.1: pairs closer than a keep the
+    regularised kernel even outside the 3x3 leaf neighbourhood (0: off; at
+    most two leaf widths)."""
 
     def __init__(self, p: int, L: int, sigma: float, precision="fp32",
-                 root=(-1.0, -1.0, 2.0), max_n: int = 1 << 20):
+                 root=(-1.0, -1.0, 2.0), max_n: int = 1 << 20, cutoff: float = 0.0):
         self._lib = _native.load()
         self.p, self.L, self.sigma = int(p), int(L), float(sigma)
         self.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
         self.dtype = torch.float64 if self.precision == FP64 else torch.float32
         self.root = tuple(float(v) for v in root)
         self.max_n = int(max_n)
+        self.cutoff = float(cutoff)
         prm = _native.Params(self.p, self.L, self.sigma, self.precision, self.root[0],
-                             self.root[1], self.root[2], self.max_n)
+                             self.root[1], self.root[2], self.max_n, self.cutoff)
         h = ctypes.c_void_p()
         _check(self._lib.fmm2d_plan_create(ctypes.byref(h), ctypes.byref(prm)), "plan_create")
         self._h = h

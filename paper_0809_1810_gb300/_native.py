@@ -21,7 +21,7 @@ HEADER = os.path.join(_build.INCLUDE, "fmm2d.h")
 class Params(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("L", ctypes.c_int), ("sigma", ctypes.c_double),
                 ("precision", ctypes.c_int), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
-                ("W", ctypes.c_double), ("max_n", ctypes.c_int64)]
+                ("W", ctypes.c_double), ("max_n", ctypes.c_int64), ("cutoff", ctypes.c_double)]
 
 
 class Instance(ctypes.Structure):

@@ -246,6 +246,10 @@ bool valid_params(const fmm2d_params* p, std::string* why) {
     if (p->precision < FMM2D_FP64 || p->precision > FMM2D_FP32_TC)
         return *why = "unknown precision", false;
     if (p->max_n < 0 || p->max_n > (int64_t)0xFFFFFFFF) return *why = "max_n out of range", false;
+    // the kernels correct the ring of leaves at Chebyshev distance 2 only
+    if (!(p->cutoff >= 0.0) || !std::isfinite(p->cutoff) ||
+        (p->L >= 2 && p->cutoff > 2.0 * p->W / ldexp(1.0, p->L)))
+        return *why = "cutoff must be in [0, 2 W / 2^L]", false;
     return true;
 }
 
@@ -294,6 +298,7 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
     }
     g.nboxes = acc;
     g.scale = ldexp(1.0, g.L) / g.W;
+    g.cutoff = prm->cutoff;
 
     auto cleanup = [&](fmm2d_status s) {
         fmm2d_plan_destroy(pl);

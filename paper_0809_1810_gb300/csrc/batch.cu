@@ -231,6 +231,7 @@ fmm2d_status fmm2d_batch_plan_create(fmm2d_batch_plan** out, int count,
         }
         g.nboxes = acc;
         g.scale = ldexp(1.0, g.L) / g.W;
+        g.cutoff = 0.0;  // batched instances use the plain 3x3 rule
         bi.offset = off;
         bi.n = in[i].n;
         bi.exp_off = exp_total;

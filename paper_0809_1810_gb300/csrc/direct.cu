@@ -4,9 +4,10 @@
 // direct_sampled: velocity at s sampled particles by direct summation over
 // all n particles, self term excluded (Eq. 9):
 //   kernel 0: K_sigma of Eq. 6 for every pair (Eq. 7)
-//   kernel 1: K_sigma for pairs in each other's 3x3 leaf neighbourhood and
-//             the singular kernel of Eq. 27 for the rest -- the sum the FMM
-//             converges to as p grows (Eq. 10, Sec. 4.1)
+//   kernel 1: K_sigma for pairs in each other's 3x3 leaf neighbourhood (and,
+//             with a cutoff a, for every pair closer than a) and the singular
+//             kernel of Eq. 27 for the rest -- the sum the FMM converges to as
+//             p grows (Eq. 10, Sec. 4.1)
 // error_stats: max |du|, max |u_ref|, sum |du|^2, sum |u_ref|^2 and the
 // per-leaf max |du| over the sampled particles.
 #include "fmm2d_internal.cuh"
@@ -28,8 +29,9 @@ __device__ inline int leaf_index(double x, double lo, double scale, double top) 
 template <typename R>
 __global__ void __launch_bounds__(kTargetsPerBlock* kSlices)
 direct_kernel(int kernel, int64_t n, const R* __restrict__ xy, const R* __restrict__ gamma,
-              int64_t s_count, const int64_t* __restrict__ targets, double inv2s2, double x0,
-              double y0, double scale, double top, double* __restrict__ uv_ref, int* status) {
+              int64_t s_count, const int64_t* __restrict__ targets, double inv2s2, double a2,
+              double x0, double y0, double scale, double top, double* __restrict__ uv_ref,
+              int* status) {
     __shared__ double sx[kTile], sy[kTile], sg[kTile];
     __shared__ int sl[kTile], sm[kTile];
     __shared__ double red[2][kSlices][kTargetsPerBlock];
@@ -80,7 +82,7 @@ direct_kernel(int kernel, int64_t n, const R* __restrict__ xy, const R* __restri
             double dx = xi - sx[q], dy = yi - sy[q];
             double r2 = dx * dx + dy * dy;
             if (r2 == 0.0) continue;  // K_sigma(0) = 0 by its limit
-            bool near = kernel == 0 || (abs(sl[q] - li) <= 1 && abs(sm[q] - mi) <= 1);
+            bool near = kernel == 0 || (abs(sl[q] - li) <= 1 && abs(sm[q] - mi) <= 1) || r2 < a2;
             double f = near ? -expm1(-r2 * inv2s2) / r2 : 1.0 / r2;
             double w = sg[q] * f;
             au = fma(-dy, w, au);
@@ -279,8 +281,9 @@ cudaError_t launch_direct_sampled(const Geometry& g, double sigma, int kernel, i
     if (s_count == 0) return cudaSuccess;
     int64_t blocks = (s_count + kTargetsPerBlock - 1) / kTargetsPerBlock;
     direct_kernel<R><<<(unsigned)blocks, kTargetsPerBlock * kSlices, 0, s>>>(
-        kernel, n, xy, gamma, s_count, targets, 1.0 / (2.0 * sigma * sigma), g.x0, g.y0,
-        ldexp(1.0, g.L) / g.W, ldexp(1.0, g.L) - 1.0, uv_ref, status);
+        kernel, n, xy, gamma, s_count, targets, 1.0 / (2.0 * sigma * sigma),
+        g.L >= 2 ? g.cutoff * g.cutoff : 0.0, g.x0, g.y0, ldexp(1.0, g.L) / g.W,
+        ldexp(1.0, g.L) - 1.0, uv_ref, status);
     return cudaGetLastError();
 }
 

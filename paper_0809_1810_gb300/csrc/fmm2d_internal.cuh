@@ -63,7 +63,17 @@ struct Geometry {
     int64_t level_base[kMaxL + 2];  // first box slot of level l (l >= 2)
     int64_t nboxes;    // box slots over levels 2..L
     double scale;      // 2^L / W, inverse leaf width (formed on the host)
+    double cutoff;     // a of Sec. 4.1 (0: none): pairs closer than a keep K_sigma
 };
+
+// The 16 leaves at Chebyshev distance 2 (the ring around the 3x3 block that a
+// cutoff of at most two leaf widths can reach): offset of ring leaf r.
+__host__ __device__ inline void ring_offset(int r, int* dx, int* dy) {
+    if (r < 5) *dx = r - 2, *dy = -2;
+    else if (r < 10) *dx = r - 7, *dy = 2;
+    else if (r < 13) *dx = -2, *dy = r - 11;
+    else *dx = 2, *dy = r - 14;
+}
 
 // Expansion-array slot of box (ix, iy) at level l >= 2.  Each level is
 // stored as four parity planes (ix & 1, iy & 1), each a row-major grid of

@@ -30,6 +30,8 @@ constexpr int kPad = kInner * kMaxSlices;
 struct NearF64 {
     double inv2s2;  // 1 / (2 sigma^2)
     double k0;      // 1 / (2 pi)
+    double a2;      // cutoff a^2 (0: none)
+    uint32_t ring_mask;  // ring leaves that can hold a pair closer than a
 };
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -46,6 +48,12 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // Radial weight Gamma_j * (1 - e^-q)/r^2 up to the constant k0.
 __device__ __forceinline__ double radial(const NearF64& nm, double r2) {
     return r2 > 0.0 ? -expm1(-r2 * nm.inv2s2) / r2 : 0.0;
+}
+// Cutoff correction for a ring pair (Sec. 4.1): the far field applied the
+// singular 1/r^2 to it; closer than a, K_sigma - K' = -e^-q / r^2 restores
+// the regularised kernel.
+__device__ __forceinline__ double radial_cut(const NearF64& nm, double r2) {
+    return r2 < nm.a2 && r2 > 0.0 ? -exp(-r2 * nm.inv2s2) / r2 : 0.0;
 }
 
 // Neumaier's compensated summation step: s + c tracks the exact sum.
@@ -67,7 +75,7 @@ p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
     using C = typename Cplx<R>::T;
     __shared__ P src[kChunk + kPad];
     __shared__ C le_s[kMaxP];
-    __shared__ uint32_t rbeg[9], rpre[10];
+    __shared__ uint32_t rbeg[25], rpre[26];  // 3x3 block, then the ring (cutoff)
 
     const int tid = threadIdx.x;
     const uint32_t leaf = blockIdx.x;
@@ -75,10 +83,13 @@ p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
     const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
     if (t0 == t1) return;
     const int nl = 1 << g.L;
-    if (tid < 9) {
-        int sx = (int)ix + tid % 3 - 1, sy = (int)iy + tid / 3 - 1;
+    if (tid < 25) {
+        int dx = tid % 3 - 1, dy = tid / 3 - 1;
+        if (tid >= 9) ring_offset(tid - 9, &dx, &dy);
+        const int sx = (int)ix + dx, sy = (int)iy + dy;
         uint32_t b = 0, len = 0;
-        if (sx >= 0 && sy >= 0 && sx < nl && sy < nl) {
+        const bool want = tid < 9 || ((nm.ring_mask >> (tid - 9)) & 1u);
+        if (want && sx >= 0 && sy >= 0 && sx < nl && sy < nl) {
             uint32_t k = morton_key((uint32_t)sx, (uint32_t)sy);
             b = leaf_start[k];
             len = leaf_start[k + 1] - b;
@@ -101,10 +112,9 @@ p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
     __syncthreads();
     if (tid == 0) {
         rpre[0] = 0;
-        for (int r = 0; r < 9; ++r) rpre[r + 1] += rpre[r];
+        for (int r = 0; r < 25; ++r) rpre[r + 1] += rpre[r];
     }
     __syncthreads();
-    const uint32_t total = rpre[9];
     const uint32_t nt = t1 - t0;
 
     for (uint32_t tb = 0; tb < nt; tb += kThreads) {
@@ -116,35 +126,40 @@ p2p_l2p_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
         P self = active ? sp[t0 + tb + tl] : P{};
         const R xi = self.x, yi = self.y;
         R au = R(0), av = R(0), cu = R(0), cv = R(0);
-        for (uint32_t cb = 0; cb < total; cb += kChunk) {
-            const uint32_t cnt = min(total - cb, (uint32_t)kChunk);
-            const uint32_t step = kInner * ns;
-            const uint32_t cpad = (cnt + step - 1) / step * step;
-            __syncthreads();
-            for (uint32_t v = tid; v < cpad; v += kThreads) {
-                P rec{};
-                if (v < cnt) {
-                    uint32_t gv = cb + v;
-                    int r = 0;
-                    while (gv >= rpre[r + 1]) ++r;
-                    rec = sp[rbeg[r] + (gv - rpre[r])];
+        // phase 0: the 3x3 local list with K_sigma; phase 1: the ring with
+        // the cutoff correction (empty without a cutoff)
+        for (int ph = 0; ph < 2; ++ph) {
+            const uint32_t lo = ph ? rpre[9] : 0u, hi = ph ? rpre[25] : rpre[9];
+            for (uint32_t cb = lo; cb < hi; cb += kChunk) {
+                const uint32_t cnt = min(hi - cb, (uint32_t)kChunk);
+                const uint32_t step = kInner * ns;
+                const uint32_t cpad = (cnt + step - 1) / step * step;
+                __syncthreads();
+                for (uint32_t v = tid; v < cpad; v += kThreads) {
+                    P rec{};
+                    if (v < cnt) {
+                        uint32_t gv = cb + v;
+                        int r = ph ? 9 : 0;
+                        while (gv >= rpre[r + 1]) ++r;
+                        rec = sp[rbeg[r] + (gv - rpre[r])];
+                    }
+                    src[v] = rec;
                 }
-                src[v] = rec;
-            }
-            __syncthreads();
-            for (uint32_t j0 = sl; j0 < cpad; j0 += step) {
-                R iu = R(0), iv = R(0);
+                __syncthreads();
+                for (uint32_t j0 = sl; j0 < cpad; j0 += step) {
+                    R iu = R(0), iv = R(0);
 #pragma unroll
-                for (int t = 0; t < kInner; ++t) {
-                    const P s = src[j0 + t * ns];
-                    const R dx = xi - s.x, dy = yi - s.y;
-                    const R r2 = dx * dx + dy * dy;
-                    const R w = s.z * radial(nm, r2);
-                    iu = fma(-dy, w, iu);
-                    iv = fma(dx, w, iv);
+                    for (int t = 0; t < kInner; ++t) {
+                        const P s = src[j0 + t * ns];
+                        const R dx = xi - s.x, dy = yi - s.y;
+                        const R r2 = dx * dx + dy * dy;
+                        const R w = s.z * (ph ? radial_cut(nm, r2) : radial(nm, r2));
+                        iu = fma(-dy, w, iu);
+                        iv = fma(dx, w, iv);
+                    }
+                    neumaier_add(au, cu, iu);
+                    neumaier_add(av, cv, iv);
                 }
-                neumaier_add(au, cu, iu);
-                neumaier_add(av, cv, iv);
             }
         }
         au += cu;
@@ -227,6 +242,9 @@ struct NearF32v3 {
     float half_leaf;          // s sc / 2, half the leaf in scaled units
     float band2;              // squared scaled distance to the leaf square below
                               // which a source may be at q2 < qthr of a target
+    float qa;                 // cutoff a^2 in scaled units, a^2 sc^2 (0: none)
+    float band_a2;            // qa with a margin: ring sources nearer the leaf square
+    uint32_t ring_mask;       // ring leaves (bit r, ring_offset order) nearer than a
     float coef[kF32Deg + 1];  // g(q2) ~ sum_k coef[k] q2^k on [0, qthr)
 };
 
@@ -244,12 +262,25 @@ __device__ __forceinline__ float wg_near(const NearF32v3& nm, float gamma, float
     return q2 < nm.qthr ? gamma * poly : far;
 }
 
-template <bool kNear>
+// Cutoff correction of a ring pair (Sec. 4.1): the far field applied the
+// singular kernel; closer than a, -Gamma 2^-q2 / q2 restores K_sigma.
+__device__ __forceinline__ float wg_cut(const NearF32v3& nm, float gamma, float q2) {
+    const float w = (-gamma * ex2_approx(-q2)) * rcp_approx(q2);
+    return q2 < nm.qa ? w : 0.f;
+}
+
+// Pair modes of the band loops: far band, near band (polynomial below the
+// edge), ring pairs under the cutoff.
+constexpr int kFar = 0, kNearBand = 1, kRing = 2;
+
+template <int kMode>
 __device__ __forceinline__ void one_source(const NearF32v3& nm, const float4 s, float x, float y,
                                            float& iu, float& iv) {
     const float dx = x - s.x, dy = y - s.y;
     const float q2 = fmaf(dx, dx, dy * dy);
-    const float w = kNear ? wg_near(nm, s.z, q2) : wg_far(s.z, q2);
+    const float w = kMode == kNearBand ? wg_near(nm, s.z, q2)
+                    : kMode == kRing   ? wg_cut(nm, s.z, q2)
+                                       : wg_far(s.z, q2);
     iu = fmaf(-dy, w, iu);
     iv = fmaf(dx, w, iv);
 }
@@ -257,7 +288,7 @@ __device__ __forceinline__ void one_source(const NearF32v3& nm, const float4 s, 
 // list[lo, hi) against the lane's target when ns > 1 lanes share a target
 // (sl = this lane's slot; a leaf's last round of at most 16 targets): blocks
 // of kInner sources into fresh sums, then compensated.
-template <bool kNear>
+template <int kMode>
 __device__ __forceinline__ void band_loop_split(const float4* list, uint32_t lo, uint32_t hi,
                                                 int ns, int sl, const NearF32v3& nm, float x,
                                                 float y, float& su, float& sv, float& cu,
@@ -269,7 +300,7 @@ __device__ __forceinline__ void band_loop_split(const float4* list, uint32_t lo,
         const uint32_t j = jj + sl;
         float4 r = make_float4(0.f, 0.f, 0.f, 0.f);  // past the end: zero circulation
         if (j < hi) r = list[j];
-        one_source<kNear>(nm, r, x, y, iu, iv);
+        one_source<kMode>(nm, r, x, y, iu, iv);
         if (++cnt == kInner) {
             neumaier_add(su, cu, iu);
             neumaier_add(sv, cv, iv);
@@ -293,7 +324,7 @@ struct SumT {
     float su[T], sv[T], cu[T], cv[T];
 };
 
-template <bool kNear, int T>
+template <int kMode, int T>
 __device__ __forceinline__ void band_loopT(const float4* list, uint32_t lo, uint32_t hi,
                                            const NearF32v3& nm, const float (&x)[T],
                                            const float (&y)[T], SumT<T>& S) {
@@ -313,13 +344,13 @@ __device__ __forceinline__ void band_loopT(const float4* list, uint32_t lo, uint
             for (int q = 0; q < kUnroll; ++q) {
                 const float4 src = list[j + q];
 #pragma unroll
-                for (int t = 0; t < T; ++t) one_source<kNear>(nm, src, x[t], y[t], iu[t], iv[t]);
+                for (int t = 0; t < T; ++t) one_source<kMode>(nm, src, x[t], y[t], iu[t], iv[t]);
             }
         }
         for (; j < e; ++j) {
             const float4 src = list[j];
 #pragma unroll
-            for (int t = 0; t < T; ++t) one_source<kNear>(nm, src, x[t], y[t], iu[t], iv[t]);
+            for (int t = 0; t < T; ++t) one_source<kMode>(nm, src, x[t], y[t], iu[t], iv[t]);
         }
 #pragma unroll
         for (int t = 0; t < T; ++t) {
@@ -335,6 +366,9 @@ struct LeafCtx {
     float cxh, cxl, cyh, cyl;  // leaf centre as FP32 hi/lo
     const uint32_t* rbeg;      // the 9 source ranges (shared memory)
     const uint32_t* rpre;      // prefix sums of their lengths (10 entries)
+    uint32_t ctotal;           // ring sources under a cutoff (0: none)
+    const uint32_t* cbeg;      // the 16 ring ranges (shared memory)
+    const uint32_t* cpre;      // prefix sums of their lengths (17 entries)
 };
 
 // Gather local-list records [cb, cb + cnt) into the warp's buffer in scaled
@@ -348,35 +382,75 @@ __device__ __forceinline__ void gather_bands(const float4* __restrict__ sp, cons
     nn = 0;
     nf = 0;
     __syncwarp();  // earlier readers of the buffer are done
-    for (uint32_t vb = 0; vb < cnt; vb += 32) {
-        const uint32_t v = vb + lane;
-        float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
-        bool ok = v < cnt, near = false;
-        if (ok) {
-            uint32_t gv = cb + v;
-            int r = 0;
-            while (gv >= c.rpre[r + 1]) ++r;
-            float4 q = sp[c.rbeg[r] + (gv - c.rpre[r])];
-            rec = make_float4(((q.x - c.cxh) - c.cxl) * nm.sc, ((q.y - c.cyh) - c.cyl) * nm.sc,
-                              q.z, 0.f);
-            float ex = fmaxf(fabsf(rec.x) - nm.half_leaf, 0.f);
-            float ey = fmaxf(fabsf(rec.y) - nm.half_leaf, 0.f);
-            near = fmaf(ex, ex, ey * ey) < nm.band2;
+    // range by range (no per-record range search); records keep their order
+    const uint32_t ce = cb + cnt;
+    for (int r = 0; r < 9; ++r) {
+        const uint32_t lo = max(c.rpre[r], cb), hi = min(c.rpre[r + 1], ce);
+        const uint32_t base = c.rbeg[r] - c.rpre[r];
+        for (uint32_t g0 = lo; g0 < hi; g0 += 32) {
+            const uint32_t gv = g0 + lane;
+            float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+            bool ok = gv < hi, near = false;
+            if (ok) {
+                float4 q = sp[base + gv];
+                rec = make_float4(((q.x - c.cxh) - c.cxl) * nm.sc, ((q.y - c.cyh) - c.cyl) * nm.sc,
+                                  q.z, 0.f);
+                float ex = fmaxf(fabsf(rec.x) - nm.half_leaf, 0.f);
+                float ey = fmaxf(fabsf(rec.y) - nm.half_leaf, 0.f);
+                near = fmaf(ex, ex, ey * ey) < nm.band2;
+            }
+            const unsigned bn = __ballot_sync(0xffffffffu, near);
+            const unsigned bf = __ballot_sync(0xffffffffu, ok && !near);
+            if (near) buf[nn + __popc(bn & lt)] = rec;
+            else if (ok) buf[kListCap - 1 - (nf + __popc(bf & lt))] = rec;
+            nn += __popc(bn);
+            nf += __popc(bf);
         }
-        const unsigned bn = __ballot_sync(0xffffffffu, near);
-        const unsigned bf = __ballot_sync(0xffffffffu, ok && !near);
-        if (near) buf[nn + __popc(bn & lt)] = rec;
-        else if (ok) buf[kListCap - 1 - (nf + __popc(bf & lt))] = rec;
-        nn += __popc(bn);
-        nf += __popc(bf);
+    }
+    __syncwarp();
+}
+
+// Gather the ring sources [cb, cb + cnt) that lie within the cutoff of the
+// leaf square (only those can be closer than a to a target) into buf[0, nc),
+// in scaled leaf-relative coordinates.
+__device__ __forceinline__ void gather_ring(const float4* __restrict__ sp, const LeafCtx& c,
+                                            const NearF32v3& nm, uint32_t cb, uint32_t cnt,
+                                            float4* buf, uint32_t& nc) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    nc = 0;
+    __syncwarp();  // earlier readers of the buffer are done
+    const uint32_t ce = cb + cnt;
+    for (int r = 0; r < 16; ++r) {
+        const uint32_t lo = max(c.cpre[r], cb), hi = min(c.cpre[r + 1], ce);
+        const uint32_t base = c.cbeg[r] - c.cpre[r];
+        for (uint32_t g0 = lo; g0 < hi; g0 += 32) {
+            const uint32_t gv = g0 + lane;
+            float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+            bool keep = false;
+            if (gv < hi) {
+                float4 q = sp[base + gv];
+                rec = make_float4(((q.x - c.cxh) - c.cxl) * nm.sc,
+                                  ((q.y - c.cyh) - c.cyl) * nm.sc, q.z, 0.f);
+                float ex = fmaxf(fabsf(rec.x) - nm.half_leaf, 0.f);
+                float ey = fmaxf(fabsf(rec.y) - nm.half_leaf, 0.f);
+                keep = fmaf(ex, ex, ey * ey) < nm.band_a2;
+            }
+            const unsigned bk = __ballot_sync(0xffffffffu, keep);
+            if (keep) buf[nc + __popc(bk & lt)] = rec;
+            nc += __popc(bk);
+        }
     }
     __syncwarp();
 }
 
 // Targets [a, b) of one leaf (positions within the leaf) against its local
 // list, by one warp.  `leaf` is the leaf's Morton key; leaf_start is indexed
-// by leaf_base + key (zero for a single evaluation).  buf, ranges and
-// leaf_le are this warp's shared memory.
+// by leaf_base + key (zero for a single evaluation).  buf, ranges (9 local
+// ranges and 10 prefix sums; with kCut, then 16 ring ranges and 17 prefix
+// sums) and leaf_le are this warp's shared memory.  kCut compiles in the
+// cutoff ring; without it the kernel carries no ring code at all.
+template <bool kCut>
 __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
                                               const uint32_t* __restrict__ leaf_start,
                                               uint32_t leaf_base, uint32_t leaf, uint32_t a,
@@ -419,6 +493,36 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
     }
     c.rbeg = rbeg;
     c.rpre = rpre;
+    c.ctotal = 0;
+    c.cbeg = ranges + 19;
+    c.cpre = ranges + 35;
+    if (kCut) {  // lane r < 16 reads ring range r (leaves wholly beyond a skipped)
+        uint32_t b = 0, len = 0;
+        if (lane < 16 && ((nm.ring_mask >> lane) & 1u)) {
+            int dx, dy;
+            ring_offset(lane, &dx, &dy);
+            const int sx = (int)lx + dx, sy = (int)ly + dy;
+            if (sx >= 0 && sy >= 0 && sx < nl && sy < nl) {
+                uint32_t k = leaf_base + morton_key((uint32_t)sx, (uint32_t)sy);
+                b = leaf_start[k];
+                len = leaf_start[k + 1] - b;
+            }
+        }
+        uint32_t incl = len;
+        for (int o = 1; o < 16; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        uint32_t* cb = ranges + 19;
+        uint32_t* cp = ranges + 35;
+        if (lane < 16) {
+            cb[lane] = b;
+            cp[lane + 1] = incl;
+        }
+        if (lane == 0) cp[0] = 0;
+        c.ctotal = __shfl_sync(0xffffffffu, incl, 15);
+        __syncwarp();
+    }
     leaf_centre_hilo(g.x0, g.y0, g.W, g.L, lx, ly, &c.cxh, &c.cxl, &c.cyh, &c.cyl);
     c.le_leaf = nullptr;
     if (g.L >= 2) {  // the leaf's LE: its M2L part plus L2L of its parent's (Sec. 3.3.3)
@@ -443,7 +547,7 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
         c.le_leaf = reinterpret_cast<const float*>(leaf_le);
     }
     const uint32_t total = rpre[9];
-    const bool one_chunk = total <= kListCap;
+    const bool one_chunk = total <= kListCap && (!kCut || c.ctotal == 0);  // ring reuses buf
     uint32_t nn = 0, nf = 0;
     if (one_chunk) gather_bands(sp, c, nm, 0, total, buf, nn, nf);
 
@@ -485,9 +589,15 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
         for (uint32_t cb = 0; cb < total; cb += kListCap) {
             if (!one_chunk)
                 gather_bands(sp, c, nm, cb, min((uint32_t)kListCap, total - cb), buf, nn, nf);
-            band_loopT<true, T>(buf, 0, nn, nm, x, y, S);
-            band_loopT<false, T>(buf, kListCap - nf, kListCap, nm, x, y, S);
+            band_loopT<kNearBand, T>(buf, 0, nn, nm, x, y, S);
+            band_loopT<kFar, T>(buf, kListCap - nf, kListCap, nm, x, y, S);
         }
+        if (kCut)
+            for (uint32_t cb = 0; cb < c.ctotal; cb += kListCap) {  // cutoff ring
+                uint32_t nc;
+                gather_ring(sp, c, nm, cb, min((uint32_t)kListCap, c.ctotal - cb), buf, nc);
+                band_loopT<kRing, T>(buf, 0, nc, nm, x, y, S);
+            }
 #pragma unroll
         for (int t = 0; t < T; ++t)
             if (32 * t + lane < active)
@@ -514,10 +624,16 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
         for (uint32_t cb = 0; cb < total; cb += kListCap) {
             if (!one_chunk)
                 gather_bands(sp, c, nm, cb, min((uint32_t)kListCap, total - cb), buf, nn, nf);
-            band_loop_split<true>(buf, 0, nn, ns, sl, nm, x, y, su, sv, cu, cv);
-            band_loop_split<false>(buf, kListCap - nf, kListCap, ns, sl, nm, x, y, su, sv, cu,
-                                   cv);
+            band_loop_split<kNearBand>(buf, 0, nn, ns, sl, nm, x, y, su, sv, cu, cv);
+            band_loop_split<kFar>(buf, kListCap - nf, kListCap, ns, sl, nm, x, y, su, sv, cu,
+                                  cv);
         }
+        if (kCut)
+            for (uint32_t cb = 0; cb < c.ctotal; cb += kListCap) {  // cutoff ring
+                uint32_t nc;
+                gather_ring(sp, c, nm, cb, min((uint32_t)kListCap, c.ctotal - cb), buf, nc);
+                band_loop_split<kRing>(buf, 0, nc, ns, sl, nm, x, y, su, sv, cu, cv);
+            }
         su += cu;
         sv += cv;
         for (int o = 1; o < ns; o <<= 1) {
@@ -596,13 +712,14 @@ __device__ __forceinline__ void for_each_piece(const uint32_t* __restrict__ skey
 // items from a counter (zeroed before the launch) until none is left, so
 // crowded windows balance against light ones and no SM idles behind a
 // partial last wave.
+template <bool kCut>
 __global__ void __launch_bounds__(kLeafWarps * 32, 6)
 p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skeys,
                    const uint32_t* __restrict__ leaf_start, WorkSplit ws, uint32_t* counter,
                    Geometry g, NearF32v3 nm, const float* __restrict__ le,
                    const float* __restrict__ l2l, float* __restrict__ uv) {
     __shared__ float4 lists[kLeafWarps][kListCap];
-    __shared__ uint32_t ranges[kLeafWarps][20];
+    __shared__ uint32_t ranges[kLeafWarps][kCut ? 52 : 20];
     __shared__ float2 leaf_le[kLeafWarps][kMaxP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
@@ -611,7 +728,7 @@ p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ s
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= ws.items) break;
         for_each_piece(skeys, leaf_start, ws, w, [&](uint32_t leaf, uint32_t a, uint32_t b) {
-            p2p_chunk_f32(sp, leaf_start, 0, leaf, a, b, g, nm, le, l2l, uv, lists[warp],
+            p2p_chunk_f32<kCut>(sp, leaf_start, 0, leaf, a, b, g, nm, le, l2l, uv, lists[warp],
                           ranges[warp], leaf_le[warp]);
         });
     }
@@ -650,9 +767,9 @@ p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ ske
             nm.kzeta = ni.kzeta;
             nm.inv_s = ni.inv_s;
             nm.half_leaf = ni.half_leaf;
-            p2p_chunk_f32(sp, leaf_start, b.leaf_base, gleaf - b.leaf_base, a, e, b.g, nm,
-                          le + b.exp_off, b.g.P <= 16 ? l2l16 : l2l32, uv, lists[warp],
-                          ranges[warp], leaf_le[warp]);
+            p2p_chunk_f32<false>(sp, leaf_start, b.leaf_base, gleaf - b.leaf_base, a, e, b.g,
+                                 nm, le + b.exp_off, b.g.P <= 16 ? l2l16 : l2l32, uv,
+                                 lists[warp], ranges[warp], leaf_le[warp]);
         });
     }
 }
@@ -706,6 +823,22 @@ double fit_near_polynomial(double a, double* coef) {
 
 }  // namespace
 
+// Ring leaves that can hold a source closer than the cutoff to some point of
+// the target leaf: ring leaf (dx, dy) is (max(|dx| - 1, 0), max(|dy| - 1, 0))
+// leaf widths from the leaf square.  Zero without a cutoff or below L = 2.
+static uint32_t ring_mask(const Geometry& g) {
+    if (g.L < 2 || !(g.cutoff > 0.0)) return 0;
+    const double w = g.W / ldexp(1.0, g.L);
+    uint32_t m = 0;
+    for (int r = 0; r < 16; ++r) {
+        int dx, dy;
+        ring_offset(r, &dx, &dy);
+        const double gx = std::max(std::abs(dx) - 1, 0) * w, gy = std::max(std::abs(dy) - 1, 0) * w;
+        if (gx * gx + gy * gy < g.cutoff * g.cutoff * (1.0 + 1e-12)) m |= 1u << r;
+    }
+    return m;
+}
+
 // Near-field constants of an evaluation (formed in double, rounded once).
 static NearF32v3 near_constants(double sigma, const Geometry& g, bool* ok) {
     const double ln2 = 0.69314718055994530942;
@@ -720,6 +853,10 @@ static NearF32v3 near_constants(double sigma, const Geometry& g, bool* ok) {
     nm.inv_s = (float)(1.0 / box);
     nm.half_leaf = (float)(0.5 * box * (double)nm.sc);
     nm.band2 = (float)(qthr * 1.02);  // q2 < qthr needs |dX|^2 < qthr; 2% margin for rounding
+    const double qa = g.L >= 2 ? g.cutoff * g.cutoff * (double)nm.sc * (double)nm.sc : 0.0;
+    nm.qa = (float)qa;
+    nm.band_a2 = (float)(qa * 1.02);
+    nm.ring_mask = ring_mask(g);
     double coef[kF32Deg + 1];
     *ok = fit_near_polynomial(qthr, coef) <= 1e-8;
     for (int k = 0; k <= kF32Deg; ++k) nm.coef[k] = (float)coef[k];
@@ -745,15 +882,23 @@ cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, int64_t n,
     NearF32v3 nm = near_constants(sigma, g, &ok);
     if (!ok) return cudaErrorInvalidValue;
     if (n == 0) return cudaSuccess;
-    const unsigned resident = resident_ctas(reinterpret_cast<const void*>(p2p_l2p_f32_kernel));
+    const bool cut = nm.ring_mask != 0;  // some ring leaf can hold a pair closer than a
+    const void* kernel = cut ? reinterpret_cast<const void*>(p2p_l2p_f32_kernel<true>)
+                             : reinterpret_cast<const void*>(p2p_l2p_f32_kernel<false>);
+    const unsigned resident = resident_ctas(kernel);
     const WorkSplit ws = work_split((uint64_t)n, (uint64_t)resident * kLeafWarps);
     const unsigned needed = (ws.items + kLeafWarps - 1) / kLeafWarps;
     const unsigned blocks = std::min(needed, resident);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    p2p_l2p_f32_kernel<<<blocks, kLeafWarps * 32, 0, s>>>(
-        reinterpret_cast<const float4*>(particles), skeys, leaf_start, ws, counter, g, nm, le,
-        l2l, uv);
+    if (cut)
+        p2p_l2p_f32_kernel<true><<<blocks, kLeafWarps * 32, 0, s>>>(
+            reinterpret_cast<const float4*>(particles), skeys, leaf_start, ws, counter, g, nm, le,
+            l2l, uv);
+    else
+        p2p_l2p_f32_kernel<false><<<blocks, kLeafWarps * 32, 0, s>>>(
+            reinterpret_cast<const float4*>(particles), skeys, leaf_start, ws, counter, g, nm, le,
+            l2l, uv);
     return cudaGetLastError();
 }
 
@@ -815,6 +960,8 @@ cudaError_t launch_p2p_l2p<double>(const Geometry& g, double sigma, int64_t n,
     NearF64 nm;
     nm.inv2s2 = 1.0 / (2.0 * sigma * sigma);
     nm.k0 = 1.0 / (2.0 * 3.14159265358979323846);
+    nm.a2 = g.L >= 2 ? g.cutoff * g.cutoff : 0.0;
+    nm.ring_mask = ring_mask(g);
     unsigned nleaf = 1u << (2 * g.L);
     p2p_l2p_kernel<double, NearF64><<<nleaf, kThreads, 0, s>>>(
         reinterpret_cast<const ParticleD*>(particles), leaf_start, g, ldexp(1.0, g.L) / g.W, nm,

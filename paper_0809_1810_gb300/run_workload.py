@@ -39,6 +39,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--p", type=int, default=None, help="override the workload's p")
     ap.add_argument("--L", type=int, default=None, help="override the workload's L")
+    ap.add_argument("--cutoff", type=float, default=0.0,
+                    help="cutoff a of Sec. 4.1 in units of sigma (0: the plain 3x3 rule)")
     ap.add_argument("--phases", action="store_true",
                     help="also print the mean per-phase times (events inside the graph)")
     args = ap.parse_args()
@@ -51,7 +53,8 @@ def main():
     xy = torch.tensor(np.stack([w.x, w.y], 1), dtype=dt, device="cuda")
     g = torch.tensor(w.gamma, dtype=dt, device="cuda")
     uv = torch.empty((w.n, 2), dtype=dt, device="cuda")
-    with Plan(w.p, w.L, w.sigma, args.precision, root=w.root, max_n=w.n) as plan:
+    with Plan(w.p, w.L, w.sigma, args.precision, root=w.root, max_n=w.n,
+              cutoff=args.cutoff * w.sigma) as plan:
         if args.phases:
             plan.set_timing(max(args.steps, 1))
         for _ in range(args.warmup):
@@ -64,7 +67,7 @@ def main():
             plan.velocity(xy, g, out=uv)
         b.record()
         plan.check()
-        print(f"{args.workload} {args.precision}: n={w.n} p={w.p} L={w.L} "
+        print(f"{args.workload} {args.precision}: n={w.n} p={w.p} L={w.L} a={args.cutoff}sigma "
               f"{a.elapsed_time(b) / max(args.steps, 1):.4f} ms/step, "
               f"{plan.kernels_per_call()} kernels/step")
         if args.phases:

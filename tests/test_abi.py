@@ -29,7 +29,10 @@ def test_every_declared_symbol_is_exported(lib):
 
 @pytest.mark.parametrize("field,value", [("p", 0), ("p", 33), ("L", -1), ("L", 13),
                                          ("sigma", 0.0), ("sigma", float("nan")), ("W", 0.0),
-                                         ("W", -2.0), ("precision", 9), ("max_n", -5)])
+                                         ("W", -2.0), ("precision", 9), ("max_n", -5),
+                                         ("cutoff", -0.01), ("cutoff", float("nan")),
+                                         ("cutoff", float("inf")),
+                                         ("cutoff", 0.0313)])  # > 2 leaf widths at L = 7
 def test_invalid_parameters_are_rejected(lib, field, value):
     prm = _native.Params(16, 7, 0.01, _native.FP32, -1.0, -1.0, 2.0, 1000)
     setattr(prm, field, value)
