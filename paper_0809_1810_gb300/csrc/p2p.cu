@@ -449,8 +449,14 @@ __device__ __forceinline__ void gather_ring(const float4* __restrict__ sp, const
 // by leaf_base + key (zero for a single evaluation).  buf, ranges (9 local
 // ranges and 10 prefix sums; with kCut, then 16 ring ranges and 17 prefix
 // sums) and leaf_le are this warp's shared memory.  kCut compiles in the
-// cutoff ring; without it the kernel carries no ring code at all.
-template <bool kCut>
+// cutoff ring; without it the kernel carries no ring code at all.  kMaxT is
+// the widest pass compiled in: 4 when chunks of 128 targets occur, else 2.
+// The cutoff kernel's hot code outgrows the instruction cache (its leading
+// stall is instruction fetch); with kMaxT = 2 it also runs a leaf's last
+// round of at most 16 targets as a one-per-lane pass, without the split
+// path: 10% faster at 64 targets per leaf.  (The plain kernel keeps both:
+// there the narrower build measured slower.)
+template <bool kCut, int kMaxT = 4>
 __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
                                               const uint32_t* __restrict__ leaf_start,
                                               uint32_t leaf_base, uint32_t leaf, uint32_t a,
@@ -604,14 +610,17 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
                 finish(rec[t], x[t], y[t], S.su[t] + S.cu[t], S.sv[t] + S.cv[t]);
     };
     uint32_t tb = a;
-    if (b - tb == 128) {  // 128 targets: four per lane, the list gathered once
+    if (kMaxT >= 4 && b - tb == 128) {  // 128 targets: four per lane, the list gathered once
         pass(std::integral_constant<int, 4>{}, tb, 128u);
         tb = b;
     }
     for (; tb + 64 <= b; tb += 64) pass(std::integral_constant<int, 2>{}, tb, 64u);
-    for (; tb + 16 < b; tb += 32)  // rounds of 17..32 targets, one per lane
+    // rounds of 17..32 targets, one per lane (in the narrow cutoff kernel
+    // every remaining round, which then needs no split-path code)
+    constexpr bool kNoSplit = kCut && kMaxT < 4;
+    for (; kNoSplit ? tb < b : tb + 16 < b; tb += 32)
         pass(std::integral_constant<int, 1>{}, tb, min(32u, b - tb));
-    if (tb < b) {  // a leaf's last round of at most 16 targets: ns lanes per target
+    if (!kNoSplit && tb < b) {  // a leaf's last round of at most 16 targets: ns lanes per target
         const uint32_t tc = b - tb;
         int ns = 2;  // lanes per target: largest power of two with tc * ns <= 32
         while (tc * (uint32_t)(2 * ns) <= 32u) ns *= 2;
@@ -712,7 +721,7 @@ __device__ __forceinline__ void for_each_piece(const uint32_t* __restrict__ skey
 // items from a counter (zeroed before the launch) until none is left, so
 // crowded windows balance against light ones and no SM idles behind a
 // partial last wave.
-template <bool kCut>
+template <bool kCut, int kMaxT>
 __global__ void __launch_bounds__(kLeafWarps * 32, 6)
 p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skeys,
                    const uint32_t* __restrict__ leaf_start, WorkSplit ws, uint32_t* counter,
@@ -728,7 +737,8 @@ p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ s
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= ws.items) break;
         for_each_piece(skeys, leaf_start, ws, w, [&](uint32_t leaf, uint32_t a, uint32_t b) {
-            p2p_chunk_f32<kCut>(sp, leaf_start, 0, leaf, a, b, g, nm, le, l2l, uv, lists[warp],
+            p2p_chunk_f32<kCut, kMaxT>(sp, leaf_start, 0, leaf, a, b, g, nm, le, l2l, uv,
+                                       lists[warp],
                           ranges[warp], leaf_le[warp]);
         });
     }
@@ -883,22 +893,31 @@ cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, int64_t n,
     if (!ok) return cudaErrorInvalidValue;
     if (n == 0) return cudaSuccess;
     const bool cut = nm.ring_mask != 0;  // some ring leaf can hold a pair closer than a
-    const void* kernel = cut ? reinterpret_cast<const void*>(p2p_l2p_f32_kernel<true>)
-                             : reinterpret_cast<const void*>(p2p_l2p_f32_kernel<false>);
-    const unsigned resident = resident_ctas(kernel);
+    auto kernel_of = [&](int max_t) {
+        return cut ? (max_t >= 4 ? reinterpret_cast<const void*>(p2p_l2p_f32_kernel<true, 4>)
+                                 : reinterpret_cast<const void*>(p2p_l2p_f32_kernel<true, 2>))
+                   : reinterpret_cast<const void*>(p2p_l2p_f32_kernel<false, 4>);
+    };
+    const unsigned resident = resident_ctas(kernel_of(4));
     const WorkSplit ws = work_split((uint64_t)n, (uint64_t)resident * kLeafWarps);
+    // chunks of 128 only with 128-target windows; the plain kernel stays wide
+    const int max_t = ws.span >= 128 || !cut ? 4 : 2;
+    if (resident_ctas(kernel_of(max_t)) != resident) return cudaErrorInvalidConfiguration;
     const unsigned needed = (ws.items + kLeafWarps - 1) / kLeafWarps;
     const unsigned blocks = std::min(needed, resident);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    if (cut)
-        p2p_l2p_f32_kernel<true><<<blocks, kLeafWarps * 32, 0, s>>>(
-            reinterpret_cast<const float4*>(particles), skeys, leaf_start, ws, counter, g, nm, le,
-            l2l, uv);
+    const float4* sp = reinterpret_cast<const float4*>(particles);
+    const dim3 grid(blocks), block(kLeafWarps * 32);
+    if (cut && max_t >= 4)
+        p2p_l2p_f32_kernel<true, 4><<<grid, block, 0, s>>>(sp, skeys, leaf_start, ws, counter, g,
+                                                           nm, le, l2l, uv);
+    else if (cut)
+        p2p_l2p_f32_kernel<true, 2><<<grid, block, 0, s>>>(sp, skeys, leaf_start, ws, counter, g,
+                                                           nm, le, l2l, uv);
     else
-        p2p_l2p_f32_kernel<false><<<blocks, kLeafWarps * 32, 0, s>>>(
-            reinterpret_cast<const float4*>(particles), skeys, leaf_start, ws, counter, g, nm, le,
-            l2l, uv);
+        p2p_l2p_f32_kernel<false, 4><<<grid, block, 0, s>>>(sp, skeys, leaf_start, ws, counter, g,
+                                                            nm, le, l2l, uv);
     return cudaGetLastError();
 }
 
