@@ -3,13 +3,15 @@
 Workload (one "step" = one full FMM evaluation, tree build to velocities):
 uniform positions in [-1, 1]^2, circulations h^2 N(0,1) with h = 2/1024,
 sigma = 2h, float32 inputs and arithmetic, M2L as a 3xTF32 tensor-core
-contraction (the FP32_TC form; --precision selects another), at the stated
-p = 16, L = 7.  Its leaves span only 4 sigma, so pairs closer than the
-cutoff a of Sec. 4.1 keep the regularised kernel: a = sigma sqrt(2 ln(1/tol))
-bounds the kernel error of every pair left on the singular kernel by the
-tolerance 1e-6 (Eq. 29).  --setting selects instead the trained proposer's
-choice, the stated setting without the cutoff, or the plain fallback; the
-first two are reported beside the headline.
+contraction (the FP32_TC form; --precision selects another).  The expansion
+order p and depth L are the trained proposer's choice for a max error of
+1e-6 relative to the largest speed against the FP64 direct sum, verified by
+direct-sum sampling.  Every candidate whose leaves are narrower than the
+cutoff a = sigma sqrt(2 ln(1/tol)) of Sec. 4.1 runs with it: pairs closer
+than a keep the regularised kernel, and every pair left on the singular one
+then differs from it by at most the tolerance (Eq. 29).  --setting selects
+instead the stated p = 16, L = 7 with the cutoff, the stated setting without
+it, or the plain fallback; the first two are reported beside the headline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -44,8 +46,9 @@ import workloads as W  # noqa: E402
 
 METRIC = "FMM particles/sec at ≤1e-6 max rel err vs FP64 direct; % roofline; vs plain FP64"
 WORKLOAD = ("uniform_1m: N=2^20 uniform in [-1,1]^2, Gamma=h^2 N(0,1), h=2/1024, sigma=2h; "
-            "stated p=16, L=7 with the Sec. 4.1 cutoff a=sigma sqrt(2 ln(1/tol)) for max rel "
-            "err <= 1e-6 vs the FP64 direct sum (the proposer's choice reported beside it)")
+            "(p, L) by the trained proposer for max rel err <= 1e-6 vs the FP64 direct sum, "
+            "with the Sec. 4.1 cutoff a=sigma sqrt(2 ln(1/tol)) where leaves are narrower "
+            "(the stated p=16, L=7 reported beside it)")
 TOL = 1e-6
 VERIFY_TARGETS = 2048  # particles at which the proposal is judged (other seed than ACC_TARGETS)
 ACC_TARGETS = 8192
@@ -62,7 +65,7 @@ P2P_FLOPS_PER_PAIR = 20
 # workload and setting; reported only while the kernel source is the one
 # captured (its SHA-256) and the setting matches.
 P2P_TRAFFIC = {"sha256_p2p_cu": "2e66ed8487df1c533ff60bbba5ff9fd28408a23a52c5b79f4d5e8e2407c43b16",
-               "p": 16, "L": 7, "cutoff": True, "bytes": 23732736}
+               "p": 15, "L": 7, "cutoff": True, "bytes": 23733248}
 
 
 def m2l_pairs(L):
@@ -242,20 +245,25 @@ def depth_candidates(n):
 
 
 def reference_choice(w, tol=TOL):
-    """(p, L, how) for the CPU arm: the proposer's verified choice for this
-    workload recorded in the checkpoint, else the decision recomputed on the
-    CPU from the checkpoint (the oracle's features, FP64 network with the
+    """(p, L, cutoff, how) for the CPU arm: the proposer's verified choice for
+    this workload recorded in the checkpoint, else the decision recomputed on
+    the CPU from the checkpoint (the oracle's features, FP64 network with the
     BF16 weights and selection rule, without the sampling check)."""
     from oracle import proposer as OP
+    from paper_0809_1810_gb300 import cutoff_for
+
+    def cut(L):
+        return cutoff_for(w.sigma, w.root[2] / 2 ** L, tol)
 
     head_path = os.path.join(ROOT, "paper_0809_1810_gb300", "data", "proposer.json")
     if not os.path.exists(head_path):
-        return w.p, w.L, "configured (no trained checkpoint)"
+        return w.p, w.L, cut(w.L), "configured (no trained checkpoint)"
     with open(head_path) as f:
         head = json.load(f)
     bc = head.get("benchmark_choice")
     if bc and bc.get("tolerance") == tol:
-        return int(bc["p"]), int(bc["L"]), "the proposer's verified choice recorded at training"
+        return (int(bc["p"]), int(bc["L"]), float(bc.get("cutoff", 0.0)),
+                "the proposer's verified choice recorded at training")
     params = np.fromfile(head_path[:-5] + ".f32", dtype="<f4")
     norm = (head["in_mean"], head["in_std"], head["out_mean"], head["out_std"])
     rows = []
@@ -273,14 +281,15 @@ def reference_choice(w, tol=TOL):
     L_floor = int(math.floor(math.log2(W_ / (6.0 * w.sigma)))) if W_ > 6 * w.sigma else 0
     fb = (20, max(0, min(10, L_occ, L_floor)))
     k, p, L = OP.propose(pred, cost, X[:, 0], X[:, 1], tol, head.get("margin", 0.5), fb)
-    return p, L, "oracle proposer" if k >= 0 else "fallback"
+    return p, L, cut(L), "oracle proposer" if k >= 0 else "fallback"
 
 
 def run_reference(args):
     """CPU FP64 oracle arm: each step one oracle FMM evaluation of the full
-    workload at the setting our arm runs (by default the stated p, L with the
-    tolerance's cutoff; with --setting proposer the proposer's choice,
-    recomputed on the CPU by the oracle), on the host cores."""
+    workload at the setting our arm runs (by default the proposer's verified
+    choice recorded in the checkpoint, else recomputed on the CPU by the
+    oracle; with --setting cutoff the stated p, L with the tolerance's
+    cutoff), on the host cores."""
     world, rank, local, pg = dist_setup(args)
     if rank != 0:
         return
@@ -298,7 +307,7 @@ def run_reference(args):
     elif args.setting == "configured":
         p, L, how = w.p, w.L, "configured"
     else:
-        p, L, how = reference_choice(w)
+        p, L, a, how = reference_choice(w)
     for _ in range(args.warmup):
         oracle.fmm(w.x, w.y, w.gamma, w.sigma, p, L, w.root, a=a)
     t0 = time.perf_counter()
@@ -428,7 +437,8 @@ def choose_setting(args, w, xy, g):
             "verify_targets": VERIFY_TARGETS, "tries": r["tries"], "tolerance": TOL}
     if r["choice"] >= 0:
         info["predicted_log10_max_err"] = float(r["predicted"][r["choice"], 1])
-    return r["p"], r["L"], 0.0, info
+    info["cutoff_over_sigma"] = r["cutoff"] / w.sigma
+    return r["p"], r["L"], r["cutoff"], info
 
 
 def _time_steps(torch, plan, xy, g, uv, steps, flush):
@@ -621,10 +631,14 @@ def run_ours(args):
     configured = None
     if (p, L, cutoff) != (w.p, w.L, 0.0):
         configured = context(w.p, w.L, 0.0, {})
+    stated_cut = None
+    ps, Ls, as_, _ = choose_setting(argparse.Namespace(setting="cutoff"), w, xy, g)
+    if (p, L, cutoff) != (ps, Ls, as_):
+        stated_cut = context(ps, Ls, as_, {})
     proposer = None
     if args.setting != "proposer" and os.path.exists(PR.CHECKPOINT + ".json"):
-        pp, Lp, _, pinfo = choose_setting(argparse.Namespace(setting="proposer"), w, xy, g)
-        proposer = context(pp, Lp, 0.0, {"chosen_by": pinfo["chosen_by"]})
+        pp, Lp, ap, pinfo = choose_setting(argparse.Namespace(setting="proposer"), w, xy, g)
+        proposer = context(pp, Lp, ap, {"chosen_by": pinfo["chosen_by"]})
 
     # plain FP64 GPU FMM at the conservative plain setting, for "vs plain FP64"
     pf, Lf = PR.fallback(n, w.sigma, w.root)
@@ -664,7 +678,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "accuracy": accuracy, "roofline": roofline, "roofline_m2l": roofline_m2l,
             "cpu_baseline": cpu, "e2e": e2e,
-            "as_configured": configured, "proposer": proposer, "plain_fp64": plain_fp64,
+            "as_configured": configured, "stated_with_cutoff": stated_cut,
+            "proposer": proposer, "plain_fp64": plain_fp64,
             "batch_sweep": batch,
             "clustered_16m": large,
             "gpu_launches": int(launches_per_step * args.steps),
@@ -685,11 +700,11 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep line item")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 2^24-particle clustered line item")
-    ap.add_argument("--setting", default="cutoff",
-                    choices=["cutoff", "proposer", "configured", "fallback"],
-                    help="the stated p=16, L=7 with the Sec. 4.1 cutoff for 1e-6 (default), "
-                         "the trained proposer's choice, the stated setting without the "
-                         "cutoff, or the plain fallback")
+    ap.add_argument("--setting", default="proposer",
+                    choices=["proposer", "cutoff", "configured", "fallback"],
+                    help="the trained proposer's verified choice for 1e-6 (default), the "
+                         "stated p=16, L=7 with the Sec. 4.1 cutoff, the stated setting "
+                         "without it, or the plain fallback")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

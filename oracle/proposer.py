@@ -202,15 +202,20 @@ def features(x, y, gamma, sigma, root, p, L) -> np.ndarray:
 def cost_terms(feat) -> np.ndarray:
     """Regressors of the linear cost model for one candidate row: 1, n,
     n p, boxes P^2 (boxes = (4^(L+1) - 1)/3 of the full tree, P = 16 for
-    p <= 16 else 32, the padded order of the translation kernels) and the
+    p <= 16 else 32, the padded order of the translation kernels), the
     near-field pair estimate 9 sum_b c_b^2 = 9 4^L mean^2 (1 + cv^2), read
-    off features 3-5."""
+    off features 3-5, and 16 sum_b c_b^2 for candidates whose leaves are
+    narrower than the cutoff a = sigma sqrt(2 ln 10^6) of Sec. 4.1 (feature
+    11, log10(leaf / sigma), below log10 sqrt(2 ln 10^6)): the scan of the
+    ring of leaves the cutoff reaches."""
     p, L = float(feat[0]), int(round(float(feat[1])))
     n = 2.0 ** float(feat[3])
     mean, cv = 2.0 ** float(feat[4]), float(feat[5])
     boxes = (4.0 ** (L + 1) - 1.0) / 3.0
     P = 16.0 if p <= 16 else 32.0
-    return np.array([1.0, n, n * p, boxes * P * P, 9.0 * 4.0 ** L * mean * mean * (1.0 + cv * cv)])
+    sum_c2 = 4.0 ** L * mean * mean * (1.0 + cv * cv)
+    ring = 16.0 * sum_c2 if float(feat[11]) < math.log10(math.sqrt(2.0 * math.log(1e6))) else 0.0
+    return np.array([1.0, n, n * p, boxes * P * P, 9.0 * sum_c2, ring])
 
 
 def propose(pred_max_log10, cost, cand_p, cand_L, tol, margin, fallback):

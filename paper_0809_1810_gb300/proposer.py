@@ -24,11 +24,22 @@ import os
 import numpy as np
 import torch
 
-from . import Plan, _check, _native, _ptr, _stream
+from . import Plan, _check, _native, _ptr, _stream, cutoff_for
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CHECKPOINT = os.path.join(HERE, "data", "proposer")
 FALLBACK_P = 20
+# Every candidate runs with the cutoff of Sec. 4.1 set for this tolerance:
+# a = sigma sqrt(2 ln(1/tol)) where the leaves are narrower (cutoff_for), so
+# the error surface learned is that of the method with the cutoff.
+CUTOFF_TOL = 1e-6
+# log10(leaf / sigma) below which a candidate runs with the cutoff
+CUTOFF_LOG10_LEAF = math.log10(math.sqrt(2.0 * math.log(1.0 / CUTOFF_TOL)))
+
+
+def cutoff(sigma: float, root, L: int) -> float:
+    """The cutoff a candidate at depth L runs with (0: none needed)."""
+    return cutoff_for(sigma, root[2] / 2.0 ** L, CUTOFF_TOL)
 ORDERS = tuple(range(4, 29))
 N_IN, N_OUT, N_PARAMS = _native.MLP_INPUTS, _native.MLP_OUTPUTS, _native.MLP_PARAMS
 FEATURE_NAMES = ("p", "L", "sigma_over_h", "log2_n", "log2_mean_per_leaf",
@@ -189,15 +200,18 @@ def fallback(n: int, sigma: float, root) -> tuple:
 def cost_terms(feat) -> np.ndarray:
     """Regressors of the cost model for one candidate row: a constant, n
     (tree build), n p (P2M, L2P), boxes x P^2 with P the padded order of the
-    translation kernels (M2M, M2L, L2L) and the near-field pair estimate
-    9 sum_b c_b^2 = 9 4^L mean^2 (1 + cv^2)."""
+    translation kernels (M2M, M2L, L2L), the near-field pair estimate
+    9 sum_b c_b^2 = 9 4^L mean^2 (1 + cv^2), and, for candidates that run
+    with the cutoff (log10(leaf / sigma) below CUTOFF_LOG10_LEAF), the ring
+    scan 16 sum_b c_b^2."""
     p, L = float(feat[0]), int(round(float(feat[1])))
     n = 2.0 ** float(feat[3])
     mean, cv = 2.0 ** float(feat[4]), float(feat[5])
     boxes = (4.0 ** (L + 1) - 1.0) / 3.0
     P = 16.0 if p <= 16 else 32.0
-    pairs = 9.0 * 4.0 ** L * mean * mean * (1.0 + cv * cv)
-    return np.array([1.0, n, n * p, boxes * P * P, pairs])
+    sum_c2 = 4.0 ** L * mean * mean * (1.0 + cv * cv)
+    ring = 16.0 * sum_c2 if float(feat[11]) < CUTOFF_LOG10_LEAF else 0.0
+    return np.array([1.0, n, n * p, boxes * P * P, 9.0 * sum_c2, ring])
 
 
 def fit_cost_model(feats, seconds) -> np.ndarray:
@@ -273,7 +287,7 @@ class Proposer:
         if not verify:
             m = self.margin if margin is None else float(margin)
             p, L, ch, pred = self._select(feats, cost, tol, m, fb)
-            out.update(p=p, L=L, choice=ch, predicted=pred)
+            out.update(p=p, L=L, cutoff=cutoff(sigma, root, L), choice=ch, predicted=pred)
             return out
         import workloads as W
 
@@ -287,17 +301,19 @@ class Proposer:
             pred = pred_k if pred is None else pred
             if ch < 0:
                 break
-            with Plan(p, L, sigma, precision, root=root, max_n=n) as plan:
+            a = cutoff(sigma, root, L)
+            with Plan(p, L, sigma, precision, root=root, max_n=n, cutoff=a) as plan:
                 uv = plan.velocity(xy, gamma)
                 st = plan.error_stats(xy, uv, tgt, ref).cpu().numpy()
                 plan.check()
             err = float(st[0] / st[1])
-            out["tries"].append({"p": p, "L": L, "err": err, "predicted": float(pred_k[ch, 1])})
+            out["tries"].append({"p": p, "L": L, "cutoff": a, "err": err,
+                                 "predicted": float(pred_k[ch, 1])})
             if err <= accept * tol:
-                out.update(p=p, L=L, choice=ch, predicted=pred, verified_err=err)
+                out.update(p=p, L=L, cutoff=a, choice=ch, predicted=pred, verified_err=err)
                 return out
             work[ch] = np.inf  # struck: the selection skips non-finite costs
-        out.update(p=fb[0], L=fb[1], choice=-1, predicted=pred)
+        out.update(p=fb[0], L=fb[1], cutoff=cutoff(sigma, root, fb[1]), choice=-1, predicted=pred)
         return out
 
 
@@ -354,7 +370,8 @@ def measure(w, orders=ORDERS, depths=None, targets: int = 1024, seed: int = 0,
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for L in depths:
         for p in orders:
-            with Plan(p, L, w.sigma, precision, root=w.root, max_n=n) as plan:
+            with Plan(p, L, w.sigma, precision, root=w.root, max_n=n,
+                      cutoff=cutoff(w.sigma, w.root, L)) as plan:
                 if ref is None:
                     ref = plan.direct_sampled(xy, g, tgt, kernel=0)
                 uv = plan.velocity(xy, g)

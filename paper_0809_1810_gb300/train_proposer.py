@@ -7,8 +7,10 @@ checkpoint.
 Rows: for each particle set (uniform, Lamb-Oseen lattice and clustered
 families in turn, n in {2^18, 2^19, 2^20}, sigma/h log-uniform in [0.6, 3]),
 every candidate p in 4..28 at every useful depth L is run through the
-FP32/tensor-core FMM and compared with the FP64 direct sum at 4096 sampled
-particles (Sec. 5.1's normalisation by the largest reference speed).  Each
+FP32/tensor-core FMM -- with the cutoff of Sec. 4.1 set for 1e-6 wherever the
+leaves are narrower than it (proposer.cutoff) -- and compared with the FP64
+direct sum at 4096 sampled particles (Sec. 5.1's normalisation by the
+largest reference speed).  Each
 set's rows are saved on their own (<rows-dir>/set_<index>.npy: 12 features,
 2 labels, seconds), so an interrupted run resumes where it stopped.
 
@@ -103,7 +105,8 @@ def main(argv=None):
     model = np.array([PR.cost_terms(r) @ coef for r in allrows[:, :12]])
     cost_rel = float(np.median(np.abs(model / allrows[:, 14] - 1.0)))
     meta = {"margin": margin, "cost_coef": coef.tolist(),
-            "cost_terms": ["1", "n", "n*p", "boxes*P^2", "9*sum c^2"],
+            "cost_terms": ["1", "n", "n*p", "boxes*P^2", "9*sum c^2", "16*sum c^2 (cutoff)"],
+            "cutoff_tolerance": PR.CUTOFF_TOL,
             "cost_median_rel_err": cost_rel, "train_rows": int(len(X)),
             "val_rows": int(len(Xv)), "sets": len(files), "val_rmse": val_rmse,
             "epochs": args.epochs, "batch": args.batch, "lr": args.lr, "seed": args.seed,
@@ -122,7 +125,8 @@ def main(argv=None):
     g = _t.tensor(wb.gamma, device="cuda")
     r = prop.propose(xy, g, wb.sigma, wb.root, tol=1e-6, verify=2048)
     meta["benchmark_choice"] = {"workload": "uniform_1m (seed 2)", "tolerance": 1e-6,
-                                "p": r["p"], "L": r["L"], "tries": r["tries"]}
+                                "p": r["p"], "L": r["L"], "cutoff": r["cutoff"],
+                                "tries": r["tries"]}
     net.save(args.out, meta)
     print(json.dumps({k: v for k, v in meta.items() if k != "cost_coef"}), flush=True)
     return 0

@@ -132,4 +132,10 @@ def test_proposer_fallback_rule():
     assert PR.depth_candidates(1 << 18) == [4, 5, 6, 7, 8]
     t = PR.cost_terms(np.array([16, 7, 0, 20, 6, 0.0, 1, 0, 0, 0, 0, 0], np.float32))
     np.testing.assert_allclose(t, [1, 2 ** 20, 16 * 2 ** 20, (4 ** 8 - 1) / 3 * 256,
-                                   9 * 4 ** 7 * 64 * 64])
+                                   9 * 4 ** 7 * 64 * 64, 16 * 4 ** 7 * 64 * 64])
+    # the cutoff each candidate runs with: a = sigma sqrt(2 ln 10^6) where the
+    # leaf is narrower, capped at two leaf widths
+    s = 2 * h
+    assert PR.cutoff(s, (-1.0, -1.0, 2.0), 6) == 0.0            # leaf = 8 sigma
+    assert abs(PR.cutoff(s, (-1.0, -1.0, 2.0), 7) / s - 5.2565) < 1e-4  # leaf = 4 sigma
+    assert PR.cutoff(s, (-1.0, -1.0, 2.0), 9) == 2.0 * 2.0 / 512  # capped

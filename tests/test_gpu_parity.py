@@ -172,16 +172,26 @@ def test_uniform_1m_full_size(prec):
 
 def test_uniform_1m_benchmark_setting():
     """The benchmark's timed configuration: the 2^20-particle workload at the
-    proposer's verified setting (p = 15, L = 6, leaves of 8 sigma), FP32_TC.
-    Every output against the oracle FMM at the same (p, L), and the metric's
-    bar -- max |du| <= 1e-6 max |u| against the oracle's regularised direct
-    sum -- at 256 seeded particles."""
+    proposer's verified setting recorded in the checkpoint (p, L and the
+    cutoff of Sec. 4.1 it runs with), FP32_TC.  Every output against the
+    oracle FMM at the same (p, L, a), and the metric's bar -- max |du| <= 1e-6
+    max |u| against the oracle's regularised direct sum -- at 256 seeded
+    particles."""
+    import json
+
+    from paper_0809_1810_gb300 import Plan
+    from paper_0809_1810_gb300 import proposer as PR
+
+    with open(PR.CHECKPOINT + ".json") as f:
+        bc = json.load(f)["benchmark_choice"]
     w = W.uniform_1m()
-    w.p, w.L = 15, 6
+    w.p, w.L = int(bc["p"]), int(bc["L"])
+    a = float(bc.get("cutoff", 0.0))
+    assert a == PR.cutoff(w.sigma, w.root, w.L)
     xy, g = _dev(w, torch.float32)
-    with _plan(w, "fp32_tc") as plan:
+    with Plan(w.p, w.L, w.sigma, "fp32_tc", root=w.root, max_n=w.n, cutoff=a) as plan:
         uv = plan.velocity(xy, g, check=True).double().cpu().numpy()
-    ref = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.p, w.L, w.root)
+    ref = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.p, w.L, w.root, a=a)
     assert _rel(uv, ref) <= FP32_TOL, _rel(uv, ref)
     t = W.sample_targets(w.n, 256, 12)
     o1 = oracle.direct(w.x, w.y, w.gamma, w.sigma, targets=t)

@@ -42,10 +42,10 @@ def proposer():
     return PR.Proposer.load()
 
 
-def _run(w, xy, g, p, L, tgt, ref, reps=5):
+def _run(w, xy, g, p, L, tgt, ref, reps=5, cutoff=0.0):
     from paper_0809_1810_gb300 import Plan
 
-    with Plan(p, L, w.sigma, "fp32_tc", root=w.root, max_n=w.n) as plan:
+    with Plan(p, L, w.sigma, "fp32_tc", root=w.root, max_n=w.n, cutoff=cutoff) as plan:
         uv = plan.velocity(xy, g)
         times = []
         for _ in range(reps):
@@ -81,8 +81,11 @@ def test_proposer_meets_tolerance_and_beats_the_plain_setting(proposer):
         with Plan(1, 0, w.sigma, "fp32", root=w.root, max_n=w.n) as any_plan:
             ref = any_plan.direct_sampled(xy, g, tgt, kernel=0)
         r = proposer.propose(xy, g, w.sigma, w.root, tol=TOL, verify=2048)
-        err, ms = _run(w, xy, g, r["p"], r["L"], tgt, ref)
+        # the proposer's candidates run with the cutoff of Sec. 4.1 where
+        # their leaves are narrower than it; the fallback's leaves never are
+        err, ms = _run(w, xy, g, r["p"], r["L"], tgt, ref, cutoff=r["cutoff"])
         fb = PR.fallback(w.n, w.sigma, w.root)
+        assert PR.cutoff(w.sigma, w.root, fb[1]) == 0.0
         err_fb, ms_fb = _run(w, xy, g, fb[0], fb[1], tgt, ref)
         L_occ = int(round(math.log(w.n / 64.0, 4)))
         err_un, ms_un = _run(w, xy, g, 20, L_occ, tgt, ref)

@@ -210,8 +210,18 @@ def test_selection_rule_on_a_worked_table():
 
 def test_cost_regressors_of_a_worked_row():
     # n = 2^20, L = 7, 64 per leaf, cv 0.5, p = 20 (padded to 32)
-    f = np.array([20, 7, 2.0, 20, 6, 0.5, 1, 0, 0, 0, 0, 0])
+    # leaf / sigma = 10^0.6 = 4.0 < 5.26: the candidate runs with the cutoff
+    f = np.array([20, 7, 2.0, 20, 6, 0.5, 1, 0, 0, 0, 0, 0.6])
     t = P.cost_terms(f)
     boxes = 1 + 4 + 16 + 64 + 256 + 1024 + 4096 + 16384
     np.testing.assert_allclose(t, [1, 2 ** 20, 20 * 2 ** 20, boxes * 32 * 32,
-                                   9 * 16384 * 64 * 64 * 1.25])
+                                   9 * 16384 * 64 * 64 * 1.25, 16 * 16384 * 64 * 64 * 1.25])
+    # leaves of 8 sigma: no cutoff, no ring term
+    f[11] = math.log10(8.0)
+    assert P.cost_terms(f)[5] == 0.0
+    # the switch sits where exp(-a^2 / 2 sigma^2) = 1e-6 puts a: one leaf width
+    a_over_sigma = math.sqrt(-2.0 * math.log(1e-6))
+    f[11] = math.log10(a_over_sigma) - 1e-9
+    assert P.cost_terms(f)[5] > 0
+    f[11] = math.log10(a_over_sigma) + 1e-9
+    assert P.cost_terms(f)[5] == 0.0
