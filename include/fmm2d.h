@@ -115,6 +115,24 @@ fmm2d_status fmm2d_velocity(fmm2d_plan* plan, int64_t n, const void* xy_dev,
 fmm2d_status fmm2d_velocity_host(fmm2d_plan* plan, int64_t n, const void* xy_host,
                                  const void* gamma_host, void* uv_host, cudaStream_t stream);
 
+/* Velocities at m evaluation points that carry no circulation, induced by n
+ * particles (the velocity field of Eq. 7 at arbitrary points z; the
+ * single-source experiment of Sec. 5.2 evaluates it on a lattice of such
+ * points).  The points enter the evaluation as particles of zero
+ * circulation: they induce nothing, take part in the tree, the near field
+ * and L2P like particles, and a point that coincides with a particle gets
+ * K_sigma(0) = 0 from it.
+ *   xy_dev, gamma_dev  n particles as in fmm2d_velocity (device)
+ *   txy_dev            m interleaved points (x, y) in the plan's element type,
+ *                      inside the root box (device)
+ *   tuv_dev            2 m velocities (u, v) at the points (device, output)
+ * Needs n + m <= max_n; uses the plan's staging buffers (allocated on the
+ * first host or target call), so calls on one plan must not overlap.
+ * Asynchronous on `stream`; input errors are reported by fmm2d_plan_check. */
+fmm2d_status fmm2d_velocity_targets(fmm2d_plan* plan, int64_t n, const void* xy_dev,
+                                    const void* gamma_dev, int64_t m, const void* txy_dev,
+                                    void* tuv_dev, cudaStream_t stream);
+
 /* Wait for `stream` and report (and clear) any input error the device
  * recorded during earlier calls on this plan. */
 fmm2d_status fmm2d_plan_check(fmm2d_plan* plan, cudaStream_t stream);

@@ -139,6 +139,25 @@ class Plan:
             self.check(stream)
         return out
 
+    def velocity_at(self, xy, gamma, targets, out=None, stream=None, check=False):
+        """Velocities (m, 2) at m points `targets` (m, 2) that carry no
+        circulation, induced by the particles (fmm2d_velocity_targets)."""
+        xy, gamma, n = self._inputs(xy, gamma)
+        if targets.dtype != self.dtype or not targets.is_cuda:
+            raise TypeError(f"targets must be {self.dtype} CUDA tensors")
+        targets = targets.contiguous()
+        m = targets.numel() // 2
+        if targets.numel() != 2 * m:
+            raise ValueError("targets must hold 2 m values")
+        if out is None:
+            out = torch.empty((m, 2), dtype=self.dtype, device=xy.device)
+        _check(self._lib.fmm2d_velocity_targets(self._h, n, _ptr(xy), _ptr(gamma), m,
+                                                _ptr(targets), _ptr(out), _stream(stream)),
+               "velocity_targets")
+        if check:
+            self.check(stream)
+        return out
+
     def velocity_host(self, xy, gamma, out, stream=None):
         """Host-buffer form (fmm2d_velocity_host): xy, gamma, out are CPU
         tensors (page-locked for asynchronous copies); synchronous."""

@@ -459,20 +459,26 @@ fmm2d_status fmm2d_plan_check(fmm2d_plan* pl, cudaStream_t stream) {
     return FMM2D_OK;
 }
 
+// Staging buffers for max_n particles (allocated on first use).
+static fmm2d_status ensure_staging(fmm2d_plan* pl) {
+    if (pl->st_xy) return FMM2D_OK;
+    size_t nm = (size_t)(pl->prm.max_n > 0 ? pl->prm.max_n : 1);
+    size_t bxy = align256(2 * nm * pl->elem), bg = align256(nm * pl->elem);
+    void* buf = nullptr;
+    CK(cudaMalloc(&buf, 2 * bxy + bg));
+    pl->st_xy = buf;
+    pl->st_gamma = static_cast<char*>(buf) + bxy;
+    pl->st_uv = static_cast<char*>(buf) + bxy + bg;
+    return FMM2D_OK;
+}
+
 fmm2d_status fmm2d_velocity_host(fmm2d_plan* pl, int64_t n, const void* xy_host,
                                  const void* gamma_host, void* uv_host, cudaStream_t stream) {
     if (!pl) return fail(FMM2D_INVALID_ARG, "null plan");
     if (n < 0 || n > pl->prm.max_n) return fail(FMM2D_INVALID_ARG, "n out of [0, max_n]");
     if (n > 0 && (!xy_host || !gamma_host || !uv_host)) return fail(FMM2D_INVALID_ARG, "null buffer");
-    if (!pl->st_xy) {
-        size_t nm = (size_t)(pl->prm.max_n > 0 ? pl->prm.max_n : 1);
-        size_t bxy = align256(2 * nm * pl->elem), bg = align256(nm * pl->elem);
-        void* buf = nullptr;
-        CK(cudaMalloc(&buf, 2 * bxy + bg));
-        pl->st_xy = buf;
-        pl->st_gamma = static_cast<char*>(buf) + bxy;
-        pl->st_uv = static_cast<char*>(buf) + bxy + bg;
-    }
+    fmm2d_status sst = ensure_staging(pl);
+    if (sst != FMM2D_OK) return sst;
     if (n > 0) {
         CK(cudaMemcpyAsync(pl->st_xy, xy_host, 2 * n * pl->elem, cudaMemcpyHostToDevice, stream));
         CK(cudaMemcpyAsync(pl->st_gamma, gamma_host, n * pl->elem, cudaMemcpyHostToDevice, stream));
@@ -482,6 +488,37 @@ fmm2d_status fmm2d_velocity_host(fmm2d_plan* pl, int64_t n, const void* xy_host,
     if (n > 0)
         CK(cudaMemcpyAsync(uv_host, pl->st_uv, 2 * n * pl->elem, cudaMemcpyDeviceToHost, stream));
     return fmm2d_plan_check(pl, stream);
+}
+
+fmm2d_status fmm2d_velocity_targets(fmm2d_plan* pl, int64_t n, const void* xy,
+                                    const void* gamma, int64_t m, const void* txy, void* tuv,
+                                    cudaStream_t stream) {
+    if (!pl) return fail(FMM2D_INVALID_ARG, "null plan");
+    if (n < 0 || m < 0 || n + m > pl->prm.max_n)
+        return fail(FMM2D_INVALID_ARG, "need n, m >= 0 and n + m <= max_n");
+    if ((n > 0 && (!xy || !gamma)) || (m > 0 && (!txy || !tuv)))
+        return fail(FMM2D_INVALID_ARG, "null buffer");
+    fmm2d_status sst = ensure_staging(pl);
+    if (sst != FMM2D_OK) return sst;
+    // particles, then the targets as particles of zero circulation: they
+    // induce nothing and receive the velocity at their positions
+    char* sxy = static_cast<char*>(pl->st_xy);
+    char* sg = static_cast<char*>(pl->st_gamma);
+    const size_t e = pl->elem;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(sxy, xy, 2 * n * e, cudaMemcpyDeviceToDevice, stream));
+        CK(cudaMemcpyAsync(sg, gamma, n * e, cudaMemcpyDeviceToDevice, stream));
+    }
+    if (m > 0) {
+        CK(cudaMemcpyAsync(sxy + 2 * n * e, txy, 2 * m * e, cudaMemcpyDeviceToDevice, stream));
+        CK(cudaMemsetAsync(sg + n * e, 0, m * e, stream));  // +0.0 in either precision
+    }
+    fmm2d_status st = run(pl, n + m, pl->st_xy, pl->st_gamma, pl->st_uv, stream);
+    if (st != FMM2D_OK) return st;
+    if (m > 0)
+        CK(cudaMemcpyAsync(tuv, static_cast<char*>(pl->st_uv) + 2 * n * e, 2 * m * e,
+                           cudaMemcpyDeviceToDevice, stream));
+    return FMM2D_OK;
 }
 
 fmm2d_status fmm2d_tree_debug(fmm2d_plan* pl, uint32_t* keys, uint32_t* perm,

@@ -47,6 +47,8 @@ def test_null_arguments_are_rejected(lib):
     assert lib.fmm2d_plan_create(None, None) == _native.INVALID_ARG
     assert lib.fmm2d_velocity(None, 0, None, None, None, None) == _native.INVALID_ARG
     assert lib.fmm2d_plan_check(None, None) == _native.INVALID_ARG
+    assert lib.fmm2d_velocity_targets(None, 0, None, None, 0, None, None, None) == \
+        _native.INVALID_ARG
     assert lib.fmm2d_plan_set_timing(None, 4) == _native.INVALID_ARG
     lib.fmm2d_plan_destroy(None)  # accepted
 
