@@ -342,6 +342,28 @@ def test_kernel_error_grows_as_leaves_shrink(oracle_lib):
     assert errs[0] < 1e-8 and errs[2] > 1e-4, errs
 
 
+def test_domain_size_series_kernel_error_falls(oracle_lib):
+    """Sec. 5.1 / Fig. 19: at a fixed lattice spacing (sigma = 0.02, h = 0.8
+    sigma) and level 4, a larger domain has wider leaves (3.2, 4.4, 6.9
+    sigma) and the far field farther away, so the error against the direct
+    sum -- there the kernel substitution of Sec. 4.1 -- falls by orders of
+    magnitude; at p = 19 truncation stays below it, and the Eq. 29 estimate
+    at the leaf width bounds it where it dominates."""
+    errs = []
+    for side in (63, 88, 138):
+        w = W.lamb_oseen_fixed_spacing(side, p=19, L=4)
+        d = oracle_lib.direct(w.x, w.y, w.gamma, w.sigma)
+        f = oracle_lib.fmm(w.x, w.y, w.gamma, w.sigma, w.p, w.L, w.root)
+        m = np.linalg.norm(d, axis=1).max()
+        errs.append(np.linalg.norm(f - d, axis=1).max() / m)
+        leaf = w.root[2] / 16
+        est = math.exp(-leaf ** 2 / (2 * w.sigma ** 2)) * np.abs(w.gamma).sum() / (
+            2 * math.pi * leaf) / m
+        if leaf / w.sigma < 5:
+            assert errs[-1] <= est
+    assert errs[0] > 100 * errs[1] > 100 * 10 * errs[2], errs
+
+
 def test_single_source_near_domain_is_exact(oracle_lib):
     """Sec. 5.2: with one source at the centre, evaluation points in the
     source leaf's local list see machine error (computed directly), the rest

@@ -72,6 +72,24 @@ def lamb_oseen_lattice(n_side: int, nu_t: float = 0.05, gamma0: float = 1.0,
                     extra={"nu_t": nu_t, "gamma0": gamma0})
 
 
+def lamb_oseen_fixed_spacing(n_side: int, h: float = 0.016, sigma: float = 0.02,
+                             nu_t: float = 0.0005 * 4, gamma0: float = 1.0, p: int = 13,
+                             L: int = 4, dtype=np.float64) -> Workload:
+    """The Lamb-Oseen setup of Sec. 5.1 at a fixed lattice spacing: sigma =
+    0.02, h / sigma = 0.8, nu = 0.0005, t = 4; the square domain grows with
+    the particle count (side n_side h, centred on the vortex), as in the
+    domain-size series of Fig. 19 (63^2, 88^2, 138^2 particles).  The root box
+    is the domain."""
+    side = n_side * h
+    root = (-0.5 * side, -0.5 * side, side)
+    x, y, _ = lattice_coords(n_side, root)
+    r2 = x * x + y * y
+    g = h * h * gamma0 / (4.0 * math.pi * nu_t) * np.exp(-r2 / (4.0 * nu_t))
+    return Workload(f"lamb_oseen_{n_side}x{n_side}_h{h:g}", x.astype(dtype), y.astype(dtype),
+                    g.astype(dtype), sigma, p, L, h, root=root,
+                    extra={"nu_t": nu_t, "gamma0": gamma0})
+
+
 def uniform_random(n: int, seed: int, h: float, sigma_over_h: float = 2.0, p: int = 16,
                    L: int = 7, dtype=np.float32) -> Workload:
     rng = np.random.Generator(np.random.PCG64(seed))
