@@ -324,14 +324,15 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
         align256(tab_count * 4),                              // tables fp32
         align256((size_t)(2 * g.P + 1) * (2 * g.P + 1) * 8),  // binomials
         256,                                                  // status, work counter
+        align256(((size_t)1 << g.L) * sizeof(float4)),        // leaf-centre table
     };
     size_t total = 0;
     for (size_t s : sizes) total += s;
     cudaError_t e = cudaMalloc(&pl->ws, total);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "workspace cudaMalloc"));
     char* p = static_cast<char*>(pl->ws);
-    void* slots[14];
-    for (int i = 0; i < 14; ++i) {
+    void* slots[15];
+    for (int i = 0; i < 15; ++i) {
         slots[i] = p;
         p += sizes[i];
     }
@@ -351,6 +352,7 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
     pl->d_status = (int*)slots[13];
     pl->p2p_counter = reinterpret_cast<uint32_t*>(static_cast<char*>(slots[13]) + 128);
     pl->sb.status = pl->d_status;
+    float4* centres = (float4*)slots[14];
 
     e = cudaHostAlloc((void**)&pl->h_status, sizeof(int), cudaHostAllocDefault);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaHostAlloc"));
@@ -363,8 +365,10 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
                                 binom, pl->cap);
     }
     if (e == cudaSuccess) e = launch_tables_to_f32(pl->tab64, pl->tab32, (int64_t)tab_count, pl->cap);
+    if (e == cudaSuccess) e = launch_centre_table(g, centres, pl->cap);
     if (e == cudaSuccess) e = cudaStreamSynchronize(pl->cap);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "table build"));
+    g.centre_tab = centres;  // the kernels read leaf centres from the table
     for (int k = 0; k <= kPhases; ++k) {
         e = cudaEventCreate(&pl->ev_mark[k]);
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaEventCreate"));

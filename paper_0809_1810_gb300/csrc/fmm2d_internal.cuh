@@ -64,6 +64,9 @@ struct Geometry {
     int64_t nboxes;    // box slots over levels 2..L
     double scale;      // 2^L / W, inverse leaf width (formed on the host)
     double cutoff;     // a of Sec. 4.1 (0: none): pairs closer than a keep K_sigma
+    // leaf centres per axis index as FP32 hi/lo pairs, (x hi, x lo, y hi, y lo)
+    // at index i, built once per plan (null: computed where needed)
+    const float4* centre_tab;
 };
 
 // The 16 leaves at Chebyshev distance 2 (the ring around the 3x3 block that a
@@ -122,6 +125,9 @@ struct Tables {
 cudaError_t launch_build_tables(int p, int P, double* m2m, double* l2l, double* m2l,
                                 double* binom_scratch, cudaStream_t s);
 cudaError_t launch_tables_to_f32(const double* src, float* dst, int64_t count, cudaStream_t s);
+// Leaf-centre table of a plan: entry i = (x hi, x lo, y hi, y lo) of the
+// centre coordinates x0 + (i + 1/2) s and y0 + (i + 1/2) s, i < 2^L.
+cudaError_t launch_centre_table(const Geometry& g, float4* tab, cudaStream_t s);
 
 // Sorted keys after an LSD sort of key_bits-bit keys (kRadixBits per pass):
 // the buffer the last pass wrote.
@@ -299,20 +305,34 @@ __device__ inline unsigned segment_mask(int G) {
     return G == 32 ? 0xffffffffu : (0xffffu << (lane & 16));
 }
 
-// Centre of leaf (ix, iy) at level L as an FP32 hi/lo pair, formed in FP64
-// by lane 0 of the warp and broadcast (FP64 is slow; this is its only use).
-// Every lane of the warp must call it.
-__device__ inline void leaf_centre_hilo(double x0, double y0, double W, int L, uint32_t ix,
-                                        uint32_t iy, float* cxh, float* cxl, float* cyh,
-                                        float* cyl) {
+// Leaf-centre coordinate x0 + (i + 1/2) s, s = W 2^-L, formed in FP64 with
+// every rounding explicit (no contraction, so the per-plan table and the
+// direct computation agree bit for bit), split into an FP32 hi/lo pair.
+__device__ inline void centre_hilo_1d(double x0, double W, int L, uint32_t i, float* hi,
+                                      float* lo) {
+    const double s = W * ldexp(1.0, -L);
+    const double c = __dadd_rn(x0, __dmul_rn((double)i + 0.5, s));
+    *hi = (float)c;
+    *lo = (float)__dsub_rn(c, (double)*hi);
+}
+
+// Centre of leaf (ix, iy) as FP32 hi/lo pairs: from the plan's table when it
+// has one, else computed in FP64 by lane 0 of the warp and broadcast (FP64 is
+// slow on this part).  Every lane of the warp must call it.
+__device__ inline void leaf_centre_hilo(const Geometry& g, uint32_t ix, uint32_t iy, float* cxh,
+                                        float* cxl, float* cyh, float* cyl) {
+    if (g.centre_tab) {
+        const float4 a = g.centre_tab[ix], b = g.centre_tab[iy];
+        *cxh = a.x;
+        *cxl = a.y;
+        *cyh = b.z;
+        *cyl = b.w;
+        return;
+    }
     float v[4] = {0.f, 0.f, 0.f, 0.f};
     if ((threadIdx.x & 31) == 0) {
-        double s = W * ldexp(1.0, -L);
-        double cx = x0 + ((double)ix + 0.5) * s, cy = y0 + ((double)iy + 0.5) * s;
-        v[0] = (float)cx;
-        v[1] = (float)(cx - (double)v[0]);
-        v[2] = (float)cy;
-        v[3] = (float)(cy - (double)v[2]);
+        centre_hilo_1d(g.x0, g.W, g.L, ix, &v[0], &v[1]);
+        centre_hilo_1d(g.y0, g.W, g.L, iy, &v[2], &v[3]);
     }
     *cxh = __shfl_sync(0xffffffffu, v[0], 0);
     *cxl = __shfl_sync(0xffffffffu, v[1], 0);

@@ -529,7 +529,7 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
         c.ctotal = __shfl_sync(0xffffffffu, incl, 15);
         __syncwarp();
     }
-    leaf_centre_hilo(g.x0, g.y0, g.W, g.L, lx, ly, &c.cxh, &c.cxl, &c.cyh, &c.cyl);
+    leaf_centre_hilo(g, lx, ly, &c.cxh, &c.cxl, &c.cyh, &c.cyl);
     c.le_leaf = nullptr;
     if (g.L >= 2) {  // the leaf's LE: its M2L part plus L2L of its parent's (Sec. 3.3.3)
         const float2* own = reinterpret_cast<const float2*>(

@@ -107,7 +107,24 @@ __global__ void to_f32_kernel(const double* src, float* dst, int64_t count) {
         dst[i] = (float)src[i];
 }
 
+// One thread per axis index: the same FP64 arithmetic as the direct
+// computation (centre_hilo_1d), so the table holds the same bits.
+__global__ void centre_table_kernel(Geometry g, float4* tab) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (1u << g.L)) return;
+    float4 v;
+    centre_hilo_1d(g.x0, g.W, g.L, i, &v.x, &v.y);
+    centre_hilo_1d(g.y0, g.W, g.L, i, &v.z, &v.w);
+    tab[i] = v;
+}
+
 }  // namespace
+
+cudaError_t launch_centre_table(const Geometry& g, float4* tab, cudaStream_t s) {
+    const int n = 1 << g.L;
+    centre_table_kernel<<<(n + 255) / 256, 256, 0, s>>>(g, tab);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_build_tables(int p, int P, double* m2m, double* l2l, double* m2l,
                                 double* binom_scratch, cudaStream_t s) {

@@ -41,7 +41,7 @@ __device__ __forceinline__ void p2m_quad(const typename ParticleOf<R>::type* __r
     R cxh, cxl, cyh, cyl;
     if (sizeof(R) == 4) {
         float a0, a1, a2, a3;
-        leaf_centre_hilo(g.x0, g.y0, g.W, g.L, ix, iy, &a0, &a1, &a2, &a3);
+        leaf_centre_hilo(g, ix, iy, &a0, &a1, &a2, &a3);
         cxh = a0;
         cxl = a1;
         cyh = a2;
