@@ -17,6 +17,8 @@ Functions and the paper passage each follows:
 * :func:`fmm` -- O3, the plain FMM in the order of Sec. 3.1 / Fig. 3, with the
   same optional cutoff.
 * ``op_*`` -- single expansions and translations: Eqs. 20-22, Secs. 3.3.2-3.3.3.
+* :func:`convect` -- one convection step of Eq. 5 (forward Euler or Heun)
+  on a given velocity function.
 * :func:`kernel_error_estimate` -- Eq. 29 (squared-distance reading).
 * :func:`truncation_bound` -- Eqs. 30-31 (geometric-tail reading).
 
@@ -253,3 +255,19 @@ def kernel_error_estimate(a, sigma, sum_gamma):
 
 def truncation_bound(A, b, p, dist):
     return float(_load().orc_truncation_bound(A, b, p, dist))
+
+
+def convect(x, y, gamma, dt, velocity, order=2):
+    """One convection step of the vortex method (Eq. 5, dx_i/dt = u(x_i)),
+    with `velocity(x, y) -> (n, 2)` the velocity at the particles: forward
+    Euler (order 1) or Heun's explicit trapezoid rule (order 2).  Returns the
+    new (x, y) in float64."""
+    x, y = _f64(x), _f64(y)
+    u1 = velocity(x, y)
+    if order == 1:
+        return x + dt * u1[:, 0], y + dt * u1[:, 1]
+    if order != 2:
+        raise ValueError("order must be 1 or 2")
+    xs, ys = x + dt * u1[:, 0], y + dt * u1[:, 1]
+    u2 = velocity(xs, ys)
+    return x + 0.5 * dt * (u1[:, 0] + u2[:, 0]), y + 0.5 * dt * (u1[:, 1] + u2[:, 1])
