@@ -115,6 +115,21 @@ fmm2d_status fmm2d_velocity(fmm2d_plan* plan, int64_t n, const void* xy_dev,
 fmm2d_status fmm2d_velocity_host(fmm2d_plan* plan, int64_t n, const void* xy_host,
                                  const void* gamma_host, void* uv_host, cudaStream_t stream);
 
+/* One explicit step of the convection part of the vortex method, Eq. 5
+ * (dx_i/dt = u(x_i) with u from the FMM of this plan), in place:
+ *   order 1  forward Euler, x' = x + dt u(x)                 (one evaluation)
+ *   order 2  Heun, x* = x + dt u(x), x' = x + dt (u(x) + u(x*)) / 2   (two)
+ *   xy_dev     n interleaved positions in the plan's element type (device,
+ *              read and overwritten with the new positions)
+ *   gamma_dev  n circulations (device; the viscous part of Eq. 5, which would
+ *              change them, is not part of this library)
+ * The positions must stay inside the root box: an intermediate position
+ * outside it is reported by fmm2d_plan_check, the final ones only by the
+ * next evaluation.  Uses the plan's staging buffers (calls on one plan must
+ * not overlap).  Asynchronous on `stream`. */
+fmm2d_status fmm2d_convect(fmm2d_plan* plan, int64_t n, void* xy_dev, const void* gamma_dev,
+                           double dt, int order, cudaStream_t stream);
+
 /* Velocities at m evaluation points that carry no circulation, induced by n
  * particles (the velocity field of Eq. 7 at arbitrary points z; the
  * single-source experiment of Sec. 5.2 evaluates it on a lattice of such

@@ -158,6 +158,20 @@ class Plan:
             self.check(stream)
         return out
 
+    def convect(self, xy, gamma, dt: float, order: int = 2, stream=None, check=False):
+        """One convection step of Eq. 5 in place (fmm2d_convect): forward
+        Euler (order 1) or Heun (order 2) on the FMM velocities.  xy must be
+        a contiguous CUDA tensor of the plan dtype; it holds the new
+        positions afterwards."""
+        if not xy.is_contiguous():
+            raise ValueError("xy must be contiguous (it is updated in place)")
+        _, gamma, n = self._inputs(xy, gamma)
+        _check(self._lib.fmm2d_convect(self._h, n, _ptr(xy), _ptr(gamma), float(dt), int(order),
+                                       _stream(stream)), "convect")
+        if check:
+            self.check(stream)
+        return xy
+
     def velocity_host(self, xy, gamma, out, stream=None):
         """Host-buffer form (fmm2d_velocity_host): xy, gamma, out are CPU
         tensors (page-locked for asynchronous copies); synchronous."""

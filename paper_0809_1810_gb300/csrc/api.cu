@@ -64,6 +64,7 @@ struct fmm2d_plan {
     void* st_xy = nullptr;
     void* st_gamma = nullptr;
     void* st_uv = nullptr;
+    void* st_u1 = nullptr;  // first-stage velocities of a convection step
     // graph cache
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
@@ -92,6 +93,34 @@ struct fmm2d_plan {
 };
 
 namespace {
+
+// out = x + dt u (u2 null) or x + dt (u + u2) / 2, over m reals: the
+// position updates of a convection step.
+template <typename R>
+__global__ void convect_update_kernel(int64_t m, R* __restrict__ out, const R* __restrict__ x,
+                                      R dt, const R* __restrict__ u, const R* __restrict__ u2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const R v = u2 ? R(0.5) * (u[i] + u2[i]) : u[i];
+        out[i] = x[i] + dt * v;
+    }
+}
+
+cudaError_t launch_convect_update(size_t elem, int64_t m, void* out, const void* x, double dt,
+                                  const void* u, const void* u2, cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    const int64_t want = (m + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 4096 ? want : 4096);
+    if (elem == 8)
+        convect_update_kernel<double><<<blocks, 256, 0, s>>>(
+            m, static_cast<double*>(out), static_cast<const double*>(x), dt,
+            static_cast<const double*>(u), static_cast<const double*>(u2));
+    else
+        convect_update_kernel<float><<<blocks, 256, 0, s>>>(
+            m, static_cast<float*>(out), static_cast<const float*>(x), (float)dt,
+            static_cast<const float*>(u), static_cast<const float*>(u2));
+    return cudaGetLastError();
+}
 
 template <typename R>
 Tables<R> tables_of(const fmm2d_plan* pl);
@@ -469,10 +498,11 @@ static fmm2d_status ensure_staging(fmm2d_plan* pl) {
     size_t nm = (size_t)(pl->prm.max_n > 0 ? pl->prm.max_n : 1);
     size_t bxy = align256(2 * nm * pl->elem), bg = align256(nm * pl->elem);
     void* buf = nullptr;
-    CK(cudaMalloc(&buf, 2 * bxy + bg));
+    CK(cudaMalloc(&buf, 3 * bxy + bg));
     pl->st_xy = buf;
     pl->st_gamma = static_cast<char*>(buf) + bxy;
     pl->st_uv = static_cast<char*>(buf) + bxy + bg;
+    pl->st_u1 = static_cast<char*>(buf) + 2 * bxy + bg;
     return FMM2D_OK;
 }
 
@@ -492,6 +522,35 @@ fmm2d_status fmm2d_velocity_host(fmm2d_plan* pl, int64_t n, const void* xy_host,
     if (n > 0)
         CK(cudaMemcpyAsync(uv_host, pl->st_uv, 2 * n * pl->elem, cudaMemcpyDeviceToHost, stream));
     return fmm2d_plan_check(pl, stream);
+}
+
+fmm2d_status fmm2d_convect(fmm2d_plan* pl, int64_t n, void* xy, const void* gamma, double dt,
+                           int order, cudaStream_t stream) {
+    if (!pl) return fail(FMM2D_INVALID_ARG, "null plan");
+    if (n < 0 || n > pl->prm.max_n) return fail(FMM2D_INVALID_ARG, "n out of [0, max_n]");
+    if (n > 0 && (!xy || !gamma)) return fail(FMM2D_INVALID_ARG, "null buffer");
+    if (order != 1 && order != 2) return fail(FMM2D_INVALID_ARG, "order must be 1 or 2");
+    if (!std::isfinite(dt)) return fail(FMM2D_INVALID_ARG, "dt must be finite");
+    fmm2d_status st = ensure_staging(pl);
+    if (st != FMM2D_OK) return st;
+    if (n == 0) return FMM2D_OK;
+    // both evaluations read the staging positions and write the staging
+    // velocities, so the plan's recorded graph serves both
+    const size_t e = pl->elem, bytes = 2 * (size_t)n * e;
+    CK(cudaMemcpyAsync(pl->st_xy, xy, bytes, cudaMemcpyDeviceToDevice, stream));
+    st = run(pl, n, pl->st_xy, gamma, pl->st_uv, stream);
+    if (st != FMM2D_OK) return st;
+    if (order == 1) {
+        CK(launch_convect_update(e, 2 * n, xy, xy, dt, pl->st_uv, nullptr, stream));
+        return FMM2D_OK;
+    }
+    // Heun: x* = x + dt u(x), x' = x + dt (u(x) + u(x*)) / 2
+    CK(cudaMemcpyAsync(pl->st_u1, pl->st_uv, bytes, cudaMemcpyDeviceToDevice, stream));
+    CK(launch_convect_update(e, 2 * n, pl->st_xy, xy, dt, pl->st_u1, nullptr, stream));
+    st = run(pl, n, pl->st_xy, gamma, pl->st_uv, stream);
+    if (st != FMM2D_OK) return st;
+    CK(launch_convect_update(e, 2 * n, xy, xy, dt, pl->st_u1, pl->st_uv, stream));
+    return FMM2D_OK;
 }
 
 fmm2d_status fmm2d_velocity_targets(fmm2d_plan* pl, int64_t n, const void* xy,

@@ -49,6 +49,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.fmm2d_plan_check(None, None) == _native.INVALID_ARG
     assert lib.fmm2d_velocity_targets(None, 0, None, None, 0, None, None, None) == \
         _native.INVALID_ARG
+    assert lib.fmm2d_convect(None, 0, None, None, 0.1, 2, None) == _native.INVALID_ARG
     assert lib.fmm2d_plan_set_timing(None, 4) == _native.INVALID_ARG
     lib.fmm2d_plan_destroy(None)  # accepted
 
