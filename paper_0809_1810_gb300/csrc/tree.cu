@@ -41,6 +41,16 @@ __device__ inline uint32_t leaf_coord(double x, double lo, double hi, double sca
     return (uint32_t)f;
 }
 
+// The defining FP64 expression, for coordinates near a cell edge.  Not
+// inlined: as a short inline branch it was evaluated for every coordinate
+// (the FP64 pipe, about 1/64 of the FP32 rate here, then limited the kernel).
+__device__ __noinline__ uint32_t leaf_coord_fp64(float x, double lo_d, double scale, double top) {
+    double fd = floor(((double)x - lo_d) * scale);
+    if (!(fd >= 0.0)) fd = 0.0;
+    if (fd > top) fd = top;
+    return (uint32_t)fd;
+}
+
 __device__ inline uint32_t leaf_coord_f32(float x, float lo, float hi, float x0f, float scalef,
                                           float margin, double lo_d, double scale, double top,
                                           int* flags) {
@@ -50,10 +60,7 @@ __device__ inline uint32_t leaf_coord_f32(float x, float lo, float hi, float x0f
     float fr = f - fl;
     if (fr > margin && fr < 1.0f - margin && fl >= 0.0f && fl <= (float)top)
         return (uint32_t)fl;
-    double fd = floor(((double)x - lo_d) * scale);  // the defining FP64 expression
-    if (!(fd >= 0.0)) fd = 0.0;
-    if (fd > top) fd = top;
-    return (uint32_t)fd;
+    return leaf_coord_fp64(x, lo_d, scale, top);
 }
 
 // Keys of one tile plus the histogram of the first digit.
