@@ -64,8 +64,8 @@ P2P_FLOPS_PER_PAIR = 20
 # dram__bytes_write.sum) from one ncu capture of the kernel on the benchmark
 # workload and setting; reported only while the kernel source is the one
 # captured (its SHA-256) and the setting matches.
-P2P_TRAFFIC = {"sha256_p2p_cu": "cba1027c3ee1e02fc54a9c1d42e790ede708b4aeb31a30d968cee71f45e39804",
-               "p": 15, "L": 7, "cutoff": True, "bytes": 23735552}
+P2P_TRAFFIC = {"sha256_p2p_cu": "181441e39f0b27085e844c4201d09577a4e4785b750a29cc31f7076ec9539e67",
+               "p": 15, "L": 7, "cutoff": True, "bytes": 21105152}
 
 
 def m2l_pairs(L):
@@ -568,8 +568,8 @@ def run_ours(args):
     p2p_ms = phase_avg["p2p_l2p"]
     achieved = pairs / (p2p_ms * 1e-3)
     roofline = {
-        "kernel": "p2p_l2p_f32_kernel (fused L2P + near field"
-                  + (" + cutoff ring)" if cutoff > 0 else ")"),
+        "kernel": "p2p_l2p_f32_kernel (near field" + (" + cutoff ring" if cutoff > 0 else "")
+                  + ") then l2p_f32_kernel (far part), timed together from the end of the tree",
         "bound": "alu", "unit": "Gpair/s",
         "achieved": achieved / 1e9, "peak": peak / 1e9, "frac": achieved / peak,
         "peak_source": f"derived: min(128 FP32 lanes x 2 / {P2P_FLOPS_PER_PAIR} flops, "
@@ -601,6 +601,8 @@ def run_ours(args):
         "flops_per_launch": m2l_flops,
         "flops_counted": "8 p^2 per interaction-list box pair, levels 2..L (useful complex "
                          "MACs; the 3xTF32 split and the zero padding to P = 16/32 run more)",
+        "note": "the far field runs beside the near field in the graph: its phase times "
+                "include waiting for SM room while the near field holds the GPU",
         "avg_launch_ms": m2l_ms,
     }
 

@@ -210,7 +210,10 @@ fmm2d_status fmm2d_plan_set_timing(fmm2d_plan* plan, int ring);
 /* Phase durations in milliseconds of the call made `age` calls ago (0 = the
  * latest), FMM2D_NUM_PHASES doubles written to ms_host.  Waits for that
  * call's events.  FMM2D_INVALID_ARG when timing is off or the call has left
- * the ring. */
+ * the ring.  In the FP32 forms at L >= 2 the far field (P2M, M2M, M2L, L2L)
+ * runs beside the near field: the last phase then spans from the end of the
+ * tree to the end of the far part's L2P, and the far-field phases are
+ * measured on their own branch. */
 fmm2d_status fmm2d_plan_phase_ms(fmm2d_plan* plan, int age, double* ms_host);
 
 /* ------------------------------------------------------------------------

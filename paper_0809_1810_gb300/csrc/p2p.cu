@@ -371,6 +371,47 @@ struct LeafCtx {
     const uint32_t* cpre;      // prefix sums of their lengths (17 entries)
 };
 
+// The leaf's local expansion, written to `out` (P coefficients, shared
+// memory): its M2L part plus the L2L of its parent's (Sec. 3.3.3).  One warp.
+__device__ __forceinline__ void leaf_le_build(const Geometry& g, const float* __restrict__ le,
+                                              const float* __restrict__ l2l, uint32_t lx,
+                                              uint32_t ly, float2* out) {
+    const int lane = threadIdx.x & 31;
+    const float2* own =
+        reinterpret_cast<const float2*>(le + box_slot(g.level_base, g.L, lx, ly) * (2 * g.P));
+    float2 v = lane < g.P ? own[lane] : make_float2(0.f, 0.f);
+    if (g.L >= 3) {
+        const float2* par = reinterpret_cast<const float2*>(
+            le + box_slot(g.level_base, g.L - 1, lx >> 1, ly >> 1) * (2 * g.P));
+        const float2* t = reinterpret_cast<const float2*>(l2l) +
+                          (int64_t)(((ly & 1u) << 1) | (lx & 1u)) * g.P * g.P;
+        float2 pk_own = lane < g.P ? par[lane] : make_float2(0.f, 0.f);
+        for (int k = 0; k < g.P; ++k) {
+            float2 pk = cshfl(pk_own, k, 32);
+            if (lane < g.P) v = cfma(t[k * g.P + lane], pk, v);
+        }
+    }
+    if (lane >= g.p) v = make_float2(0.f, 0.f);
+    __syncwarp();  // earlier readers of `out` are done
+    if (lane < g.P) out[lane] = v;
+    __syncwarp();
+}
+
+// L2P (Eq. 12) added to a target's velocity: w = (1/s) sum_n L~_n zeta^n at
+// zeta = (z - z_leaf) / s, from the target's scaled leaf-relative (x, y).
+__device__ __forceinline__ void l2p_add(int p, float kzeta, float inv_s, const float2* Lc,
+                                        float x, float y, float& u, float& v) {
+    float2 zeta = make_float2(x * kzeta, y * kzeta);
+    float2 w = Lc[p - 1];
+    for (int m = p - 2; m >= 0; --m) {
+        float2 t = cmul(w, zeta);
+        float2 lm = Lc[m];
+        w = make_float2(t.x + lm.x, t.y + lm.y);
+    }
+    u = fmaf(inv_s, w.x, u);
+    v = fmaf(-inv_s, w.y, v);
+}
+
 // Gather local-list records [cb, cb + cnt) into the warp's buffer in scaled
 // leaf-relative coordinates: near band at the front (nn records), far band
 // at the back (nf records).
@@ -531,25 +572,8 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
     }
     leaf_centre_hilo(g, lx, ly, &c.cxh, &c.cxl, &c.cyh, &c.cyl);
     c.le_leaf = nullptr;
-    if (g.L >= 2) {  // the leaf's LE: its M2L part plus L2L of its parent's (Sec. 3.3.3)
-        const float2* own = reinterpret_cast<const float2*>(
-            le + box_slot(g.level_base, g.L, lx, ly) * (2 * g.P));
-        float2 v = lane < g.P ? own[lane] : make_float2(0.f, 0.f);
-        if (g.L >= 3) {
-            const float2* par = reinterpret_cast<const float2*>(
-                le + box_slot(g.level_base, g.L - 1, lx >> 1, ly >> 1) * (2 * g.P));
-            const float2* t = reinterpret_cast<const float2*>(l2l) +
-                              (int64_t)(((ly & 1u) << 1) | (lx & 1u)) * g.P * g.P;
-            float2 pk_own = lane < g.P ? par[lane] : make_float2(0.f, 0.f);
-            for (int k = 0; k < g.P; ++k) {
-                float2 pk = cshfl(pk_own, k, 32);
-                if (lane < g.P) v = cfma(t[k * g.P + lane], pk, v);
-            }
-        }
-        if (lane >= g.p) v = make_float2(0.f, 0.f);
-        __syncwarp();  // earlier readers of leaf_le are done
-        if (lane < g.P) leaf_le[lane] = v;
-        __syncwarp();
+    if (g.L >= 2 && le) {  // null le: near field only, the far field is added later
+        leaf_le_build(g, le, l2l, lx, ly, leaf_le);
         c.le_leaf = reinterpret_cast<const float*>(leaf_le);
     }
     const uint32_t total = rpre[9];
@@ -560,18 +584,9 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
     // far field (L2P, Eq. 12) plus near sum -> velocity of one target
     auto finish = [&](const float4& rec, float x, float y, float su, float sv) {
         float u = __fmul_rn(nm.kvel, su), v = __fmul_rn(nm.kvel, sv);
-        if (c.le_leaf) {  // w = (1/s) sum_n L~_n zeta^n, zeta = (z - z_leaf) / s
-            float2 zeta = make_float2(x * nm.kzeta, y * nm.kzeta);
-            const float2* Lc = reinterpret_cast<const float2*>(c.le_leaf);
-            float2 w = Lc[g.p - 1];
-            for (int m = g.p - 2; m >= 0; --m) {
-                float2 t = cmul(w, zeta);
-                float2 lm = Lc[m];
-                w = make_float2(t.x + lm.x, t.y + lm.y);
-            }
-            u = fmaf(nm.inv_s, w.x, u);
-            v = fmaf(-nm.inv_s, w.y, v);
-        }
+        if (c.le_leaf)
+            l2p_add(g.p, nm.kzeta, nm.inv_s, reinterpret_cast<const float2*>(c.le_leaf), x, y,
+                    u, v);
         const uint32_t idx = __float_as_uint(rec.w);
         uv[2 * (int64_t)idx] = u;
         uv[2 * (int64_t)idx + 1] = v;
@@ -883,11 +898,13 @@ static unsigned resident_ctas(const void* kernel) {
     return (unsigned)std::max(1, sms * std::max(per_sm, 1));
 }
 
-template <>
-cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, int64_t n,
-                                  const void* particles, const uint32_t* skeys,
-                                  const uint32_t* leaf_start, uint32_t* counter, const float* le,
-                                  const float* l2l, float* uv, cudaStream_t s) {
+// The FP32 near-field launch: the whole persistent grid (all CTAs that fit
+// on the GPU at once), work counter zeroed first.  With le null it writes the
+// near part alone.
+static cudaError_t launch_near_f32(const Geometry& g, double sigma, int64_t n,
+                                   const void* particles, const uint32_t* skeys,
+                                   const uint32_t* leaf_start, uint32_t* counter,
+                                   const float* le, const float* l2l, float* uv, cudaStream_t s) {
     bool ok;
     NearF32v3 nm = near_constants(sigma, g, &ok);
     if (!ok) return cudaErrorInvalidValue;
@@ -918,6 +935,65 @@ cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, int64_t n,
     else
         p2p_l2p_f32_kernel<false, 4><<<grid, block, 0, s>>>(sp, skeys, leaf_start, ws, counter, g,
                                                             nm, le, l2l, uv);
+    return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, int64_t n,
+                                  const void* particles, const uint32_t* skeys,
+                                  const uint32_t* leaf_start, uint32_t* counter, const float* le,
+                                  const float* l2l, float* uv, cudaStream_t s) {
+    return launch_near_f32(g, sigma, n, particles, skeys, leaf_start, counter, le, l2l, uv, s);
+}
+
+cudaError_t launch_near_only_f32(const Geometry& g, double sigma, int64_t n,
+                                 const void* particles, const uint32_t* skeys,
+                                 const uint32_t* leaf_start, uint32_t* counter, float* uv,
+                                 cudaStream_t s) {
+    return launch_near_f32(g, sigma, n, particles, skeys, leaf_start, counter, nullptr, nullptr,
+                           uv, s);
+}
+
+// L2P after a near-field-only pass: one warp per leaf adds the leaf's local
+// expansion to each of its targets' velocities, with the operations the
+// fused kernel applies (leaf_le_build, l2p_add), so the sum is the same bit
+// for bit.
+__global__ void __launch_bounds__(kLeafWarps * 32)
+l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start, Geometry g,
+               float sc, float kzeta, float inv_s, const float* __restrict__ le,
+               const float* __restrict__ l2l, float* __restrict__ uv) {
+    __shared__ float2 leaf_le[kLeafWarps][kMaxP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t leaf = blockIdx.x * kLeafWarps + warp;
+    if (leaf >= (1u << (2 * g.L))) return;  // warp-uniform
+    const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
+    if (t0 == t1) return;
+    const uint32_t lx = morton_compact(leaf), ly = morton_compact(leaf >> 1);
+    float cxh, cxl, cyh, cyl;
+    leaf_centre_hilo(g, lx, ly, &cxh, &cxl, &cyh, &cyl);
+    leaf_le_build(g, le, l2l, lx, ly, leaf_le[warp]);
+    for (uint32_t k = t0 + lane; k < t1; k += 32) {
+        const float4 rec = sp[k];
+        const float x = ((rec.x - cxh) - cxl) * sc, y = ((rec.y - cyh) - cyl) * sc;
+        const uint32_t idx = __float_as_uint(rec.w);
+        float u = uv[2 * (int64_t)idx], v = uv[2 * (int64_t)idx + 1];
+        l2p_add(g.p, kzeta, inv_s, leaf_le[warp], x, y, u, v);
+        uv[2 * (int64_t)idx] = u;
+        uv[2 * (int64_t)idx + 1] = v;
+    }
+}
+
+cudaError_t launch_l2p_f32(const Geometry& g, double sigma, const void* particles,
+                           const uint32_t* leaf_start, const float* le, const float* l2l,
+                           float* uv, cudaStream_t s) {
+    if (g.L < 2) return cudaSuccess;
+    bool ok;
+    const NearF32v3 nm = near_constants(sigma, g, &ok);
+    if (!ok) return cudaErrorInvalidValue;
+    const unsigned blocks = (unsigned)(((uint64_t)1 << (2 * g.L)) / kLeafWarps);
+    l2p_f32_kernel<<<blocks, kLeafWarps * 32, 0, s>>>(reinterpret_cast<const float4*>(particles),
+                                                      leaf_start, g, nm.sc, nm.kzeta, nm.inv_s,
+                                                      le, l2l, uv);
     return cudaGetLastError();
 }
 
