@@ -161,15 +161,19 @@ template <typename R>
 cudaError_t launch_p2p_l2p(const Geometry& g, double sigma, int64_t n, const void* particles,
                            const uint32_t* skeys, const uint32_t* leaf_start, uint32_t* counter,
                            const R* le, const R* l2l, R* uv, cudaStream_t s);
-// The FP32 near field without its far part, and the L2P that adds the far
-// part afterwards (the fused kernel's sum, bit for bit).
+// The FP32 near field without its far part, written to `out` (2 floats per
+// target) at the input indices or (sorted_out) in sorted order, and the L2P
+// that adds the far part afterwards -- reading the near parts in sorted order
+// from uv_sorted, or from uv itself when uv_sorted is null -- and writes the
+// velocities to uv at the input indices (the fused kernel's sum, bit for bit).
 cudaError_t launch_near_only_f32(const Geometry& g, double sigma, int64_t n,
                                  const void* particles, const uint32_t* skeys,
-                                 const uint32_t* leaf_start, uint32_t* counter, float* uv,
+                                 const uint32_t* leaf_start, uint32_t* counter, float* out,
+                                 bool sorted_out,
                                  cudaStream_t s);
 cudaError_t launch_l2p_f32(const Geometry& g, double sigma, const void* particles,
                            const uint32_t* leaf_start, const float* le, const float* l2l,
-                           float* uv, cudaStream_t s);
+                           const float* uv_sorted, float* uv, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Batched evaluation: many instances in one packed problem.  Instance i owns

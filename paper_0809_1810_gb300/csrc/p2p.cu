@@ -371,23 +371,38 @@ struct LeafCtx {
     const uint32_t* cpre;      // prefix sums of their lengths (17 entries)
 };
 
+// The two vectors a leaf's local expansion is formed from: its M2L part and
+// its parent's expansion (lane k < P holds coefficient k; zero elsewhere).
+struct LeafLeParts {
+    float2 own, par;
+};
+
+__device__ __forceinline__ LeafLeParts leaf_le_load(const Geometry& g, const float* __restrict__ le,
+                                                    uint32_t lx, uint32_t ly) {
+    const int lane = threadIdx.x & 31;
+    LeafLeParts q{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    if (lane < g.P) {
+        q.own = reinterpret_cast<const float2*>(
+            le + box_slot(g.level_base, g.L, lx, ly) * (2 * g.P))[lane];
+        if (g.L >= 3)
+            q.par = reinterpret_cast<const float2*>(
+                le + box_slot(g.level_base, g.L - 1, lx >> 1, ly >> 1) * (2 * g.P))[lane];
+    }
+    return q;
+}
+
 // The leaf's local expansion, written to `out` (P coefficients, shared
 // memory): its M2L part plus the L2L of its parent's (Sec. 3.3.3).  One warp.
-__device__ __forceinline__ void leaf_le_build(const Geometry& g, const float* __restrict__ le,
-                                              const float* __restrict__ l2l, uint32_t lx,
-                                              uint32_t ly, float2* out) {
+__device__ __forceinline__ void leaf_le_finish(const Geometry& g, const float* __restrict__ l2l,
+                                               uint32_t lx, uint32_t ly, const LeafLeParts& q,
+                                               float2* out) {
     const int lane = threadIdx.x & 31;
-    const float2* own =
-        reinterpret_cast<const float2*>(le + box_slot(g.level_base, g.L, lx, ly) * (2 * g.P));
-    float2 v = lane < g.P ? own[lane] : make_float2(0.f, 0.f);
+    float2 v = q.own;
     if (g.L >= 3) {
-        const float2* par = reinterpret_cast<const float2*>(
-            le + box_slot(g.level_base, g.L - 1, lx >> 1, ly >> 1) * (2 * g.P));
         const float2* t = reinterpret_cast<const float2*>(l2l) +
                           (int64_t)(((ly & 1u) << 1) | (lx & 1u)) * g.P * g.P;
-        float2 pk_own = lane < g.P ? par[lane] : make_float2(0.f, 0.f);
         for (int k = 0; k < g.P; ++k) {
-            float2 pk = cshfl(pk_own, k, 32);
+            float2 pk = cshfl(q.par, k, 32);
             if (lane < g.P) v = cfma(t[k * g.P + lane], pk, v);
         }
     }
@@ -395,6 +410,12 @@ __device__ __forceinline__ void leaf_le_build(const Geometry& g, const float* __
     __syncwarp();  // earlier readers of `out` are done
     if (lane < g.P) out[lane] = v;
     __syncwarp();
+}
+
+__device__ __forceinline__ void leaf_le_build(const Geometry& g, const float* __restrict__ le,
+                                              const float* __restrict__ l2l, uint32_t lx,
+                                              uint32_t ly, float2* out) {
+    leaf_le_finish(g, l2l, lx, ly, leaf_le_load(g, le, lx, ly), out);
 }
 
 // L2P (Eq. 12) added to a target's velocity: w = (1/s) sum_n L~_n zeta^n at
@@ -497,7 +518,7 @@ __device__ __forceinline__ void gather_ring(const float4* __restrict__ sp, const
 // round of at most 16 targets as a one-per-lane pass, without the split
 // path: 10% faster at 64 targets per leaf.  (The plain kernel keeps both:
 // there the narrower build measured slower.)
-template <bool kCut, int kMaxT = 4>
+template <bool kCut, int kMaxT = 4, bool kSorted = false>
 __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
                                               const uint32_t* __restrict__ leaf_start,
                                               uint32_t leaf_base, uint32_t leaf, uint32_t a,
@@ -581,15 +602,17 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
     uint32_t nn = 0, nf = 0;
     if (one_chunk) gather_bands(sp, c, nm, 0, total, buf, nn, nf);
 
-    // far field (L2P, Eq. 12) plus near sum -> velocity of one target
-    auto finish = [&](const float4& rec, float x, float y, float su, float sv) {
+    // far field (L2P, Eq. 12) plus near sum -> velocity of one target, at
+    // its input index or (kSorted, near part alone) at its sorted position
+    // ks, coalesced, for the L2P kernel that follows
+    auto finish = [&](const float4& rec, uint32_t ks, float x, float y, float su, float sv) {
         float u = __fmul_rn(nm.kvel, su), v = __fmul_rn(nm.kvel, sv);
         if (c.le_leaf)
             l2p_add(g.p, nm.kzeta, nm.inv_s, reinterpret_cast<const float2*>(c.le_leaf), x, y,
                     u, v);
-        const uint32_t idx = __float_as_uint(rec.w);
-        uv[2 * (int64_t)idx] = u;
-        uv[2 * (int64_t)idx + 1] = v;
+        const uint32_t o = kSorted ? ks : __float_as_uint(rec.w);
+        uv[2 * (int64_t)o] = u;
+        uv[2 * (int64_t)o + 1] = v;
     };
 
     // passes of 32 T targets, T per lane (targets tb + lane + 32 t); in a
@@ -622,23 +645,25 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
 #pragma unroll
         for (int t = 0; t < T; ++t)
             if (32 * t + lane < active)
-                finish(rec[t], x[t], y[t], S.su[t] + S.cu[t], S.sv[t] + S.cv[t]);
+                finish(rec[t], c.t0 + tb + 32 * t + lane, x[t], y[t], S.su[t] + S.cu[t],
+                       S.sv[t] + S.cv[t]);
     };
     uint32_t tb = a;
     if (kMaxT >= 4 && b - tb == 128) {  // 128 targets: four per lane, the list gathered once
         pass(std::integral_constant<int, 4>{}, tb, 128u);
         tb = b;
     }
-    for (; tb + 64 <= b; tb += 64) pass(std::integral_constant<int, 2>{}, tb, 64u);
-    // rounds of 17..32 targets, one per lane (in the narrow cutoff kernel
-    // every remaining round, which then needs no split-path code)
-    constexpr bool kNoSplit = kCut && kMaxT < 4;
-    for (; kNoSplit ? tb < b : tb + 16 < b; tb += 32)
-        pass(std::integral_constant<int, 1>{}, tb, min(32u, b - tb));
-    if (!kNoSplit && tb < b) {  // a leaf's last round of at most 16 targets: ns lanes per target
+    // passes of 64 targets, two per lane, and at a chunk's end passes of 49
+    // to 63 (one gather of the list for what would otherwise be two rounds;
+    // the last round then keeps more than 16 targets, as a leaf's last round
+    // of at most 16 takes the split path below in whichever work item it
+    // falls)
+    for (; tb + 48 < b; tb += 64) pass(std::integral_constant<int, 2>{}, tb, min(64u, b - tb));
+    // rounds of 17..32 targets, one per lane
+    for (; tb + 16 < b; tb += 32) pass(std::integral_constant<int, 1>{}, tb, min(32u, b - tb));
+    if (tb < b) {  // a leaf's last round of at most 16 targets: ns lanes per target
         const uint32_t tc = b - tb;
-        int ns = 2;  // lanes per target: largest power of two with tc * ns <= 32
-        while (tc * (uint32_t)(2 * ns) <= 32u) ns *= 2;
+        const int ns = (int)(32u / tc);  // lanes per target, 2..32
         const uint32_t tl = lane / ns;
         const int sl = lane % ns;
         const bool active = tl < tc;
@@ -660,11 +685,18 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
             }
         su += cu;
         sv += cv;
+        // the target's ns partial sums, a segmented tree: after the step of
+        // width o, lane sl holds the sum of lanes sl .. sl + 2o - 1 of its
+        // segment (clipped at ns)
         for (int o = 1; o < ns; o <<= 1) {
-            su += __shfl_xor_sync(0xffffffffu, su, o);
-            sv += __shfl_xor_sync(0xffffffffu, sv, o);
+            const float pu = __shfl_down_sync(0xffffffffu, su, o);
+            const float pv = __shfl_down_sync(0xffffffffu, sv, o);
+            if (sl + o < ns) {
+                su += pu;
+                sv += pv;
+            }
         }
-        if (active && sl == 0) finish(rec, x, y, su, sv);
+        if (active && sl == 0) finish(rec, c.t0 + tb + tl, x, y, su, sv);
     }
     __syncwarp();  // the buffer may be reused by this warp's next chunk
 }
@@ -736,7 +768,7 @@ __device__ __forceinline__ void for_each_piece(const uint32_t* __restrict__ skey
 // items from a counter (zeroed before the launch) until none is left, so
 // crowded windows balance against light ones and no SM idles behind a
 // partial last wave.
-template <bool kCut, int kMaxT>
+template <bool kCut, int kMaxT, bool kSorted>
 __global__ void __launch_bounds__(kLeafWarps * 32, 6)
 p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skeys,
                    const uint32_t* __restrict__ leaf_start, WorkSplit ws, uint32_t* counter,
@@ -752,9 +784,8 @@ p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ s
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= ws.items) break;
         for_each_piece(skeys, leaf_start, ws, w, [&](uint32_t leaf, uint32_t a, uint32_t b) {
-            p2p_chunk_f32<kCut, kMaxT>(sp, leaf_start, 0, leaf, a, b, g, nm, le, l2l, uv,
-                                       lists[warp],
-                          ranges[warp], leaf_le[warp]);
+            p2p_chunk_f32<kCut, kMaxT, kSorted>(sp, leaf_start, 0, leaf, a, b, g, nm, le, l2l,
+                                                uv, lists[warp], ranges[warp], leaf_le[warp]);
         });
     }
 }
@@ -900,20 +931,21 @@ static unsigned resident_ctas(const void* kernel) {
 
 // The FP32 near-field launch: the whole persistent grid (all CTAs that fit
 // on the GPU at once), work counter zeroed first.  With le null it writes the
-// near part alone.
+// near part alone, at the input indices or (sorted_out) in sorted order.
 static cudaError_t launch_near_f32(const Geometry& g, double sigma, int64_t n,
                                    const void* particles, const uint32_t* skeys,
                                    const uint32_t* leaf_start, uint32_t* counter,
-                                   const float* le, const float* l2l, float* uv, cudaStream_t s) {
+                                   const float* le, const float* l2l, float* uv, bool sorted_out,
+                                   cudaStream_t s) {
     bool ok;
     NearF32v3 nm = near_constants(sigma, g, &ok);
     if (!ok) return cudaErrorInvalidValue;
     if (n == 0) return cudaSuccess;
     const bool cut = nm.ring_mask != 0;  // some ring leaf can hold a pair closer than a
     auto kernel_of = [&](int max_t) {
-        return cut ? (max_t >= 4 ? reinterpret_cast<const void*>(p2p_l2p_f32_kernel<true, 4>)
-                                 : reinterpret_cast<const void*>(p2p_l2p_f32_kernel<true, 2>))
-                   : reinterpret_cast<const void*>(p2p_l2p_f32_kernel<false, 4>);
+        return cut ? (max_t >= 4 ? reinterpret_cast<const void*>(p2p_l2p_f32_kernel<true, 4, false>)
+                                 : reinterpret_cast<const void*>(p2p_l2p_f32_kernel<true, 2, false>))
+                   : reinterpret_cast<const void*>(p2p_l2p_f32_kernel<false, 4, false>);
     };
     const unsigned resident = resident_ctas(kernel_of(4));
     const WorkSplit ws = work_split((uint64_t)n, (uint64_t)resident * kLeafWarps);
@@ -925,17 +957,21 @@ static cudaError_t launch_near_f32(const Geometry& g, double sigma, int64_t n,
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const float4* sp = reinterpret_cast<const float4*>(particles);
-    const dim3 grid(blocks), block(kLeafWarps * 32);
+    auto go = [&](auto kernel) {
+        if (resident_ctas(reinterpret_cast<const void*>(kernel)) != resident)
+            return cudaErrorInvalidConfiguration;
+        kernel<<<dim3(blocks), dim3(kLeafWarps * 32), 0, s>>>(sp, skeys, leaf_start, ws, counter,
+                                                              g, nm, le, l2l, uv);
+        return cudaGetLastError();
+    };
     if (cut && max_t >= 4)
-        p2p_l2p_f32_kernel<true, 4><<<grid, block, 0, s>>>(sp, skeys, leaf_start, ws, counter, g,
-                                                           nm, le, l2l, uv);
-    else if (cut)
-        p2p_l2p_f32_kernel<true, 2><<<grid, block, 0, s>>>(sp, skeys, leaf_start, ws, counter, g,
-                                                           nm, le, l2l, uv);
-    else
-        p2p_l2p_f32_kernel<false, 4><<<grid, block, 0, s>>>(sp, skeys, leaf_start, ws, counter, g,
-                                                            nm, le, l2l, uv);
-    return cudaGetLastError();
+        return sorted_out ? go(p2p_l2p_f32_kernel<true, 4, true>)
+                          : go(p2p_l2p_f32_kernel<true, 4, false>);
+    if (cut)
+        return sorted_out ? go(p2p_l2p_f32_kernel<true, 2, true>)
+                          : go(p2p_l2p_f32_kernel<true, 2, false>);
+    return sorted_out ? go(p2p_l2p_f32_kernel<false, 4, true>)
+                      : go(p2p_l2p_f32_kernel<false, 4, false>);
 }
 
 template <>
@@ -943,57 +979,99 @@ cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, int64_t n,
                                   const void* particles, const uint32_t* skeys,
                                   const uint32_t* leaf_start, uint32_t* counter, const float* le,
                                   const float* l2l, float* uv, cudaStream_t s) {
-    return launch_near_f32(g, sigma, n, particles, skeys, leaf_start, counter, le, l2l, uv, s);
+    return launch_near_f32(g, sigma, n, particles, skeys, leaf_start, counter, le, l2l, uv, false,
+                           s);
 }
 
 cudaError_t launch_near_only_f32(const Geometry& g, double sigma, int64_t n,
                                  const void* particles, const uint32_t* skeys,
-                                 const uint32_t* leaf_start, uint32_t* counter, float* uv,
-                                 cudaStream_t s) {
+                                 const uint32_t* leaf_start, uint32_t* counter, float* out,
+                                 bool sorted_out, cudaStream_t s) {
     return launch_near_f32(g, sigma, n, particles, skeys, leaf_start, counter, nullptr, nullptr,
-                           uv, s);
+                           out, sorted_out, s);
 }
 
 // L2P after a near-field-only pass: one warp per leaf adds the leaf's local
-// expansion to each of its targets' velocities, with the operations the
-// fused kernel applies (leaf_le_build, l2p_add), so the sum is the same bit
-// for bit.
+// expansion to each of its targets' near-field velocities and writes the sums
+// at the targets' input indices, with the operations the fused kernel applies
+// (leaf_le_load/finish, l2p_add), so the sum is the same bit for bit.  The
+// kernel is bound by the latency of its loads.  kSorted: the near parts are
+// read in sorted order (coalesced), and the loads that depend on the leaf
+// alone (its expansion parts, centre and target range), then the lane's
+// first two targets, are all issued before the expansion is formed.
+// Otherwise the near parts are read back at the targets' input indices, leaf
+// by leaf.
+template <bool kSorted>
 __global__ void __launch_bounds__(kLeafWarps * 32)
 l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start, Geometry g,
                float sc, float kzeta, float inv_s, const float* __restrict__ le,
-               const float* __restrict__ l2l, float* __restrict__ uv) {
+               const float* __restrict__ l2l, const float2* __restrict__ uvs,
+               float* __restrict__ uv) {
     __shared__ float2 leaf_le[kLeafWarps][kMaxP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t leaf = blockIdx.x * kLeafWarps + warp;
     if (leaf >= (1u << (2 * g.L))) return;  // warp-uniform
-    const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
-    if (t0 == t1) return;
     const uint32_t lx = morton_compact(leaf), ly = morton_compact(leaf >> 1);
     float cxh, cxl, cyh, cyl;
-    leaf_centre_hilo(g, lx, ly, &cxh, &cxl, &cyh, &cyl);
-    leaf_le_build(g, le, l2l, lx, ly, leaf_le[warp]);
-    for (uint32_t k = t0 + lane; k < t1; k += 32) {
-        const float4 rec = sp[k];
+    auto add = [&](const float4& rec, float u, float v) {
         const float x = ((rec.x - cxh) - cxl) * sc, y = ((rec.y - cyh) - cyl) * sc;
-        const uint32_t idx = __float_as_uint(rec.w);
-        float u = uv[2 * (int64_t)idx], v = uv[2 * (int64_t)idx + 1];
         l2p_add(g.p, kzeta, inv_s, leaf_le[warp], x, y, u, v);
+        const uint32_t idx = __float_as_uint(rec.w);
         uv[2 * (int64_t)idx] = u;
         uv[2 * (int64_t)idx + 1] = v;
+    };
+    if (!kSorted) {
+        const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
+        if (t0 == t1) return;
+        leaf_centre_hilo(g, lx, ly, &cxh, &cxl, &cyh, &cyl);
+        leaf_le_build(g, le, l2l, lx, ly, leaf_le[warp]);
+        for (uint32_t k = t0 + lane; k < t1; k += 32) {
+            const float4 rec = sp[k];
+            const uint32_t idx = __float_as_uint(rec.w);
+            add(rec, uv[2 * (int64_t)idx], uv[2 * (int64_t)idx + 1]);
+        }
+        return;
+    }
+    const LeafLeParts q = leaf_le_load(g, le, lx, ly);
+    leaf_centre_hilo(g, lx, ly, &cxh, &cxl, &cyh, &cyl);
+    const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
+    if (t0 == t1) return;
+    const uint32_t k0 = t0 + lane, k1 = k0 + 32;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+    float2 w0 = make_float2(0.f, 0.f), w1 = w0;
+    if (k0 < t1) {
+        r0 = sp[k0];
+        w0 = uvs[k0];
+    }
+    if (k1 < t1) {
+        r1 = sp[k1];
+        w1 = uvs[k1];
+    }
+    leaf_le_finish(g, l2l, lx, ly, q, leaf_le[warp]);
+    if (k0 < t1) add(r0, w0.x, w0.y);
+    if (k1 < t1) add(r1, w1.x, w1.y);
+    for (uint32_t k = k1 + 32; k < t1; k += 32) {
+        const float2 w = uvs[k];
+        add(sp[k], w.x, w.y);
     }
 }
 
 cudaError_t launch_l2p_f32(const Geometry& g, double sigma, const void* particles,
                            const uint32_t* leaf_start, const float* le, const float* l2l,
-                           float* uv, cudaStream_t s) {
+                           const float* uv_sorted, float* uv, cudaStream_t s) {
     if (g.L < 2) return cudaSuccess;
     bool ok;
     const NearF32v3 nm = near_constants(sigma, g, &ok);
     if (!ok) return cudaErrorInvalidValue;
     const unsigned blocks = (unsigned)(((uint64_t)1 << (2 * g.L)) / kLeafWarps);
-    l2p_f32_kernel<<<blocks, kLeafWarps * 32, 0, s>>>(reinterpret_cast<const float4*>(particles),
-                                                      leaf_start, g, nm.sc, nm.kzeta, nm.inv_s,
-                                                      le, l2l, uv);
+    const float4* sp = reinterpret_cast<const float4*>(particles);
+    const float2* uvs = reinterpret_cast<const float2*>(uv_sorted);
+    if (uv_sorted)
+        l2p_f32_kernel<true><<<blocks, kLeafWarps * 32, 0, s>>>(sp, leaf_start, g, nm.sc, nm.kzeta,
+                                                                nm.inv_s, le, l2l, uvs, uv);
+    else
+        l2p_f32_kernel<false><<<blocks, kLeafWarps * 32, 0, s>>>(
+            sp, leaf_start, g, nm.sc, nm.kzeta, nm.inv_s, le, l2l, uvs, uv);
     return cudaGetLastError();
 }
 
