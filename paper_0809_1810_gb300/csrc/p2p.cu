@@ -412,6 +412,28 @@ __device__ __forceinline__ void leaf_le_finish(const Geometry& g, const float* _
     __syncwarp();
 }
 
+// leaf_le_finish for P = 16, the loop unrolled so that the translation
+// table's loads are issued together (the same operations in the same order).
+__device__ __forceinline__ void leaf_le_finish16(const Geometry& g, const float* __restrict__ l2l,
+                                                 uint32_t lx, uint32_t ly, const LeafLeParts& q,
+                                                 float2* out) {
+    const int lane = threadIdx.x & 31;
+    float2 v = q.own;
+    if (g.L >= 3) {
+        const float2* t = reinterpret_cast<const float2*>(l2l) +
+                          (int64_t)(((ly & 1u) << 1) | (lx & 1u)) * 16 * 16;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            float2 pk = cshfl(q.par, k, 32);
+            if (lane < 16) v = cfma(t[k * 16 + lane], pk, v);
+        }
+    }
+    if (lane >= g.p) v = make_float2(0.f, 0.f);
+    __syncwarp();  // earlier readers of `out` are done
+    if (lane < 16) out[lane] = v;
+    __syncwarp();
+}
+
 __device__ __forceinline__ void leaf_le_build(const Geometry& g, const float* __restrict__ le,
                                               const float* __restrict__ l2l, uint32_t lx,
                                               uint32_t ly, float2* out) {
@@ -1013,12 +1035,17 @@ l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_
     if (leaf >= (1u << (2 * g.L))) return;  // warp-uniform
     const uint32_t lx = morton_compact(leaf), ly = morton_compact(leaf >> 1);
     float cxh, cxl, cyh, cyl;
+    const bool uv8 = (reinterpret_cast<uintptr_t>(uv) & 7u) == 0;  // one 8-byte store
     auto add = [&](const float4& rec, float u, float v) {
         const float x = ((rec.x - cxh) - cxl) * sc, y = ((rec.y - cyh) - cyl) * sc;
         l2p_add(g.p, kzeta, inv_s, leaf_le[warp], x, y, u, v);
         const uint32_t idx = __float_as_uint(rec.w);
-        uv[2 * (int64_t)idx] = u;
-        uv[2 * (int64_t)idx + 1] = v;
+        if (kSorted && uv8) {
+            *reinterpret_cast<float2*>(uv + 2 * (int64_t)idx) = make_float2(u, v);
+        } else {
+            uv[2 * (int64_t)idx] = u;
+            uv[2 * (int64_t)idx + 1] = v;
+        }
     };
     if (!kSorted) {
         const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
@@ -1047,7 +1074,10 @@ l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_
         r1 = sp[k1];
         w1 = uvs[k1];
     }
-    leaf_le_finish(g, l2l, lx, ly, q, leaf_le[warp]);
+    if (g.P == 16)
+        leaf_le_finish16(g, l2l, lx, ly, q, leaf_le[warp]);
+    else
+        leaf_le_finish(g, l2l, lx, ly, q, leaf_le[warp]);
     if (k0 < t1) add(r0, w0.x, w0.y);
     if (k1 < t1) add(r1, w1.x, w1.y);
     for (uint32_t k = k1 + 32; k < t1; k += 32) {
