@@ -53,11 +53,12 @@ TOL = 1e-6
 VERIFY_TARGETS = 2048  # particles at which the proposal is judged (other seed than ACC_TARGETS)
 ACC_TARGETS = 8192
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
-# algorithmic FP32 work per near pair: 2 differences, r^2 (mul + fma), the
-# argument scaling, 1 - e, the product with rcp, the circulation, 2 fmas for
-# the velocity components (flops counting an fma as 2), plus ex2 and rcp on
-# the MUFU unit
-P2P_FLOPS_PER_PAIR = 20
+# the fewest instructions one near pair of Eq. 6 takes in the 2^-q2 form:
+# on the FP32 pipe the 2 coordinate differences, dy^2, r^2 = fma(dx, dx, dy^2),
+# Gamma (1 - 2^-q2) as one fma, the product with 1/q2 and the 2 fmas of the
+# velocity components (8); on the MUFU pipe ex2 and rcp (2)
+P2P_FP32_INSTR_PER_PAIR = 8
+P2P_MUFU_INSTR_PER_PAIR = 2
 
 
 # DRAM traffic of one near-field launch (dram__bytes_read.sum +
@@ -117,16 +118,23 @@ def _peaks():
 
 # P2P unit rates per SM per clock (Blackwell SM: 128 FP32 lanes, 16 MUFU lanes).
 FP32_LANES_PER_SM = 128
-MUFU_LANES_PER_SM = 16
+# ex2 / rcp lanes per SM: the near-field capture has the XU pipe 36% of its
+# peak while issuing at least 0.31 MUFU warp instructions per SM cycle
+# (2 per evaluated pair), which needs a peak of about one warp instruction
+# per SM cycle: 32 lanes, twice the 16 of earlier parts
+MUFU_LANES_PER_SM = 32
+ISSUE_LANES_PER_SM = 128  # 4 schedulers x one warp instruction per cycle
 N_SMS = 152
 
 
 def p2p_peak_pairs_per_s(sm_mhz: float) -> float:
-    """ALU roofline of the near-field pair: min(FP32 rate / 20 flops,
-    MUFU rate / 2 ops) per SM per clock, times SMs and clock."""
-    fp32 = FP32_LANES_PER_SM * 2 / P2P_FLOPS_PER_PAIR
-    mufu = MUFU_LANES_PER_SM / 2
-    return min(fp32, mufu) * N_SMS * sm_mhz * 1e6
+    """ALU roofline of the near-field pair: the least of the FP32 pipe
+    (8 instructions), the MUFU pipe (2) and instruction issue (all 10) per SM
+    per clock, times SMs and clock."""
+    fp32 = FP32_LANES_PER_SM / P2P_FP32_INSTR_PER_PAIR
+    mufu = MUFU_LANES_PER_SM / P2P_MUFU_INSTR_PER_PAIR
+    issue = ISSUE_LANES_PER_SM / (P2P_FP32_INSTR_PER_PAIR + P2P_MUFU_INSTR_PER_PAIR)
+    return min(fp32, mufu, issue) * N_SMS * sm_mhz * 1e6
 
 
 class ClockSampler:
@@ -572,8 +580,10 @@ def run_ours(args):
                   + ") then l2p_f32_kernel (far part), timed together from the end of the tree",
         "bound": "alu", "unit": "Gpair/s",
         "achieved": achieved / 1e9, "peak": peak / 1e9, "frac": achieved / peak,
-        "peak_source": f"derived: min(128 FP32 lanes x 2 / {P2P_FLOPS_PER_PAIR} flops, "
-                       f"16 MUFU lanes / 2 ops) per SM per clock x 152 SMs x "
+        "peak_source": f"derived: min(128 FP32 lanes / {P2P_FP32_INSTR_PER_PAIR}, "
+                       f"{MUFU_LANES_PER_SM} MUFU lanes / {P2P_MUFU_INSTR_PER_PAIR}, 128 issue "
+                       f"lanes / {P2P_FP32_INSTR_PER_PAIR + P2P_MUFU_INSTR_PER_PAIR} "
+                       f"instructions) pairs per SM per clock x 152 SMs x "
                        f"{sm_max:.0f} MHz ({peak_kind} sm_max_mhz)",
         "pairs_per_launch": pairs, "near_pairs": near_pairs,
         "ring_pairs": ring_pairs,
