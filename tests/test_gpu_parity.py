@@ -198,6 +198,25 @@ def test_uniform_1m_benchmark_setting():
     assert _rel_speed(uv[t], o1) <= 1e-6, _rel_speed(uv[t], o1)
 
 
+def test_above_the_l2_threshold_every_output():
+    """5 x 2^20 uniform particles: the plan's near parts and velocities
+    (16 B per particle) no longer fit in half the L2, so the near field writes
+    its velocities at the input indices and L2P reads them back there (the
+    other L2P variant from the one the 2^20 tests run).  Every output against
+    the oracle FMM at the same p, L, with and without the cutoff."""
+    n = 5 << 20
+    w = W.uniform_random(n, 77, 2.0 / np.sqrt(n), sigma_over_h=2.0, p=12, L=8,
+                         dtype=np.float32)
+    xy, g = _dev(w, torch.float32)
+    for a in (0.0, 5.0 * w.sigma):
+        from paper_0809_1810_gb300 import Plan
+
+        with Plan(w.p, w.L, w.sigma, "fp32_tc", root=w.root, max_n=w.n, cutoff=a) as plan:
+            uv = plan.velocity(xy, g, check=True).double().cpu().numpy()
+        ref = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.p, w.L, w.root, a=a)
+        assert _rel(uv, ref) <= FP32_TOL, (a, _rel(uv, ref))
+
+
 def test_clustered_16m_against_direct_sum():
     """The large clustered workload (2^24 particles in 64 Gaussian patches,
     sigma = h, p = 20, L = 9, uneven leaf occupancy) in FP32_TC: the GPU FP64
