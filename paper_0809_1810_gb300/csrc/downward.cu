@@ -1,17 +1,18 @@
 // Downward sweep, L2L part (Sec. 3.3.3): for levels 3..L each box adds its
 // parent's complete local expansion, re-expanded about its own centre:
 //   L~_n(child) += sum_{k>=n} L2L[q]_{nk} L~_k(parent),  q = child quadrant.
-// Level l runs after level l-1 is complete.  Levels 3 .. 4 run in one
-// single-CTA launch (a barrier between levels), levels 5 .. L-1 one launch
-// each; the leaf level is folded into the near-field kernel, which forms
-// each leaf's expansion from its own M2L part and its parent's.  The
+// Level l runs after level l-1 is complete.  Levels 3 .. L-1 run two to a
+// launch (a 4 x 4 block of boxes and then its 8 x 8 children per CTA), an
+// odd last level alone; the leaf level is folded into the near-field or L2P
+// kernel, which forms each leaf's expansion from its own M2L part and its
+// parent's.  The
 // 4-quadrant L2L table is staged in shared memory.
 #include "fmm2d_internal.cuh"
 
 namespace fmm2d {
 namespace {
 
-constexpr int kTopLevel = 2;  // levels 3.. run one launch per level (a single CTA serialises them)
+constexpr int kTopLevel = 2;  // the coarsest level with local expansions (M2L only)
 
 template <typename R, int G>
 __device__ __forceinline__ void l2l_box(const Geometry& g, int level, int64_t slot, bool valid,
@@ -61,20 +62,33 @@ l2l_level_kernel(Geometry g, int level, const R* __restrict__ l2l, R* __restrict
     l2l_box<R, G>(g, level, g.level_base[level] + (valid ? gid : 0), valid, tab, le);
 }
 
+// Two consecutive levels in one launch: a CTA takes a 4 x 4 block of boxes at
+// `level`, then the 8 x 8 block of their children at level + 1, with a CTA
+// barrier between (the children read their parents' expansions, which this
+// CTA has just completed).  The per-box arithmetic is l2l_box's, so the
+// expansions are those of two single-level launches bit for bit; the launch
+// saved shortens the far-field branch, whose last kernels can end after the
+// near field.
 template <typename R, int G>
-__global__ void __launch_bounds__(1024)
-l2l_top_kernel(Geometry g, int lhi, const R* __restrict__ l2l, R* __restrict__ le) {
+__global__ void __launch_bounds__(256)
+l2l_two_level_kernel(Geometry g, int level, const R* __restrict__ l2l, R* __restrict__ le) {
     using C = typename Cplx<R>::T;
     __shared__ C tab[4 * G * G];
     stage_l2l_table<R, G>(l2l, tab);
-    for (int level = 3; level <= lhi; ++level) {
-        int64_t nb = (int64_t)1 << (2 * level);
-        for (int64_t base = 0; base < nb * G; base += blockDim.x) {
-            int64_t gid = (base + threadIdx.x) / G;
-            bool valid = gid < nb;
-            l2l_box<R, G>(g, level, g.level_base[level] + (valid ? gid : 0), valid, tab, le);
-        }
-        __syncthreads();
+    constexpr int kPer = 256 / G;  // boxes per sweep of the CTA
+    const uint32_t tiles = 1u << (level - 2);  // 4 x 4 blocks per axis at `level`
+    const uint32_t tx = blockIdx.x % tiles, ty = blockIdx.x / tiles;
+    const int b = threadIdx.x / G;
+#pragma unroll 1
+    for (int b0 = 0; b0 < 16; b0 += kPer) {
+        const uint32_t ix = 4 * tx + ((b0 + b) & 3), iy = 4 * ty + ((b0 + b) >> 2);
+        l2l_box<R, G>(g, level, box_slot(g.level_base, level, ix, iy), true, tab, le);
+    }
+    __syncthreads();  // this CTA's boxes at `level` are complete
+#pragma unroll 1
+    for (int b0 = 0; b0 < 64; b0 += kPer) {
+        const uint32_t ix = 8 * tx + ((b0 + b) & 7), iy = 8 * ty + ((b0 + b) >> 3);
+        l2l_box<R, G>(g, level + 1, box_slot(g.level_base, level + 1, ix, iy), true, tab, le);
     }
 }
 
@@ -112,14 +126,15 @@ cudaError_t launch_batch_l2l(const BatchInst* inst, const BatchLists& bl, int P,
 
 template <typename R>
 cudaError_t launch_l2l(const Geometry& g, const Tables<R>& t, R* le, cudaStream_t s) {
-    int lhi = g.L - 1 < kTopLevel ? g.L - 1 : kTopLevel;
-    if (lhi >= 3) {
+    int level = kTopLevel + 1;
+    for (; level + 1 <= g.L - 1; level += 2) {  // levels in pairs
+        const unsigned blocks = 1u << (2 * (level - 2));
         if (g.P <= 16)
-            l2l_top_kernel<R, 16><<<1, 1024, 0, s>>>(g, lhi, t.l2l, le);
+            l2l_two_level_kernel<R, 16><<<blocks, 256, 0, s>>>(g, level, t.l2l, le);
         else
-            l2l_top_kernel<R, 32><<<1, 1024, 0, s>>>(g, lhi, t.l2l, le);
+            l2l_two_level_kernel<R, 32><<<blocks, 256, 0, s>>>(g, level, t.l2l, le);
     }
-    for (int level = kTopLevel + 1; level <= g.L - 1; ++level) {
+    if (level <= g.L - 1) {  // an odd level left over
         int64_t threads = ((int64_t)1 << (2 * level)) * g.P;
         int blocks = (int)((threads + 255) / 256);
         if (g.P <= 16)
