@@ -289,6 +289,36 @@ def test_truncation_error_within_bound(oracle_lib):
             assert err <= oracle_lib.truncation_bound(A, b, p, dist) * (1 + 1e-12) + 1e-16
 
 
+def test_truncation_bound_is_attained(oracle_lib):
+    """Eqs. 30-31 from above: sources on the circle of radius r, all on the ray
+    from x_* through the evaluation point y, with circulations of one sign,
+    make every step of the bound an equality: the remainder of one source is
+    c ((x - x_*)/(y - x_*))^p / (y - x), of modulus |c| b^p / ((1 - b) |y - x_*|)
+    there.  So the measured error must reach the bound itself; a bound with the
+    1/(1 - b) factor dropped, or with b^(p-1) or b^(p+1), fails here or in the
+    test above."""
+    r = 0.1
+    for theta in (0.0, 0.7, 2.9):
+        u = np.array([math.cos(theta), math.sin(theta)])
+        gam = np.array([0.4, 1.3, 0.25])  # one sign: A = sum |Gamma| / 2pi adds up coherently
+        src = np.tile(r * u, (3, 1))
+        A = np.abs(gam).sum() / (2 * math.pi)
+        for b in (0.3, 0.5, 0.7):
+            dist = r / b
+            y = (dist * u)[None, :]
+            zy = y[0, 0] + 1j * y[0, 1]
+            zs = src[:, 0] + 1j * src[:, 1]
+            exact = (-1j * gam / (2 * math.pi) / (zy - zs)).sum()
+            for p in (2, 5, 10, 20):
+                a = oracle_lib.op_p2m(src[:, 0], src[:, 1], gam, (0.0, 0.0), p)
+                err = abs(oracle_lib.op_me_eval(a, (0.0, 0.0), y[:, 0], y[:, 1])[0] - exact)
+                bound = oracle_lib.truncation_bound(A, b, p, dist)
+                # equality up to the rounding of the series and of the exact sum
+                # (a few ulp of |exact|, large against b^p at p = 20)
+                slack = 1e-9 * bound + 1e-14 * abs(exact)
+                assert abs(err - bound) <= slack, (theta, b, p, err, bound)
+
+
 # --------------------------------------------------------------------------
 # Full FMM (Sec. 3.1, Fig. 3)
 # --------------------------------------------------------------------------
