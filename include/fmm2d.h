@@ -313,8 +313,9 @@ fmm2d_status fmm2d_batch_tree_debug(fmm2d_batch_plan* plan, uint32_t* keys_dev, 
  * library, held by every GPU that loads the library until the process exits.
  * The call makes no cudaMalloc, cudaFree or other allocating call.
  * The first call on a device looks up that array's device address (once per
- * device, with the device current); make that first call before any stream
- * capture.  All calls share the one array and it keeps the last call's
+ * device, with the device current; again only if that device's context was
+ * destroyed and created anew, e.g. by cudaDeviceReset); make that first call
+ * before any stream capture.  All calls share the one array and it keeps the last call's
  * contents (the status word is cleared at the start of each call): calls
  * whose work overlaps on the GPU -- on different streams, or from different
  * host threads -- race on it and must be serialised by the caller. */

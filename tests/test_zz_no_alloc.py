@@ -101,3 +101,48 @@ def test_noalloc_flags_out_of_domain(lib):
     w.x[3] = 1.25
     _, _, _, flags = _noalloc(lib, w, 1, torch.float32)
     assert flags == (1 << 2)
+
+
+@pytest.mark.parametrize("L", [0, 2, 4])
+def test_noalloc_single_pass_depths_match_plan_tree(lib, L):
+    # depths of at most 8 key bits sort in one pass, which goes from the
+    # scratch array straight into the caller's keys and permutation
+    w = W.uniform_random(30001, 90 + L, 2.0 / 173, p=6, L=L, dtype=np.float32)
+    got = _noalloc(lib, w, 1, torch.float32)
+    want = _with_plan(w, "fp32", torch.float32)
+    assert torch.equal(got[0], want[0])
+    assert torch.equal(got[1], want[1])
+    assert torch.equal(got[2], want[2])
+    assert got[3] == 0
+
+
+def test_noalloc_empty_input_gives_empty_leaves(lib):
+    start = torch.full(((1 << 6) + 1,), 7, dtype=torch.int32, device="cuda")
+    flags = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    st = lib.fmm2d_tree_build_noalloc(1, 0, None, None, 3, -1.0, -1.0, 2.0, None, None,
+                                      _p(start), _p(flags), None)
+    assert st == 0
+    torch.cuda.synchronize()
+    assert int(start.abs().sum().item()) == 0  # every leaf range empty
+    assert int(flags.item()) == 0
+
+
+def test_noalloc_without_flags_buffer_uses_its_own_status_word(lib):
+    # flags = NULL: the input-error word lives in the scratch array instead;
+    # the tree is the same
+    w = W.uniform_random(20000, 95, 2.0 / 141, p=6, L=6, dtype=np.float32)
+    n = w.n
+    xy = torch.tensor(np.stack([w.x, w.y], 1), device="cuda")
+    g = torch.tensor(w.gamma, device="cuda")
+    keys = torch.empty(n, dtype=torch.int32, device="cuda")
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    start = torch.empty((1 << 12) + 1, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        st = lib.fmm2d_tree_build_noalloc(1, n, _p(xy), _p(g), w.L, w.root[0], w.root[1],
+                                          w.root[2], _p(keys), _p(perm), _p(start), None, None)
+        assert st == 0
+        torch.cuda.synchronize()
+        want = _with_plan(w, "fp32", torch.float32)
+        assert torch.equal(keys.cpu(), want[0])
+        assert torch.equal(perm.cpu(), want[1])
+        assert torch.equal(start.cpu(), want[2])
