@@ -204,7 +204,10 @@ fmm2d_status fmm2d_error_stats(fmm2d_plan* plan, int64_t n, const void* xy_dev, 
 /* ring > 0: every later fmm2d_velocity call records CUDA events at its phase
  * boundaries (event-record nodes inside the CUDA graph) into the next of
  * `ring` slots, so the last `ring` calls can be read back.  ring = 0 turns
- * timing off.  Synchronises the device; 0 <= ring <= 4096. */
+ * timing off.  While timing is on the FP32 forms run their phases one after
+ * another (untimed, the far-field phases run beside the near field), so each
+ * phase time is the duration of its own kernels.  Synchronises the device;
+ * 0 <= ring <= 4096. */
 fmm2d_status fmm2d_plan_set_timing(fmm2d_plan* plan, int ring);
 
 /* Phase durations in milliseconds of the call made `age` calls ago (0 = the
@@ -433,6 +436,53 @@ fmm2d_status fmm2d_propose(fmm2d_mlp* net, int ncand, const float* features_host
 /* Number of kernel launches one fmm2d_velocity call makes (the kernel nodes
  * of its recorded CUDA graph); -1 before the first call. */
 int fmm2d_plan_kernels_per_call(const fmm2d_plan* plan);
+
+/* A split of one evaluation over several devices (Sec. 3.3: the leaves in
+ * Morton order cut into contiguous key ranges, one per device).  The
+ * multipole expansion of Eq. 20 is linear in the particles, so each device
+ * forms the multipoles of its own particles, the devices add up the partial
+ * expansions of the boxes in each other's interaction lists (Eq. 22, Sec.
+ * 3.3.1), and each device then evaluates its own particles together with
+ * the halo particles of the neighbouring leaves (Eq. 10) from the summed
+ * multipoles.  The caller moves the data (peer copies or NCCL).
+ *
+ * Length, in reals of the plan's element type, of its multipole array:
+ * boxes of levels 2..L one level after another, each level four parity
+ * planes (ix & 1, iy & 1) of a row-major (2^(level-1))^2 grid of boxes,
+ * 2P reals per box (P = 16 when p <= 16, else 32; coefficient k as (re, im)
+ * at reals 2k, 2k+1, scaled by the box width: a~_k = a_k / s^k; zero beyond
+ * p).  0 when L < 2. */
+int64_t fmm2d_plan_multipole_reals(const fmm2d_plan* plan);
+
+/* Tree build, P2M (Eq. 20) and M2M (Sec. 3.3.2) of n particles; the
+ * multipoles of every box are written to me_dev (device,
+ * fmm2d_plan_multipole_reals reals, caller-owned).  Launched on `stream`
+ * directly (no graph); input errors as for fmm2d_velocity. */
+fmm2d_status fmm2d_multipoles(fmm2d_plan* plan, int64_t n, const void* xy_dev,
+                              const void* gamma_dev, void* me_dev, cudaStream_t stream);
+
+/* The rest of one evaluation from given multipoles: tree build of the n
+ * particles, M2L (Eq. 22) and L2L (Sec. 3.3.3) from me_dev (read, not
+ * changed), then the near field over the n particles and L2P (Eqs. 10, 12),
+ * velocities of all n particles to uv_dev in input order.  In a split,
+ * the n particles are the device's own followed by its halo particles
+ * (sources only: their velocities lack parts and are to be discarded), and
+ * me_dev the summed multipoles.  Launched on `stream` directly (no graph). */
+fmm2d_status fmm2d_velocity_from_multipoles(fmm2d_plan* plan, int64_t n, const void* xy_dev,
+                                            const void* gamma_dev, const void* me_dev,
+                                            void* uv_dev, cudaStream_t stream);
+
+/* Failure detection (no counterpart in the paper): every wait of the
+ * tensor-core M2L (FMM2D_FP32_TC) on a pipeline barrier polls at most
+ * `polls` times (each poll suspends the waiting thread for about 32 ns);
+ * when one runs out the kernel stops, records FMM2D_TIMEOUT (reported by
+ * fmm2d_plan_check), waits for the copies and MMAs it already issued with
+ * the default limit, frees its tensor memory and returns, leaving the
+ * affected local expansions unwritten.  polls = 0 restores the default
+ * (2^26 polls, about two seconds: never reached by a healthy run).  A small
+ * limit exists to test this path without hanging or faulting the GPU.  The
+ * next fmm2d_velocity call records its graph anew. */
+fmm2d_status fmm2d_plan_set_spin_limit(fmm2d_plan* plan, uint32_t polls);
 
 #ifdef __cplusplus
 }

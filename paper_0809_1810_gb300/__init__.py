@@ -231,6 +231,34 @@ class Plan:
         """Kernel launches one velocity call makes (-1 before the first)."""
         return int(self._lib.fmm2d_plan_kernels_per_call(self._h))
 
+    def multipole_reals(self) -> int:
+        """Length of the plan's multipole array (fmm2d_plan_multipole_reals)."""
+        return int(self._lib.fmm2d_plan_multipole_reals(self._h))
+
+    def multipoles(self, xy, gamma, out=None, stream=None):
+        """Multipoles of every box from these particles (tree, P2M, M2M)."""
+        n = xy.shape[0]
+        if out is None:
+            out = torch.zeros(max(self.multipole_reals(), 1), dtype=xy.dtype, device=xy.device)
+        _check(self._lib.fmm2d_multipoles(self._h, n, _ptr(xy), _ptr(gamma), _ptr(out),
+                                          _stream(stream)), "multipoles")
+        return out
+
+    def velocity_from_multipoles(self, xy, gamma, me, out=None, stream=None):
+        """The evaluation with P2M and M2M replaced by the given multipoles."""
+        n = xy.shape[0]
+        if out is None:
+            out = torch.empty((n, 2), dtype=xy.dtype, device=xy.device)
+        _check(self._lib.fmm2d_velocity_from_multipoles(self._h, n, _ptr(xy), _ptr(gamma),
+                                                        _ptr(me), _ptr(out), _stream(stream)),
+               "velocity_from_multipoles")
+        return out
+
+    def set_spin_limit(self, polls: int):
+        """Poll limit of the tensor-core M2L's device waits (0: the default);
+        a small limit makes them run out (FMM2D_TIMEOUT at the next check)."""
+        _check(self._lib.fmm2d_plan_set_spin_limit(self._h, int(polls)), "set_spin_limit")
+
     def phase_ms(self, age: int = 0):
         buf = (ctypes.c_double * NUM_PHASES)()
         _check(self._lib.fmm2d_plan_phase_ms(self._h, int(age), buf), "phase_ms")

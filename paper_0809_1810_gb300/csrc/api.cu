@@ -91,11 +91,11 @@ struct fmm2d_plan {
     void* tc_ws = nullptr;
     float* me_hi = nullptr;
     float* me_lo = nullptr;
-    float* bt_hi = nullptr;
-    float* bt_lo = nullptr;
+    float* bimg = nullptr;  // operator stages
     int4* tiles = nullptr;
-    int ntiles = 0;
+    M2LTcConfig tc{};
     M2LTcMaps* maps = nullptr;
+    uint32_t spin = 0;  // poll limit of its device waits (0: the default)
 };
 
 namespace {
@@ -165,45 +165,60 @@ cudaError_t enqueue(fmm2d_plan* pl, int64_t n, const R* xy, const R* gamma, R* u
     if (sizeof(R) == 4 && g.L >= 2 && pl->cap2 && n > 0) {
         // FP32 forms: the near field (without its far part) starts with the
         // tree done, on the whole persistent grid; the far field runs on a
-        // second branch of the graph, its latency-bound kernels filling the
-        // SMs that the near field's last work items leave idle; L2P adds the
-        // far part once both are done (the fused kernel's sum, bit for bit).
-        // Measured against the sequential order: 7% faster at 2^20
-        // particles (L = 7), 3% at 2^24.
+        // second branch of the graph, its kernels filling the SMs that the
+        // near field's last work items leave idle; L2P adds the far part once
+        // both are done (the fused kernel's sum, bit for bit).  Measured
+        // against the sequential order: 7% faster at 2^20 particles (L = 7),
+        // 3% at 2^24.  A timed graph (phase marks on) runs the same kernels
+        // one after another instead, so that each phase is the duration of
+        // its own kernels, not of their wait for room on the GPU.
         float* uvf = reinterpret_cast<float*>(uv);
-        STEP(cudaEventRecord(pl->ev_fork, s));
-        STEP(cudaStreamWaitEvent(pl->cap2, pl->ev_fork, 0));
+        const bool fork = pl->ring == 0;
         // the near parts go to a sorted-order buffer (coalesced) while it and
         // the velocities fit in half the L2; beyond that the partial-sector
         // writes of the scattered final store reach memory, and reading the
         // near parts back at the input indices costs less (measured at 2^24:
         // 1.2% of the step)
         const bool sorted = (uint64_t)n * 4 * sizeof(float) <= pl->l2_bytes / 2;
-        STEP(launch_near_only_f32(g, pl->prm.sigma, n, pl->particles, skeys, pl->sb.leaf_start,
-                                  pl->p2p_counter, sorted ? pl->uv_sorted : uvf, sorted, s));
-        cudaStream_t s2 = pl->cap2;
+        auto near_only = [&]() {
+            return launch_near_only_f32(g, pl->prm.sigma, n, pl->particles, skeys,
+                                        pl->sb.leaf_start, pl->p2p_counter,
+                                        sorted ? pl->uv_sorted : uvf, sorted, s);
+        };
+        cudaStream_t s2 = s;
+        if (fork) {
+            STEP(cudaEventRecord(pl->ev_fork, s));
+            STEP(cudaStreamWaitEvent(pl->cap2, pl->ev_fork, 0));
+            STEP(near_only());
+            s2 = pl->cap2;
+        }
         STEP(launch_p2m<R>(g, pl->particles, pl->sb.leaf_start, t, me, s2));
         STEP(mark(pl, 2, s2));
         if (g.L >= 4) STEP(launch_m2m<R>(g, t, me, s2));
         STEP(mark(pl, 3, s2));
         if (pl->prm.precision == FMM2D_FP32_TC) {
-            STEP(launch_m2l_tc(g, *pl->maps, pl->tiles, pl->ntiles,
+            STEP(launch_m2l_tc(g, pl->tc, *pl->maps, pl->tiles,
                                reinterpret_cast<const float*>(me), pl->me_hi, pl->me_lo,
-                               reinterpret_cast<float*>(le), pl->d_status, s2));
+                               pl->bimg, reinterpret_cast<float*>(le), pl->d_status, pl->spin,
+                               s2));
         } else {
             STEP(launch_m2l<R>(g, t, me, le, s2));
         }
         STEP(mark(pl, 4, s2));
         if (g.L >= 4) STEP(launch_l2l<R>(g, t, le, s2));
         STEP(mark(pl, 5, s2));
-        STEP(cudaEventRecord(pl->ev_join, s2));
-        STEP(cudaStreamWaitEvent(s, pl->ev_join, 0));
+        if (fork) {
+            STEP(cudaEventRecord(pl->ev_join, s2));
+            STEP(cudaStreamWaitEvent(s, pl->ev_join, 0));
+        } else {
+            STEP(near_only());
+        }
         STEP(launch_l2p_f32(g, pl->prm.sigma, pl->particles, pl->sb.leaf_start,
                             reinterpret_cast<const float*>(le),
                             reinterpret_cast<const float*>(t.l2l),
                             sorted ? pl->uv_sorted : nullptr, uvf, s));
         STEP(mark(pl, 6, s));
-        pl->overlapped = true;
+        pl->overlapped = fork;
         return cudaSuccess;
     }
     pl->overlapped = false;
@@ -213,9 +228,10 @@ cudaError_t enqueue(fmm2d_plan* pl, int64_t n, const R* xy, const R* gamma, R* u
     STEP(mark(pl, 3, s));
     if (g.L >= 2) {
         if (pl->prm.precision == FMM2D_FP32_TC) {
-            STEP(launch_m2l_tc(g, *pl->maps, pl->tiles, pl->ntiles,
+            STEP(launch_m2l_tc(g, pl->tc, *pl->maps, pl->tiles,
                                reinterpret_cast<const float*>(me), pl->me_hi, pl->me_lo,
-                               reinterpret_cast<float*>(le), pl->d_status, s));
+                               pl->bimg, reinterpret_cast<float*>(le), pl->d_status, pl->spin,
+                               s));
         } else {
             STEP(launch_m2l<R>(g, t, me, le, s));
         }
@@ -226,9 +242,61 @@ cudaError_t enqueue(fmm2d_plan* pl, int64_t n, const R* xy, const R* gamma, R* u
     STEP(launch_p2p_l2p<R>(g, pl->prm.sigma, n, pl->particles, skeys, pl->sb.leaf_start,
                            pl->p2p_counter, le, t.l2l, uv, s));
     STEP(mark(pl, 6, s));
-#undef STEP
     return cudaSuccess;
 }
+
+// Partial evaluations for a split of one evaluation over several devices,
+// launched directly on the caller's stream (not recorded in the graph):
+// upward (tree, P2M, M2M; the multipoles copied to me_out), or the rest of
+// the evaluation from a complete multipole array me_in (tree, M2L, L2L, near
+// field and L2P), the steps of Sec. 3.1 in the same order.
+template <typename R>
+cudaError_t enqueue_partial(fmm2d_plan* pl, bool upward, int64_t n, const R* xy, const R* gamma,
+                            const R* me_in, R* me_out, R* uv, cudaStream_t s) {
+    const Geometry& g = pl->geo;
+    Tables<R> t = tables_of<R>(pl);
+    R* me = static_cast<R*>(pl->me);
+    R* le = static_cast<R*>(pl->le);
+    const size_t me_bytes = (size_t)g.nboxes * 2 * g.P * sizeof(R);
+    cudaError_t e;
+    STEP(launch_tree_build<R>(g, n, xy, gamma, pl->sb, pl->particles, s));
+    const uint32_t* skeys = pl->sb.keys[sort_passes(2 * g.L) & 1];
+    if (upward) {
+        if (g.L >= 2) {
+            STEP(launch_p2m<R>(g, pl->particles, pl->sb.leaf_start, t, me, s));
+            if (g.L >= 4) STEP(launch_m2m<R>(g, t, me, s));
+            STEP(cudaMemcpyAsync(me_out, me, me_bytes, cudaMemcpyDeviceToDevice, s));
+        }
+        return cudaSuccess;
+    }
+    if (g.L >= 2) {
+        STEP(cudaMemcpyAsync(me, me_in, me_bytes, cudaMemcpyDeviceToDevice, s));
+        if (pl->prm.precision == FMM2D_FP32_TC) {
+            STEP(launch_m2l_tc(g, pl->tc, *pl->maps, pl->tiles,
+                               reinterpret_cast<const float*>(me), pl->me_hi, pl->me_lo,
+                               pl->bimg, reinterpret_cast<float*>(le), pl->d_status, pl->spin,
+                               s));
+        } else {
+            STEP(launch_m2l<R>(g, t, me, le, s));
+        }
+        if (g.L >= 4) STEP(launch_l2l<R>(g, t, le, s));
+    }
+    if (sizeof(R) == 4 && g.L >= 2 && n > 0) {
+        float* uvf = reinterpret_cast<float*>(uv);
+        const bool sorted = (uint64_t)n * 4 * sizeof(float) <= pl->l2_bytes / 2;
+        STEP(launch_near_only_f32(g, pl->prm.sigma, n, pl->particles, skeys, pl->sb.leaf_start,
+                                  pl->p2p_counter, sorted ? pl->uv_sorted : uvf, sorted, s));
+        STEP(launch_l2p_f32(g, pl->prm.sigma, pl->particles, pl->sb.leaf_start,
+                            reinterpret_cast<const float*>(le),
+                            reinterpret_cast<const float*>(t.l2l),
+                            sorted ? pl->uv_sorted : nullptr, uvf, s));
+        return cudaSuccess;
+    }
+    STEP(launch_p2p_l2p<R>(g, pl->prm.sigma, n, pl->particles, skeys, pl->sb.leaf_start,
+                           pl->p2p_counter, le, t.l2l, uv, s));
+    return cudaSuccess;
+}
+#undef STEP
 
 void drop_graph(fmm2d_plan* pl) {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
@@ -474,21 +542,12 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
             if (e != cudaSuccess) return cleanup(cuda_fail(e, "tensor-core M2L configuration"));
             configured = true;
         }
-        int ntiles = 0;
-        size_t me_floats = (size_t)g.nboxes * 2 * g.P;
-        size_t bt_floats = (size_t)kOffsetSlots * 4 * g.P * g.P;
-        // tile count first (no device work), then one allocation for everything
-        {
-            int cnt = 0;
-            for (int l = 2; l <= g.L; ++l) {
-                int Wh = 1 << (l - 1), bw = Wh < 128 ? Wh : 128;
-                int bh = (128 / bw) < Wh ? 128 / bw : Wh;
-                cnt += 4 * ((Wh + bh - 1) / bh) * ((Wh + bw - 1) / bw);
-            }
-            ntiles = cnt;
-        }
-        size_t bytes = align256(me_floats * 4) * 2 + align256(bt_floats * 4) * 2 +
-                       align256((size_t)ntiles * sizeof(int4));
+        M2LTcConfig cfg = m2l_tc_plan(g, nullptr);  // tile count first (no device work)
+        std::vector<int4> tiles(cfg.ntiles);
+        cfg = m2l_tc_plan(g, tiles.data());
+        size_t me_floats = (size_t)g.nboxes * 2 * cfg.Pk;
+        size_t bytes = align256(me_floats * 4) * 2 + align256((size_t)cfg.b_floats * 4) +
+                       align256((size_t)cfg.ntiles * sizeof(int4));
         e = cudaMalloc(&pl->tc_ws, bytes);
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "tensor-core workspace cudaMalloc"));
         char* q = static_cast<char*>(pl->tc_ws);
@@ -496,24 +555,19 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
         q += align256(me_floats * 4);
         pl->me_lo = (float*)q;
         q += align256(me_floats * 4);
-        pl->bt_hi = (float*)q;
-        q += align256(bt_floats * 4);
-        pl->bt_lo = (float*)q;
-        q += align256(bt_floats * 4);
+        pl->bimg = (float*)q;
+        q += align256((size_t)cfg.b_floats * 4);
         pl->tiles = (int4*)q;
         pl->maps = new M2LTcMaps();
-        std::vector<int4> tiles(ntiles);
-        int count = 0;
         int64_t per = (int64_t)g.P * g.P * 2;
-        e = m2l_tc_prepare(g, pl->tab64 + 8 * per, pl->me_hi, pl->me_lo, pl->bt_hi, pl->bt_lo,
-                           pl->maps, tiles.data(), &count, pl->cap);
-        if (e == cudaSuccess && count != ntiles) e = cudaErrorInvalidValue;
+        e = m2l_tc_prepare(g, cfg, pl->tab64 + 8 * per, pl->me_hi, pl->me_lo, pl->bimg, pl->maps,
+                           pl->cap);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(pl->tiles, tiles.data(), (size_t)ntiles * sizeof(int4),
+            e = cudaMemcpyAsync(pl->tiles, tiles.data(), (size_t)cfg.ntiles * sizeof(int4),
                                 cudaMemcpyHostToDevice, pl->cap);
         if (e == cudaSuccess) e = cudaStreamSynchronize(pl->cap);
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "tensor-core M2L set-up"));
-        pl->ntiles = ntiles;
+        pl->tc = cfg;
     }
     *out = pl;
     return FMM2D_OK;
@@ -571,6 +625,47 @@ static fmm2d_status ensure_staging(fmm2d_plan* pl) {
     pl->st_gamma = static_cast<char*>(buf) + bxy;
     pl->st_uv = static_cast<char*>(buf) + bxy + bg;
     pl->st_u1 = static_cast<char*>(buf) + 2 * bxy + bg;
+    return FMM2D_OK;
+}
+
+int64_t fmm2d_plan_multipole_reals(const fmm2d_plan* pl) {
+    return pl ? pl->geo.nboxes * 2 * pl->geo.P : -1;
+}
+
+fmm2d_status fmm2d_multipoles(fmm2d_plan* pl, int64_t n, const void* xy, const void* gamma,
+                              void* me_dev, cudaStream_t stream) {
+    if (!pl) return fail(FMM2D_INVALID_ARG, "null plan");
+    if (n < 0 || n > pl->prm.max_n) return fail(FMM2D_INVALID_ARG, "n out of [0, max_n]");
+    if ((n > 0 && (!xy || !gamma)) || (pl->geo.nboxes > 0 && !me_dev))
+        return fail(FMM2D_INVALID_ARG, "null buffer");
+    cudaError_t e = pl->elem == 8
+                        ? enqueue_partial<double>(pl, true, n, static_cast<const double*>(xy),
+                                                  static_cast<const double*>(gamma), nullptr,
+                                                  static_cast<double*>(me_dev), nullptr, stream)
+                        : enqueue_partial<float>(pl, true, n, static_cast<const float*>(xy),
+                                                 static_cast<const float*>(gamma), nullptr,
+                                                 static_cast<float*>(me_dev), nullptr, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "multipoles");
+    return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_velocity_from_multipoles(fmm2d_plan* pl, int64_t n, const void* xy,
+                                            const void* gamma, const void* me_dev, void* uv,
+                                            cudaStream_t stream) {
+    if (!pl) return fail(FMM2D_INVALID_ARG, "null plan");
+    if (n < 0 || n > pl->prm.max_n) return fail(FMM2D_INVALID_ARG, "n out of [0, max_n]");
+    if ((n > 0 && (!xy || !gamma || !uv)) || (pl->geo.nboxes > 0 && !me_dev))
+        return fail(FMM2D_INVALID_ARG, "null buffer");
+    cudaError_t e = pl->elem == 8
+                        ? enqueue_partial<double>(pl, false, n, static_cast<const double*>(xy),
+                                                  static_cast<const double*>(gamma),
+                                                  static_cast<const double*>(me_dev), nullptr,
+                                                  static_cast<double*>(uv), stream)
+                        : enqueue_partial<float>(pl, false, n, static_cast<const float*>(xy),
+                                                 static_cast<const float*>(gamma),
+                                                 static_cast<const float*>(me_dev), nullptr,
+                                                 static_cast<float*>(uv), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "velocity_from_multipoles");
     return FMM2D_OK;
 }
 
@@ -748,5 +843,12 @@ fmm2d_status fmm2d_plan_phase_ms(fmm2d_plan* pl, int age, double* ms) {
 }
 
 int fmm2d_plan_kernels_per_call(const fmm2d_plan* pl) { return pl ? pl->kernel_nodes : -1; }
+
+fmm2d_status fmm2d_plan_set_spin_limit(fmm2d_plan* pl, uint32_t polls) {
+    if (!pl) return fail(FMM2D_INVALID_ARG, "null plan");
+    pl->spin = polls;
+    drop_graph(pl);  // the limit is a kernel argument recorded in the graph
+    return FMM2D_OK;
+}
 
 }  // extern "C"

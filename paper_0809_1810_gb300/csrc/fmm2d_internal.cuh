@@ -241,21 +241,42 @@ cudaError_t launch_batch_error(const BatchInst* inst, const int64_t* dev_offsets
                                double* leaf_err, uint32_t nleaf_total, int* status,
                                cudaStream_t s);
 
-// Tensor maps of the tensor-core M2L: multipole hi/lo parts per level (4D:
-// 2P reals x row x column x parity plane) and the real-ified offset matrices
-// (3D: k' x n' x offset slot).
+// Tensor-core M2L (m2l_tc.cu).  The 27 interaction-list boxes of each of the
+// four children of a target parent are the children of the parent's 8
+// neighbours, so per neighbour offset D the operator is one dense block
+// matrix [4 target children x 2Pk] x [4 source children x 2Pk] (zero blocks
+// for adjacent children, which the near field takes), Pk = p rounded up to a
+// multiple of 4.  Multipole hi/lo parts are kept per level in a layout made
+// for TMA boxes of a tile's source halo: [parity plane][k-group of 4 reals]
+// [row][column][4 reals]; one 4-D map per level and part.
 struct M2LTcMaps {
     CUtensorMap me_hi[kMaxL + 1];
     CUtensorMap me_lo[kMaxL + 1];
-    CUtensorMap b_hi, b_lo;
 };
-int m2l_tc_smem_bytes(int P);
+// Per-plan configuration of the tensor-core M2L.
+struct M2LTcConfig {
+    int Pk;             // p rounded up to a multiple of 4 (4..32)
+    int ntiles;         // CTAs: tiles of target parents over levels 2..L
+    int halo_bytes;     // shared memory of one halo slot (hi or lo part)
+    int b_stages;       // operator stages in flight
+    int smem;           // dynamic shared memory per CTA
+    int64_t b_floats;   // size of the operator image
+};
+// Default bound on the polls of one device wait in the tensor-core M2L: long
+// enough never to expire in a correct run, short enough that a hung pipeline
+// returns FMM2D_TIMEOUT instead of holding the GPU.
+constexpr uint32_t kSpinDefault = 1u << 26;
 cudaError_t m2l_tc_configure();
-cudaError_t m2l_tc_prepare(const Geometry& g, const double* m2l64, float* me_hi, float* me_lo,
-                           float* bhi, float* blo, M2LTcMaps* maps, int4* tiles_host, int* ntiles,
+// Host-side plan of the tiles and shared memory (no device work).
+M2LTcConfig m2l_tc_plan(const Geometry& g, int4* tiles_host);
+// Tensor maps, tile list upload and the operator image (FP64 tables split
+// into TF32 hi/lo, laid out as the kernel's shared-memory stages).
+cudaError_t m2l_tc_prepare(const Geometry& g, const M2LTcConfig& cfg, const double* m2l64,
+                           float* me_hi, float* me_lo, float* bimg, M2LTcMaps* maps,
                            cudaStream_t s);
-cudaError_t launch_m2l_tc(const Geometry& g, const M2LTcMaps& maps, const int4* tiles, int ntiles,
-                          const float* me, float* me_hi, float* me_lo, float* le, int* status,
+cudaError_t launch_m2l_tc(const Geometry& g, const M2LTcConfig& cfg, const M2LTcMaps& maps,
+                          const int4* tiles, const float* me, float* me_hi, float* me_lo,
+                          const float* bimg, float* le, int* status, uint32_t spin,
                           cudaStream_t s);
 
 template <typename R>

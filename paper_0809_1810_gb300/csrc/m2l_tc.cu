@@ -1,41 +1,80 @@
-// M2L (Eq. 22) as a dense contraction on the 5th-generation tensor cores,
-// in 3xTF32 split products with FP32 accumulation in tensor memory.
+// M2L (Eq. 22) over the interaction lists (Sec. 3.3.1) as a dense
+// contraction on the 5th-generation tensor cores, in 3xTF32 split products
+// with FP32 accumulation in tensor memory.
 //
-// With box-size-scaled expansions the M2L operator of a source box at offset
-// (dx, dy) from the target is one fixed complex P x P matrix (tables.cu).
-// Written over real numbers (re/im interleaved), the local expansions of a
-// tile of 128 same-parity target boxes are
-//   LE[128 x 2P] = sum_{27 offsets} ME_shifted[128 x 2P] * B_offset[2P x 2P].
-// The expansion arrays are stored as four parity planes per level, each a
-// row-major grid, so for a fixed offset the 128 source rows of a tile form a
-// rectangle of one source plane: one TMA box, with the domain edge
-// zero-filled by the copy engine.
+// Formulation.  With box-size-scaled expansions the M2L operator between two
+// boxes of one level depends only on their offset (tables.cu), and the
+// interaction list of a box is the children of its parent's neighbours that
+// are not its own neighbours.  So for a target parent T and each of its 8
+// neighbour offsets D, the local expansions of T's four children receive
+//   LE[T, 4 x 2Pk] += ME[T + D, 4 x 2Pk] * B_D[4 x 2Pk, 4 x 2Pk]
+// where B_D holds the scaled child-offset matrices (real-ified: re/im
+// interleaved) and zero blocks where the two children are adjacent (those
+// pairs belong to the near field or to a finer level), Pk = p rounded up to
+// a multiple of 4.  One tile of 128 target parents is the GEMM
+//   D[128 x N] = sum over (D, source child, k) of A * B,   N = 8 Pk <= 256,
+// one column per real coefficient of the four children.
 //
-// Precision: x = hi + lo with hi = tf32(x) (round to nearest) and
-// lo = tf32(x - hi); D = A_hi B_hi + A_hi B_lo + A_lo B_hi, so the products
-// carry ~22 bits.  The tensor core's accumulation truncates, and its error
-// grows with the number of MMAs summed into one accumulator, so the products
-// go to 8 accumulators in tensor memory -- the A_hi B_hi products of the 27
-// offsets spread round-robin over 7, all correction products (small) in the
-// 8th -- and the epilogue adds the 8 with round-to-nearest FP32 adds.  The
-// multipole expansions are split by m2l_split_kernel, the matrices once per
-// plan by m2l_tc_tables_kernel.
+// Data reuse.  A tile is a tw x th rectangle of target parents; its source
+// parents are the (tw+2) x (th+2) halo around it.  The halo is loaded once
+// per K chunk by TMA into shared memory in the no-swizzle K-major layout,
+// whose rows sit 16 bytes apart within a k-group (4 reals): target parent
+// (x, y) is MMA row m = y Hw + x (Hw = tw + 2), and the source parent at
+// offset D is halo row m + (Hw + 1) + D_y Hw + D_x, so the 8 offsets read the
+// same halo through descriptors whose start address moves by whole rows.
+// MMA rows that fall on halo columns are computed and discarded.  The
+// operator stages (B_D for one source child and K chunk, hi and lo) are
+// stored in global memory exactly as the kernel's shared-memory slots hold
+// them and arrive by plain bulk copies.
 //
-// CTA = 4 warps.  Warp 0 lane 0 issues the TMA copies into an S-stage ring,
-// warp 1 lane 0 issues tcgen05.mma (M = 128, N = 2P, K = 8) and commits each
-// stage back to the producer; all 128 threads then read the accumulator
-// rows from tensor memory (thread t = row t) and store the local expansions.
-// Every wait on an mbarrier is bounded; on expiry the kernel records
-// FMM2D_TIMEOUT in the status word, drains what it issued, frees tensor
-// memory and returns.
+// Precision: x = hi + lo with hi = tf32(x) (round to nearest) and lo =
+// tf32(x - hi); D = A_hi B_hi + A_hi B_lo + A_lo B_hi.  The tensor core's
+// accumulation truncates and its error grows with the number of MMAs summed
+// into one accumulator, so the A_hi B_hi products go to chains of 16 MMAs (two
+// K chunks of the 8 offsets) in a tensor-memory accumulator that the epilogue
+// warps drain into FP32 registers with round-to-nearest adds (two such
+// accumulators alternate when tensor memory has room for them); the small
+// correction products all go to one accumulator, added at the end.
+//
+// CTA = 10 warps.  Warp 8 lane 0 issues the TMA halo boxes and the bulk
+// copies of the operator stages into rings of shared-memory slots; warp 9
+// lane 0 issues tcgen05.mma (M = 128, N = 8 Pk, K = 8) and commits every slot
+// back to the producer; warps 0-7 drain the accumulators (warp w reads tensor
+// memory lanes 32 (w % 4) + [0, 32), column half w / 4) and store the local
+// expansions.  Every wait on an mbarrier is bounded by a poll limit; when one
+// runs out the kernel records FMM2D_TIMEOUT, stops issuing, waits with the
+// default limit for the copies it issued and for the MMAs it issued (the MMA
+// thread commits them to `done` on every path), then frees tensor memory and
+// returns.
 #include <cuda.h>
+
+#include <algorithm>
+#include <climits>
 
 #include "fmm2d_internal.cuh"
 
 namespace fmm2d {
 namespace {
 
-constexpr uint32_t kSpinLimit = 1u << 24;
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kProducerWarp = 8;
+constexpr int kMmaWarp = 9;
+constexpr int kHaloSlots = 4;
+constexpr int kMaxBStages = 24;
+constexpr int kChainSteps = 2;          // K chunks per main-accumulator chain: 16 MMAs
+constexpr uint32_t kPollNs = 32;        // suspend hint of one poll
+// dynamic shared memory a CTA opts into: the 227 KB per block less room for
+// the kernel's static barriers
+constexpr int kSmemLimit = 226 * 1024;
+
+// Tensor-memory columns of a CTA: a power of two >= 32 covering the main
+// accumulators and the correction accumulator.
+__host__ __device__ constexpr uint32_t tmem_cols(int n_cols) {
+    return n_cols <= 32 ? 32u : n_cols <= 64 ? 64u : n_cols <= 128 ? 128u : n_cols <= 256 ? 256u
+                                                                                       : 512u;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -48,44 +87,62 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
                  "r"(bytes)
                  : "memory");
 }
-// Bounded wait for the phase with parity `phase` to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t phase) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
-        uint32_t ok;
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+// Wait for the phase with parity `phase`: at most `limit` polls of about
+// kPollNs each; gives up early once `abort` is set (null: never).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t phase, uint32_t limit,
+                                          volatile int* abort) {
+    {  // non-blocking first test: a phase already complete costs no suspension
+        uint32_t done;
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
             " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
+            : "=r"(done)
             : "r"(smem_u32(b)), "r"(phase)
             : "memory");
+        if (done) return true;
+    }
+    for (uint32_t it = 0; it < limit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(b)), "r"(phase), "r"(kPollNs)
+            : "memory");
         if (ok) return true;
+        if (abort && *abort) return false;
     }
     return false;
 }
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, int c3, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
-        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1,
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
                                             int c2, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
         "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
         : "memory");
 }
-// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzled
-// canonical layout (rows of 128 B, 8-row groups 1024 B apart).
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(dst),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// Shared-memory matrix descriptor, K-major operand in the no-swizzle layout:
+// core matrices of 8 rows x 16 bytes, rows 16 bytes apart (stride byte offset
+// 128 between 8-row groups), k-groups `kstride` bytes apart (leading byte
+// offset).  Any 16-byte-aligned start address is legal, so the operand can
+// begin at any row.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t kstride) {
     uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)1 << 16;            // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset between 8-row groups
-    d |= (uint64_t)1 << 46;            // descriptor version
-    d |= (uint64_t)2 << 61;            // 128-byte swizzle
+    d |= (uint64_t)((kstride >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)(128 >> 4) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version; swizzle bits 0 = none
     return d;
 }
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc,
@@ -101,20 +158,16 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
             smem_u32(bar))
         : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -126,82 +179,155 @@ __host__ __device__ constexpr uint32_t idesc_tf32(uint32_t n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-constexpr int kAccs = 8;       // accumulators in tensor memory
-constexpr int kMainAccs = 7;   // for A_hi B_hi; the last one takes the corrections
+// Parent offsets per operator stage: enough MMAs (3 per offset) between two
+// barrier round trips of the issuing thread to keep the tensor pipe busy,
+// within shared memory (a stage is 64 N bytes per offset).
+__host__ __device__ constexpr int offsets_per_stage(int n_cols) { return n_cols <= 192 ? 4 : 2; }
 
-// KC K-chunks of 32 floats (2P = 32 KC), ST pipeline stages.  At 2P = 32 a
-// stage is 40 KB: two stages let two CTAs share an SM (many tiles), four
-// keep more loads in flight for one CTA per SM (fewer tiles than SMs).  At
-// 2P = 64 a stage is 96 KB and two fit.
-template <int KC, int ST>
-struct TcShape {
-    static constexpr int kN = 32 * KC;                    // 2P columns
-    static constexpr int kTmemCols = kAccs * kN;          // 256 or 512 (power of two)
-    static constexpr int kStages = ST;
-    static constexpr int kABytes = 128 * 128;             // one 128 x 32-float K chunk
-    static constexpr int kBBytes = kN * 128;              // one kN x 32-float K chunk
-    static constexpr int kStageBytes = 2 * KC * (kABytes + kBBytes);
-    static constexpr int kSmem = kStages * kStageBytes + 1024;  // + alignment slack
+// Neighbour offset d (0..7) of a parent: the 3 x 3 block without its centre.
+__host__ __device__ inline void parent_offset(int d, int* dx, int* dy) {
+    const int idx = d < 4 ? d : d + 1;
+    *dx = idx % 3 - 1;
+    *dy = idx / 3 - 1;
+}
+
+struct M2LTcArgs {
+    const int4* tiles;  // (level, X0, Y0, tw | th << 8) per CTA
+    const float* bimg;  // operator stages
+    float* le;
+    int* status;
+    int64_t level_base[kMaxL + 2];
+    int P;           // terms per box in the expansion arrays
+    int halo_bytes;  // one halo slot (hi or lo part)
+    int b_stages;    // operator slots
+    uint32_t spin;   // poll limit of the pipeline waits
 };
 
+// Multipoles split into TF32 hi/lo parts in the halo layout: box b of level
+// l (parity plane, row Y, column X of its plane) goes to
+// [level_base[l] KG + ((plane KG + kg) G + Y) G + X] (float4 units), kg the
+// k-group of 4 reals, KG = Pk / 2, G = 2^(l-1).
 __global__ void __launch_bounds__(256)
-m2l_split_kernel(const float* __restrict__ me, float* __restrict__ hi, float* __restrict__ lo,
-                 int64_t count) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        float x = me[i];
-        float h = tf32_rna(x);
-        hi[i] = h;
-        lo[i] = tf32_rna(x - h);
+m2l_tc_split_kernel(const float* __restrict__ me, float4* __restrict__ hi,
+                    float4* __restrict__ lo, Geometry g, int Pk) {
+    const int KG = Pk / 2;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < g.nboxes;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int l = slot_level(g.level_base, g.L, b);
+        const int64_t G = (int64_t)1 << (l - 1);
+        const int64_t r = b - g.level_base[l];
+        const int64_t plane = r / (G * G), rem = r % (G * G);
+        const float4* src = reinterpret_cast<const float4*>(me + b * (2 * g.P));
+        const int64_t out0 = g.level_base[l] * KG + (plane * KG * G) * G + rem;
+        for (int kg = 0; kg < KG; ++kg) {
+            const float4 v = src[kg];
+            float4 h, o;
+            h.x = tf32_rna(v.x);
+            h.y = tf32_rna(v.y);
+            h.z = tf32_rna(v.z);
+            h.w = tf32_rna(v.w);
+            o.x = tf32_rna(v.x - h.x);
+            o.y = tf32_rna(v.y - h.y);
+            o.z = tf32_rna(v.z - h.z);
+            o.w = tf32_rna(v.w - h.w);
+            const int64_t at = out0 + (int64_t)kg * G * G;
+            hi[at] = h;
+            lo[at] = o;
+        }
     }
 }
 
-// B^T of every offset slot, real-ified: for complex T[n][k] (stored [k][n]),
-// Bt[2n][2k] = Re T, Bt[2n][2k+1] = -Im T, Bt[2n+1][2k] = Im T, Bt[2n+1][2k+1] = Re T.
-__global__ void m2l_tc_tables_kernel(const double* __restrict__ m2l64, int P,
-                                     float* __restrict__ bhi, float* __restrict__ blo) {
-    const int n2 = 2 * P;
-    const int64_t total = (int64_t)kOffsetSlots * n2 * n2;
+// Operator image: stage s = (source child sp, K chunk kc, parent offset d)
+// in the order the kernel consumes them, s = (sp KC + kc) 8 + d.  A stage is
+// 16 N floats: the hi part then the lo part, each two k-groups of N rows x 4
+// reals (row = target child tp x 2Pk + real output index n', column the real
+// input index k' = 8 kc + 4 group + j).  Entry: the real-ified scaled M2L
+// matrix of child offset 2D + sp - tp (source minus target), zero for
+// adjacent children and for n or k >= p; for complex T[n][k] (stored
+// [k][n]), Bt[2n][2k] = Re T, Bt[2n][2k+1] = -Im T, Bt[2n+1][2k] = Im T,
+// Bt[2n+1][2k+1] = Re T.
+__global__ void m2l_tc_bimg_kernel(const double* __restrict__ m2l64, int P, int p, int Pk,
+                                   float* __restrict__ bimg) {
+    const int N = 8 * Pk, KC = Pk / 4;
+    const int64_t per_stage = (int64_t)N * 8;
+    const int64_t total = (int64_t)4 * KC * 8 * per_stage;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        int slot = (int)(e / (n2 * n2));
-        int row = (int)((e / n2) % n2);  // n'
-        int col = (int)(e % n2);         // k'
-        int n = row >> 1, k = col >> 1;
-        const double* t = m2l64 + (((int64_t)slot * P + k) * P + n) * 2;
-        double re = t[0], im = t[1];
-        double v = (row & 1) == 0 ? ((col & 1) == 0 ? re : -im) : ((col & 1) == 0 ? im : re);
-        float h = tf32_rna((float)v);
-        bhi[e] = h;
-        blo[e] = tf32_rna((float)(v - (double)h));
+        const int stage = (int)(e / per_stage);
+        const int rem = (int)(e % per_stage);
+        const int row = rem / 8, kk = rem % 8;
+        const int h = stage / 8, d = stage % 8;
+        const int sp = h / KC, kc = h % KC;
+        const int tp = row / (2 * Pk), np = row % (2 * Pk);
+        const int kp = kc * 8 + kk;
+        int Dx, Dy;
+        parent_offset(d, &Dx, &Dy);
+        const int ox = 2 * Dx + (sp & 1) - (tp & 1), oy = 2 * Dy + (sp >> 1) - (tp >> 1);
+        double v = 0.0;
+        const int n = np >> 1, k = kp >> 1;
+        if ((ox < -1 || ox > 1 || oy < -1 || oy > 1) && n < p && k < p) {
+            const double* t = m2l64 + (((int64_t)offset_slot(ox, oy) * P + k) * P + n) * 2;
+            const double re = t[0], im = t[1];
+            v = (np & 1) == 0 ? ((kp & 1) == 0 ? re : -im) : ((kp & 1) == 0 ? im : re);
+        }
+        const float hv = tf32_rna((float)v);
+        const float lv = tf32_rna((float)(v - (double)hv));
+        const int grp = kk / 4, j = kk % 4;
+        float* st = bimg + (int64_t)stage * 16 * N;
+        st[grp * 4 * N + row * 4 + j] = hv;
+        st[8 * N + grp * 4 * N + row * 4 + j] = lv;
     }
 }
 
-template <int KC, int ST>
-__global__ void __launch_bounds__(128, 1)
-m2l_tc_kernel(const __grid_constant__ M2LTcMaps maps, const int4* __restrict__ tiles, Geometry g,
-              float* __restrict__ le, int* status) {
-    using S = TcShape<KC, ST>;
+template <int PK4>
+__global__ void __launch_bounds__(kThreads, 1)
+m2l_parent_tc_kernel(const __grid_constant__ M2LTcMaps maps, const M2LTcArgs a) {
+    constexpr int Pk = 4 * PK4;
+    constexpr int N = 8 * Pk;          // MMA columns: 4 children x 2Pk reals
+    constexpr int HALF = N / 2;        // columns per epilogue thread
+    constexpr int KG = Pk / 2;         // k-groups of 4 reals per child
+    constexpr int KC = Pk / 4;         // K chunks of 8 reals (one MMA) per child
+    constexpr int kSteps = 4 * KC;     // halo steps: (source child, K chunk)
+    constexpr int NB = 3 * N <= 512 ? 2 : 1;  // main accumulators
+    constexpr uint32_t kTmemCols = tmem_cols((NB + 1) * N);
+    constexpr int kChains = (kSteps + kChainSteps - 1) / kChainSteps;
+    constexpr int kGD = offsets_per_stage(N);   // parent offsets per operator stage
+    constexpr int kSPH = 8 / kGD;              // operator stages per halo step
+    constexpr uint32_t kBOff = 64u * N;        // one offset: hi and lo, 2 k-groups x N x 16 B
+    constexpr uint32_t kBStage = kGD * kBOff;
+    constexpr uint32_t idesc = idesc_tf32(N);
+
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full[S::kStages], empty[S::kStages], done;
+    __shared__ __align__(8) uint64_t halo_full[kHaloSlots], halo_empty[kHaloSlots];
+    __shared__ __align__(8) uint64_t b_full[kMaxBStages], b_empty[kMaxBStages];
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], done;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t s_halo = smem_u32(smem);
+    const uint32_t s_b = s_halo + 2u * kHaloSlots * (uint32_t)a.halo_bytes;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int4 tile = tiles[blockIdx.x];
-    const int level = tile.x, plane = tile.y, X0 = tile.z, Y0 = tile.w;
-    const int px = plane & 1, py = plane >> 1;
-    const int Wh = 1 << (level - 1);
-    const int bw = Wh < 128 ? Wh : 128;
-    const int bh = (128 / bw) < Wh ? (128 / bw) : Wh;
-    const uint32_t a_box_bytes = 128u * (uint32_t)(bw * bh);
-    const uint32_t stage_tx = 2u * KC * (a_box_bytes + (uint32_t)S::kBBytes);
+    const int4 tile = a.tiles[blockIdx.x];
+    const int level = tile.x, X0 = tile.y, Y0 = tile.z;
+    const int tw = tile.w & 0xFF, th = (tile.w >> 8) & 0xFF;
+    const int Hw = tw + 2, Hh = th + 2;
+    const int G = 1 << (level - 1);
+    const uint32_t box_bytes = 32u * (uint32_t)(Hw * Hh);  // 2 k-groups x Hw x Hh x 16 B
+    const uint32_t kstride_a = 16u * (uint32_t)(Hw * Hh);
 
     if (tid == 0) {
-        for (int s = 0; s < S::kStages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+        for (int s = 0; s < kHaloSlots; ++s) {
+            mbar_init(&halo_full[s], 1);
+            mbar_init(&halo_empty[s], 1);
+        }
+        for (int s = 0; s < a.b_stages; ++s) {
+            mbar_init(&b_full[s], 1);
+            mbar_init(&b_empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&acc_full[s], 1);
+            mbar_init(&acc_empty[s], kEpiThreads);
         }
         mbar_init(&done, 1);
         abort_flag = 0;
@@ -212,7 +338,7 @@ m2l_tc_kernel(const __grid_constant__ M2LTcMaps maps, const int4* __restrict__ t
         asm volatile(
             "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                 smem_u32(&tmem_base)),
-            "r"((uint32_t)S::kTmemCols));
+            "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -220,126 +346,181 @@ m2l_tc_kernel(const __grid_constant__ M2LTcMaps maps, const int4* __restrict__ t
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
 
-    // the 27 interaction offsets of this parity: children of the parent's
-    // neighbours outside the local list (Sec. 3.3.1)
-    auto offset_of = [&](int i, int* dx, int* dy) {
-        int c = 0;
-        for (int yy = -2 - py; yy <= 3 - py; ++yy)
-            for (int xx = -2 - px; xx <= 3 - px; ++xx) {
-                if (xx >= -1 && xx <= 1 && yy >= -1 && yy <= 1) continue;
-                if (c == i) {
-                    *dx = xx;
-                    *dy = yy;
-                    return;
+    if (warp == kProducerWarp) {
+        if (lane == 0) {
+            int h_issued = 0, b_issued = 0;
+            bool ok = true;
+            for (int h = 0; h < kSteps && ok; ++h) {
+                const int sp = h / KC, kc = h % KC, hs = h % kHaloSlots;
+                if (h >= kHaloSlots &&
+                    !mbar_wait(&halo_empty[hs], ((h / kHaloSlots) - 1) & 1, a.spin, &abort_flag)) {
+                    ok = false;
+                    break;
                 }
-                ++c;
+                mbar_expect_tx(&halo_full[hs], 2 * box_bytes);
+                const uint32_t dst = s_halo + (uint32_t)(2 * hs) * (uint32_t)a.halo_bytes;
+                // the halo's columns X0 - 1 .. X0 + tw as one run of 4 Hw reals
+                // (a multiple of 4: 16-byte aligned; -4 reads the zero fill)
+                tma_load_3d(dst, &maps.me_hi[level], 4 * (X0 - 1), Y0 - 1, sp * KG + 2 * kc,
+                            &halo_full[hs]);
+                tma_load_3d(dst + (uint32_t)a.halo_bytes, &maps.me_lo[level], 4 * (X0 - 1),
+                            Y0 - 1, sp * KG + 2 * kc, &halo_full[hs]);
+                ++h_issued;
+                for (int j = 0; j < kSPH; ++j) {
+                    const int b = h * kSPH + j, bs = b % a.b_stages;
+                    if (b >= a.b_stages && !mbar_wait(&b_empty[bs], ((b / a.b_stages) - 1) & 1,
+                                                      a.spin, &abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&b_full[bs], kBStage);
+                    bulk_load(s_b + (uint32_t)bs * kBStage, a.bimg + (int64_t)b * (kBStage / 4),
+                              kBStage, &b_full[bs]);
+                    ++b_issued;
+                }
             }
-    };
-    constexpr int kOffsets = 27;
-
-    if (warp == 0 && lane == 0) {  // TMA producer
-        int issued = 0;
-        for (int i = 0; i < kOffsets; ++i) {
-            const int s = i % S::kStages;
-            if (i >= S::kStages && !mbar_wait(&empty[s], ((i / S::kStages) - 1) & 1)) {
-                atomicOr(status, kFlagTimeout);
+            if (!ok) {
+                atomicOr(a.status, kFlagTimeout);
                 abort_flag = 1;
-                break;
+                // the copies still in flight land in this CTA's shared memory:
+                // wait for the last one armed on each slot before leaving
+                for (int i = max(0, h_issued - kHaloSlots); i < h_issued; ++i)
+                    mbar_wait(&halo_full[i % kHaloSlots], (i / kHaloSlots) & 1, kSpinDefault,
+                              nullptr);
+                for (int i = max(0, b_issued - a.b_stages); i < b_issued; ++i)
+                    mbar_wait(&b_full[i % a.b_stages], (i / a.b_stages) & 1, kSpinDefault,
+                              nullptr);
             }
-            int dx, dy;
-            offset_of(i, &dx, &dy);
-            const int sxp = (px + dx) & 1, syp = (py + dy) & 1;
-            const int ox = (px + dx - sxp) / 2, oy = (py + dy - syp) / 2;  // exact halving
-            const int splane = syp * 2 + sxp;
-            const int slot = offset_slot(dx, dy);
-            uint8_t* st = smem + s * S::kStageBytes;
-            mbar_expect_tx(&full[s], stage_tx);
-            for (int kc = 0; kc < KC; ++kc) {
-                tma_load_4d(st + kc * S::kABytes, &maps.me_hi[level], kc * 32, X0 + ox, Y0 + oy,
-                            splane, &full[s]);
-                tma_load_4d(st + (KC + kc) * S::kABytes, &maps.me_lo[level], kc * 32, X0 + ox,
-                            Y0 + oy, splane, &full[s]);
-                uint8_t* sb = st + 2 * KC * S::kABytes;
-                tma_load_3d(sb + kc * S::kBBytes, &maps.b_hi, kc * 32, 0, slot, &full[s]);
-                tma_load_3d(sb + (KC + kc) * S::kBBytes, &maps.b_lo, kc * 32, 0, slot, &full[s]);
-            }
-            ++issued;
         }
-        // on abort, wait (bounded) for the copies still in flight: the last
-        // load armed on each stage
-        if (abort_flag)
-            for (int i = (issued > S::kStages ? issued - S::kStages : 0); i < issued; ++i)
-                mbar_wait(&full[i % S::kStages], (i / S::kStages) & 1);
-    } else if (warp == 1 && lane == 0) {  // MMA issuer
-        constexpr uint32_t idesc = idesc_tf32(S::kN);
-        bool ok = true;
-        for (int i = 0; i < kOffsets && ok; ++i) {
-            const int s = i % S::kStages;
-            if (!mbar_wait(&full[s], (i / S::kStages) & 1)) {
-                atomicOr(status, kFlagTimeout);
+    } else if (warp == kMmaWarp) {
+        if (lane == 0) {
+            // halo row of the source parent at each offset, in 16-byte units
+            uint32_t shift16[8];
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                int dx, dy;
+                parent_offset(d, &dx, &dy);
+                shift16[d] = (uint32_t)((Hw + 1) + dy * Hw + dx);
+            }
+            bool ok = true;
+            for (int h = 0; h < kSteps && ok; ++h) {
+                const int hs = h % kHaloSlots;
+                const int c = h / kChainSteps, cpos = h % kChainSteps, buf = c % NB;
+                if (cpos == 0 && c >= NB &&
+                    !mbar_wait(&acc_empty[buf], ((c / NB) - 1) & 1, a.spin, &abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                if (!mbar_wait(&halo_full[hs], (h / kHaloSlots) & 1, a.spin, &abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t hbase = s_halo + (uint32_t)(2 * hs) * (uint32_t)a.halo_bytes;
+                const uint64_t ah0 = sdesc(hbase, kstride_a);
+                const uint64_t al0 = sdesc(hbase + (uint32_t)a.halo_bytes, kstride_a);
+                const uint32_t acc_main = tmem + (uint32_t)(buf * N);
+                const uint32_t acc_corr = tmem + (uint32_t)(NB * N);
+                for (int j = 0; j < kSPH; ++j) {
+                    const int b = h * kSPH + j, bs = b % a.b_stages;
+                    if (!mbar_wait(&b_full[bs], (b / a.b_stages) & 1, a.spin, &abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint64_t b0 = sdesc(s_b + (uint32_t)bs * kBStage, 16u * N);
+#pragma unroll
+                    for (int e = 0; e < kGD; ++e) {
+                        const int d = j * kGD + e;
+                        // the offset's rows of the halo: a start address moved by
+                        // whole 16-byte rows (descriptor address field in 16 B)
+                        const uint64_t ah = ah0 + (uint64_t)shift16[d];
+                        const uint64_t al = al0 + (uint64_t)shift16[d];
+                        const uint64_t bh = b0 + (uint64_t)(e * (kBOff >> 4));
+                        const uint64_t bl = bh + (uint64_t)((32u * N) >> 4);
+                        mma_tf32(acc_main, ah, bh, idesc, !(cpos == 0 && d == 0));
+                        mma_tf32(acc_corr, ah, bl, idesc, !(h == 0 && d == 0));
+                        mma_tf32(acc_corr, al, bh, idesc, 1u);
+                    }
+                    mma_commit(&b_empty[bs]);  // frees the slot once these MMAs have read it
+                }
+                if (!ok) break;
+                mma_commit(&halo_empty[hs]);
+                if (cpos == kChainSteps - 1 || h == kSteps - 1) mma_commit(&acc_full[buf]);
+            }
+            if (!ok) {
+                atomicOr(a.status, kFlagTimeout);
                 abort_flag = 1;
+            }
+            mma_commit(&done);  // every MMA issued above, on every path
+        }
+    } else {  // epilogue warps 0..7
+        const int q = warp & 3, hh = warp >> 2;
+        const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hh * HALF);
+        float sum[HALF];
+#pragma unroll
+        for (int j = 0; j < HALF; ++j) sum[j] = 0.f;
+        bool ok = true;
+        for (int c = 0; c < kChains; ++c) {
+            const int buf = c % NB;
+            const bool w = mbar_wait(&acc_full[buf], (c / NB) & 1, a.spin, &abort_flag);
+            if (!__all_sync(0xffffffffu, w)) {
                 ok = false;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t st = smem_u32(smem + s * S::kStageBytes);
-            for (int kc = 0; kc < KC; ++kc) {
-                const uint32_t a_hi = st + kc * S::kABytes, a_lo = st + (KC + kc) * S::kABytes;
-                const uint32_t b0 = st + 2 * KC * S::kABytes;
-                const uint32_t b_hi = b0 + kc * S::kBBytes, b_lo = b0 + (KC + kc) * S::kBBytes;
-                const uint32_t acc_main = tmem + (uint32_t)((i % kMainAccs) * S::kN);
-                const uint32_t acc_corr = tmem + (uint32_t)(kMainAccs * S::kN);
 #pragma unroll
-                for (int k8 = 0; k8 < 4; ++k8) {
-                    const uint32_t off = k8 * 32;  // 8 tf32 = 32 bytes along K
-                    const uint64_t dah = sdesc_sw128(a_hi + off), dal = sdesc_sw128(a_lo + off);
-                    const uint64_t dbh = sdesc_sw128(b_hi + off), dbl = sdesc_sw128(b_lo + off);
-                    const bool first = kc == 0 && k8 == 0;  // first product of the accumulator
-                    mma_tf32(acc_main, dah, dbh, idesc, !(first && i < kMainAccs));
-                    mma_tf32(acc_corr, dah, dbl, idesc, !(first && i == 0));
-                    mma_tf32(acc_corr, dal, dbh, idesc, 1);
+            for (int j = 0; j < HALF; j += 16) {
+                uint32_t r[16];
+                tmem_ld16(tbase + (uint32_t)(buf * N + j), r);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) sum[j + i] += __uint_as_float(r[i]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            mbar_arrive(&acc_empty[buf]);
+        }
+        if (!ok) {
+            if (lane == 0) atomicOr(a.status, kFlagTimeout);
+            abort_flag = 1;
+        }
+        // the MMAs' completion, on every path, before tensor memory is read
+        // again or freed
+        const bool dn = mbar_wait(&done, 0, kSpinDefault, nullptr);
+        const bool aborted = abort_flag != 0;
+        ok = __all_sync(0xffffffffu, ok && dn && !aborted);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (ok) {
+#pragma unroll
+            for (int j = 0; j < HALF; j += 16) {
+                uint32_t r[16];
+                tmem_ld16(tbase + (uint32_t)(NB * N + j), r);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) sum[j + i] += __uint_as_float(r[i]);
+            }
+            const int m = q * 32 + lane;  // accumulator row = tensor-memory lane
+            const int x = m % Hw, y = m / Hw;
+            const int X = X0 + x, Y = Y0 + y;
+            if (x < tw && y < th && X < G && Y < G) {
+#pragma unroll
+                for (int t2 = 0; t2 < 2; ++t2) {
+                    const int tp = 2 * hh + t2;  // target child (parity plane)
+                    float4* d4 = reinterpret_cast<float4*>(
+                        a.le + (a.level_base[level] + ((int64_t)(tp * G + Y) * G + X)) * (2 * a.P));
+#pragma unroll
+                    for (int j = 0; j < Pk / 2; ++j)
+                        d4[j] = make_float4(sum[t2 * 2 * Pk + 4 * j], sum[t2 * 2 * Pk + 4 * j + 1],
+                                            sum[t2 * 2 * Pk + 4 * j + 2],
+                                            sum[t2 * 2 * Pk + 4 * j + 3]);
+                    for (int j = Pk / 2; j < a.P / 2; ++j) d4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
-            mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
-        }
-        if (ok) mma_commit(&done);
-    }
-    __syncwarp();
-    // epilogue: thread t holds accumulator row t (TMEM lane t)
-    const bool ok = mbar_wait(&done, 0);
-    if (!ok) atomicOr(status, kFlagTimeout);
-    __syncwarp();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const int m = tid;
-    const int ix_local = m % bw, iy_local = m / bw;
-    const int IX = X0 + ix_local, IY = Y0 + iy_local;
-    const bool valid = ok && m < bw * bh && IX < Wh && IY < Wh;
-    float* dst = le + (g.level_base[level] + ((int64_t)(plane * Wh + IY) * Wh + IX)) * (2 * g.P);
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll
-    for (int c0 = 0; c0 < S::kN; c0 += 32) {
-        float sum[32];
-        uint32_t r[32];
-        tmem_ld32(lane_base + (uint32_t)(kMainAccs * S::kN + c0), r);  // corrections first
-#pragma unroll
-        for (int j = 0; j < 32; ++j) sum[j] = __uint_as_float(r[j]);
-        for (int a = 0; a < kMainAccs; ++a) {
-            tmem_ld32(lane_base + (uint32_t)(a * S::kN + c0), r);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) sum[j] += __uint_as_float(r[j]);
-        }
-        if (valid) {
-            float4* d4 = reinterpret_cast<float4*>(dst + c0);
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                d4[j] = make_float4(sum[4 * j], sum[4 * j + 1], sum[4 * j + 2], sum[4 * j + 3]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"((uint32_t)S::kTmemCols));
+                     "r"(kTmemCols));
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -360,97 +541,149 @@ EncodeTiledFn encoder() {
     return fn;
 }
 
-}  // namespace
-
-int m2l_tc_smem_bytes(int P) { return P <= 16 ? TcShape<1, 4>::kSmem : TcShape<2, 2>::kSmem; }
-
-cudaError_t m2l_tc_prepare(const Geometry& g, const double* m2l64, float* me_hi, float* me_lo,
-                           float* bhi, float* blo, M2LTcMaps* maps, int4* tiles_host,
-                           int* ntiles, cudaStream_t s) {
-    EncodeTiledFn enc = encoder();
-    if (!enc) return cudaErrorNotSupported;
-    const int n2 = 2 * g.P;
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    for (int l = 2; l <= g.L; ++l) {
-        const cuuint64_t Wh = 1ull << (l - 1);
-        const cuuint64_t dims[4] = {(cuuint64_t)n2, Wh, Wh, 4};
-        const cuuint64_t strides[3] = {(cuuint64_t)n2 * 4, (cuuint64_t)n2 * 4 * Wh,
-                                       (cuuint64_t)n2 * 4 * Wh * Wh};
-        const cuuint32_t bw = Wh < 128 ? (cuuint32_t)Wh : 128u;
-        const cuuint32_t bh = (128u / bw) < Wh ? 128u / bw : (cuuint32_t)Wh;
-        const cuuint32_t box[4] = {32, bw, bh, 1};
-        for (int which = 0; which < 2; ++which) {
-            float* base = (which ? me_lo : me_hi) + g.level_base[l] * n2;
-            CUresult r = enc(which ? &maps->me_lo[l] : &maps->me_hi[l],
-                             CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+// Tile of target parents at a level of G x G parents: the tw x th rectangle
+// (th (tw + 2) <= 128 MMA rows, tw <= 62) with the fewest tiles, then the
+// smallest halo.
+void choose_tile(int G, int* tw_out, int* th_out) {
+    long best = LONG_MAX, best_halo = LONG_MAX;
+    int btw = 1, bth = 1;
+    for (int tw = 1; tw <= G && tw <= 62; ++tw) {  // box inner extent 4 (tw + 2) <= 256
+        const int Hw = tw + 2;
+        const int th = std::min(G, 128 / Hw);
+        if (th < 1) break;
+        const long tiles = (long)((G + tw - 1) / tw) * ((G + th - 1) / th);
+        const long halo = (long)Hw * (th + 2);
+        if (tiles < best || (tiles == best && halo < best_halo)) {
+            best = tiles;
+            best_halo = halo;
+            btw = tw;
+            bth = th;
         }
     }
-    {
-        const cuuint64_t dims[3] = {(cuuint64_t)n2, (cuuint64_t)n2, (cuuint64_t)kOffsetSlots};
-        const cuuint64_t strides[2] = {(cuuint64_t)n2 * 4, (cuuint64_t)n2 * n2 * 4};
-        const cuuint32_t box[3] = {32, (cuuint32_t)n2, 1};
-        for (int which = 0; which < 2; ++which) {
-            CUresult r = enc(which ? &maps->b_lo : &maps->b_hi, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-                             which ? blo : bhi, dims, strides, box, estr,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-        }
-    }
-    int count = 0;
-    for (int l = 2; l <= g.L; ++l) {
-        const int Wh = 1 << (l - 1);
-        const int bw = Wh < 128 ? Wh : 128;
-        const int bh = (128 / bw) < Wh ? 128 / bw : Wh;
-        for (int pl = 0; pl < 4; ++pl)
-            for (int y = 0; y < Wh; y += bh)
-                for (int x = 0; x < Wh; x += bw) {
-                    if (tiles_host) tiles_host[count] = make_int4(l, pl, x, y);
-                    ++count;
-                }
-    }
-    *ntiles = count;
-    int64_t total = (int64_t)kOffsetSlots * n2 * n2;
-    int blocks = (int)((total + 255) / 256);
-    m2l_tc_tables_kernel<<<blocks, 256, 0, s>>>(m2l64, g.P, bhi, blo);
+    *tw_out = btw;
+    *th_out = bth;
+}
+
+template <int PK4>
+cudaError_t launch_pk(const M2LTcConfig& cfg, const M2LTcMaps& maps, const M2LTcArgs& a,
+                      cudaStream_t s) {
+    m2l_parent_tc_kernel<PK4><<<cfg.ntiles, kThreads, cfg.smem, s>>>(maps, a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_m2l_tc(const Geometry& g, const M2LTcMaps& maps, const int4* tiles, int ntiles,
-                          const float* me, float* me_hi, float* me_lo, float* le, int* status,
-                          cudaStream_t s) {
-    if (g.L < 2) return cudaSuccess;
-    const int64_t count = g.nboxes * 2 * g.P;
-    int blocks = (int)((count + 255) / 256);
-    if (blocks > 8192) blocks = 8192;
-    m2l_split_kernel<<<blocks, 256, 0, s>>>(me, me_hi, me_lo, count);
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g.P > 16)
-        m2l_tc_kernel<2, 2><<<ntiles, 128, TcShape<2, 2>::kSmem, s>>>(maps, tiles, g, le, status);
-    else if (ntiles <= sms)
-        m2l_tc_kernel<1, 4><<<ntiles, 128, TcShape<1, 4>::kSmem, s>>>(maps, tiles, g, le, status);
-    else
-        m2l_tc_kernel<1, 2><<<ntiles, 128, TcShape<1, 2>::kSmem, s>>>(maps, tiles, g, le, status);
-    return cudaGetLastError();
+template <int PK4>
+cudaError_t configure_pk() {
+    return cudaFuncSetAttribute(m2l_parent_tc_kernel<PK4>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+}
+
+}  // namespace
+
+M2LTcConfig m2l_tc_plan(const Geometry& g, int4* tiles_host) {
+    M2LTcConfig c{};
+    c.Pk = (g.p + 3) & ~3;
+    const int N = 8 * c.Pk;
+    int count = 0, halo_rows = 0;
+    for (int l = 2; l <= g.L; ++l) {
+        const int G = 1 << (l - 1);
+        int tw, th;
+        choose_tile(G, &tw, &th);
+        const int Hw = tw + 2, Hh = th + 2;
+        // rows one slot must hold: the TMA box (2 k-groups) and the furthest
+        // row an MMA reads (k-group 1, offset (1, 1), row 127)
+        halo_rows = std::max(halo_rows, std::max(2 * Hw * Hh, Hw * Hh + 2 * Hw + 130));
+        for (int y = 0; y < G; y += th)
+            for (int x = 0; x < G; x += tw) {
+                if (tiles_host) tiles_host[count] = make_int4(l, x, y, tw | (th << 8));
+                ++count;
+            }
+    }
+    c.ntiles = count;
+    c.halo_bytes = ((halo_rows * 16) + 127) & ~127;
+    const int stage = 64 * N * offsets_per_stage(N);
+    const int budget = kSmemLimit - 1024 - 2 * kHaloSlots * c.halo_bytes;
+    c.b_stages = std::min(kMaxBStages, budget / stage);
+    c.smem = 2 * kHaloSlots * c.halo_bytes + c.b_stages * stage + 1024;
+    c.b_floats = (int64_t)4 * (c.Pk / 4) * 8 * 16 * N;
+    return c;
 }
 
 cudaError_t m2l_tc_configure() {
-    cudaError_t e = cudaFuncSetAttribute(m2l_tc_kernel<1, 4>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TcShape<1, 4>::kSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(m2l_tc_kernel<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 TcShape<1, 2>::kSmem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(m2l_tc_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                TcShape<2, 2>::kSmem);
+    cudaError_t e = configure_pk<1>();
+    if (e == cudaSuccess) e = configure_pk<2>();
+    if (e == cudaSuccess) e = configure_pk<3>();
+    if (e == cudaSuccess) e = configure_pk<4>();
+    if (e == cudaSuccess) e = configure_pk<5>();
+    if (e == cudaSuccess) e = configure_pk<6>();
+    if (e == cudaSuccess) e = configure_pk<7>();
+    if (e == cudaSuccess) e = configure_pk<8>();
+    return e;
+}
+
+cudaError_t m2l_tc_prepare(const Geometry& g, const M2LTcConfig& cfg, const double* m2l64,
+                           float* me_hi, float* me_lo, float* bimg, M2LTcMaps* maps,
+                           cudaStream_t s) {
+    EncodeTiledFn enc = encoder();
+    if (!enc) return cudaErrorNotSupported;
+    if (cfg.b_stages < 2 || cfg.b_stages > kMaxBStages || cfg.Pk < 4 || cfg.Pk > kMaxP)
+        return cudaErrorInvalidValue;
+    const int KG = cfg.Pk / 2;
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int l = 2; l <= g.L; ++l) {
+        const cuuint64_t G = 1ull << (l - 1);
+        int tw, th;
+        choose_tile((int)G, &tw, &th);
+        // a row of the level's plane (G columns x 4 reals) is one contiguous
+        // run: the box's inner extent is the halo's 4 Hw reals (16 Hw bytes),
+        // landing as [k-group][row][column][4 reals] like the 4-D view would
+        const cuuint64_t dims[3] = {4 * G, G, (cuuint64_t)4 * KG};
+        const cuuint64_t strides[2] = {16 * G, 16 * G * G};
+        const cuuint32_t box[3] = {(cuuint32_t)(4 * (tw + 2)), (cuuint32_t)(th + 2), 2};
+        for (int which = 0; which < 2; ++which) {
+            float* base = (which ? me_lo : me_hi) + g.level_base[l] * 2 * cfg.Pk;
+            CUresult r = enc(which ? &maps->me_lo[l] : &maps->me_hi[l],
+                             CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        }
+    }
+    const int64_t total = cfg.b_floats / 2;  // one thread per (stage, row, k) entry
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8192);
+    m2l_tc_bimg_kernel<<<blocks, 256, 0, s>>>(m2l64, g.P, g.p, cfg.Pk, bimg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m2l_tc(const Geometry& g, const M2LTcConfig& cfg, const M2LTcMaps& maps,
+                          const int4* tiles, const float* me, float* me_hi, float* me_lo,
+                          const float* bimg, float* le, int* status, uint32_t spin,
+                          cudaStream_t s) {
+    if (g.L < 2) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>((g.nboxes + 255) / 256, 4096);
+    m2l_tc_split_kernel<<<blocks, 256, 0, s>>>(me, reinterpret_cast<float4*>(me_hi),
+                                               reinterpret_cast<float4*>(me_lo), g, cfg.Pk);
+    M2LTcArgs a{};
+    a.tiles = tiles;
+    a.bimg = bimg;
+    a.le = le;
+    a.status = status;
+    for (int l = 0; l <= kMaxL + 1; ++l) a.level_base[l] = g.level_base[l];
+    a.P = g.P;
+    a.halo_bytes = cfg.halo_bytes;
+    a.b_stages = cfg.b_stages;
+    a.spin = spin ? spin : kSpinDefault;
+    switch (cfg.Pk / 4) {
+        case 1: return launch_pk<1>(cfg, maps, a, s);
+        case 2: return launch_pk<2>(cfg, maps, a, s);
+        case 3: return launch_pk<3>(cfg, maps, a, s);
+        case 4: return launch_pk<4>(cfg, maps, a, s);
+        case 5: return launch_pk<5>(cfg, maps, a, s);
+        case 6: return launch_pk<6>(cfg, maps, a, s);
+        case 7: return launch_pk<7>(cfg, maps, a, s);
+        case 8: return launch_pk<8>(cfg, maps, a, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace fmm2d
