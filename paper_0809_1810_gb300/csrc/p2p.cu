@@ -230,6 +230,7 @@ constexpr uint32_t kTicket = 128;  // largest sorted-target window (a power of t
 #define FMM2D_P2P_LIST_CAP 560  // 37 KB of shared memory per CTA: 6 CTAs per SM
 #endif
 constexpr int kListCap = FMM2D_P2P_LIST_CAP;  // source records per warp buffer
+static_assert(kListCap % 2 == 0, "the source lists hold whole pairs");
 constexpr int kF32Deg = 3;
 constexpr double kPolyEdge = 0.15;  // q2 below which the polynomial is used
 
@@ -248,75 +249,134 @@ struct NearF32v3 {
     float coef[kF32Deg + 1];  // g(q2) ~ sum_k coef[k] q2^k on [0, qthr)
 };
 
-// Gamma_j g(q2) with the circulation folded into the subtraction:
-// Gamma (1 - e) / q2 = fma(-Gamma, e, Gamma) rcp(q2), e = 2^-q2 (one
-// instruction fewer than forming 1 - e first, and one rounding fewer).
-__device__ __forceinline__ float wg_far(float gamma, float q2) {
-    return fmaf(-gamma, ex2_approx(-q2), gamma) * rcp_approx(q2);
+// Packed FP32 pairs (f32x2): one instruction applies the same operation to
+// the two halves of a register pair, so the pair arithmetic of two sources
+// against one target takes one issue slot per step instead of two.
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+    float2 r;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
 }
-__device__ __forceinline__ float wg_near(const NearF32v3& nm, float gamma, float q2) {
-    float poly = nm.coef[kF32Deg];
-#pragma unroll
-    for (int k = kF32Deg - 1; k >= 0; --k) poly = fmaf(poly, q2, nm.coef[k]);
-    const float far = wg_far(gamma, q2);
-    return q2 < nm.qthr ? gamma * poly : far;
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+    float2 r;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " mul.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
 }
+// a * b + c, rounded once per half
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+    float2 r;
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
+}
+__device__ __forceinline__ float2 f2_dup(float v) { return make_float2(v, v); }
 
-// Cutoff correction of a ring pair (Sec. 4.1): the far field applied the
-// singular kernel; closer than a, -Gamma 2^-q2 / q2 restores K_sigma.
-__device__ __forceinline__ float wg_cut(const NearF32v3& nm, float gamma, float q2) {
-    const float w = (-gamma * ex2_approx(-q2)) * rcp_approx(q2);
-    return q2 < nm.qa ? w : 0.f;
+// Source lists hold sources in pairs: pair k occupies buf[2k] = (x_a, x_b,
+// y_a, y_b) and buf[2k + 1] = (Gamma_a, Gamma_b, -Gamma_a, -Gamma_b), in
+// scaled leaf-relative coordinates; source j is half j & 1 of pair j >> 1.
+// A band of odd length is completed by a dummy source of zero circulation
+// far from every target (q2 ~ 1e36: its weight is exactly zero).
+constexpr float kFarAway = 1e18f;
+__device__ __forceinline__ void put_source(float4* buf, uint32_t j, float x, float y, float g) {
+    float* p0 = reinterpret_cast<float*>(buf + 2 * (j >> 1));
+    const uint32_t h = j & 1u;
+    p0[h] = x;
+    p0[2 + h] = y;
+    p0[4 + h] = g;
+    p0[6 + h] = -g;
+}
+__device__ __forceinline__ void put_dummy(float4* buf, uint32_t j) {
+    put_source(buf, j, kFarAway, kFarAway, 0.f);
 }
 
 // Pair modes of the band loops: far band, near band (polynomial below the
 // edge), ring pairs under the cutoff.
 constexpr int kFar = 0, kNearBand = 1, kRing = 2;
 
+// Two sources (a pair of the list) against one target at (tx, tx), (ty, ty):
+// the velocity sums of the two halves, iu = sum Gamma g(q2) (-dy) and
+// iv = sum Gamma g(q2) dx with dx = x_t - x_s, dy = y_t - y_s.
+// Radial weight Gamma g(q2) = fma(-Gamma, e, Gamma) rcp(q2), e = 2^-q2
+// (Gamma (1 - e)/q2 with the circulation folded into the subtraction: one
+// instruction fewer than forming 1 - e first, and one rounding fewer).  Near
+// band: below qthr the cubic in q2 times Gamma instead.  Ring: the cutoff
+// correction of Sec. 4.1 -- the far field applied the singular kernel, and
+// closer than a, -Gamma 2^-q2 / q2 restores K_sigma; zero beyond a.
 template <int kMode>
-__device__ __forceinline__ void one_source(const NearF32v3& nm, const float4 s, float x, float y,
-                                           float& iu, float& iv) {
-    const float dx = x - s.x, dy = y - s.y;
-    const float q2 = fmaf(dx, dx, dy * dy);
-    const float w = kMode == kNearBand ? wg_near(nm, s.z, q2)
-                    : kMode == kRing   ? wg_cut(nm, s.z, q2)
-                                       : wg_far(s.z, q2);
-    iu = fmaf(-dy, w, iu);
-    iv = fmaf(dx, w, iv);
+__device__ __forceinline__ void pair_sources(const NearF32v3& nm, const float4 P0, const float4 P1,
+                                             float2 tx, float2 ty, float2& iu, float2& iv) {
+    const float2 dx = f2_sub(tx, make_float2(P0.x, P0.y));
+    const float2 ndy = f2_sub(make_float2(P0.z, P0.w), ty);  // -dy
+    const float2 q = f2_fma(ndy, ndy, f2_mul(dx, dx));
+    const float2 e = make_float2(ex2_approx(-q.x), ex2_approx(-q.y));
+    const float2 r = make_float2(rcp_approx(q.x), rcp_approx(q.y));
+    float2 w;
+    if (kMode == kRing) {
+        w = f2_mul(f2_mul(make_float2(P1.z, P1.w), e), r);
+        w.x = q.x < nm.qa ? w.x : 0.f;
+        w.y = q.y < nm.qa ? w.y : 0.f;
+    } else {
+        const float2 g = make_float2(P1.x, P1.y);
+        w = f2_mul(f2_fma(make_float2(P1.z, P1.w), e, g), r);
+        if (kMode == kNearBand) {
+            float2 poly = f2_dup(nm.coef[kF32Deg]);
+#pragma unroll
+            for (int k = kF32Deg - 1; k >= 0; --k) poly = f2_fma(poly, q, f2_dup(nm.coef[k]));
+            const float2 wn = f2_mul(g, poly);
+            w.x = q.x < nm.qthr ? wn.x : w.x;
+            w.y = q.y < nm.qthr ? wn.y : w.y;
+        }
+    }
+    iu = f2_fma(ndy, w, iu);
+    iv = f2_fma(dx, w, iv);
 }
 
-// list[lo, hi) against the lane's target when ns > 1 lanes share a target
-// (sl = this lane's slot; a leaf's last round of at most 16 targets): blocks
-// of kInner sources into fresh sums, then compensated.
+// Pairs [lo, hi) of the list against the lane's target when ns > 1 lanes
+// share a target (sl = this lane's slot; a leaf's last round of at most 16
+// targets): blocks of kInner pairs into fresh sums, then compensated.
 template <int kMode>
 __device__ __forceinline__ void band_loop_split(const float4* list, uint32_t lo, uint32_t hi,
                                                 int ns, int sl, const NearF32v3& nm, float x,
                                                 float y, float& su, float& sv, float& cu,
                                                 float& cv) {
-    float iu = 0.f, iv = 0.f;
+    const float2 tx = f2_dup(x), ty = f2_dup(y);
+    float2 iu = make_float2(0.f, 0.f), iv = make_float2(0.f, 0.f);
     int cnt = 0;
 #pragma unroll 1
-    for (uint32_t jj = lo; jj < hi; jj += ns) {
-        const uint32_t j = jj + sl;
-        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);  // past the end: zero circulation
-        if (j < hi) r = list[j];
-        one_source<kMode>(nm, r, x, y, iu, iv);
-        if (++cnt == kInner) {
-            neumaier_add(su, cu, iu);
-            neumaier_add(sv, cv, iv);
-            iu = iv = 0.f;
+    for (uint32_t kk = lo; kk < hi; kk += ns) {
+        const uint32_t k = kk + sl;
+        // past the end: a pair of dummies (zero circulation, far away)
+        float4 P0 = make_float4(kFarAway, kFarAway, kFarAway, kFarAway);
+        float4 P1 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < hi) {
+            P0 = list[2 * k];
+            P1 = list[2 * k + 1];
+        }
+        pair_sources<kMode>(nm, P0, P1, tx, ty, iu, iv);
+        if (++cnt == kInner / 2) {
+            neumaier_add(su, cu, iu.x + iu.y);
+            neumaier_add(sv, cv, iv.x + iv.y);
+            iu = iv = make_float2(0.f, 0.f);
             cnt = 0;
         }
     }
-    neumaier_add(su, cu, iu);
-    neumaier_add(sv, cv, iv);
+    neumaier_add(su, cu, iu.x + iu.y);
+    neumaier_add(sv, cv, iv.x + iv.y);
 }
 
-// list[lo, hi) against T targets per lane (passes of 32 T targets):
-// blocks of kInnerT sources into fresh sums, then compensated.  One
-// shared-memory read of a source serves T pairs.  Each target sees the same
-// sequence of operations whatever T is, so a target's velocity does not
-// depend on how its rounds were grouped into passes.
+// Pairs [lo, hi) of the list against T targets per lane (passes of 32 T
+// targets): blocks of kInnerT / 2 pairs into fresh sums, then compensated.
+// One shared-memory read of a pair serves 2 T source-target pairs.  Each
+// target sees the same sequence of operations whatever T is, so a target's
+// velocity does not depend on how its rounds were grouped into passes.
 constexpr int kInnerT = 32;
 
 template <int T>
@@ -328,37 +388,51 @@ template <int kMode, int T>
 __device__ __forceinline__ void band_loopT(const float4* list, uint32_t lo, uint32_t hi,
                                            const NearF32v3& nm, const float (&x)[T],
                                            const float (&y)[T], SumT<T>& S) {
-    // sources per iteration (measured: eight pairs in flight at two targets
-    // per lane, four at one and at four; longer bodies cost more in
-    // instruction fetch than they save in loop overhead)
-    constexpr int kUnroll = T >= 4 ? 1 : 4;
-    uint32_t j = lo;
-    while (j < hi) {
-        const uint32_t e = min(j + (uint32_t)kInnerT, hi);
-        float iu[T], iv[T];
+    // pairs per iteration (two at one and two targets per lane, one at four)
+    constexpr int kUnroll = T >= 4 ? 1 : 2;
+    float2 tx[T], ty[T];
 #pragma unroll
-        for (int t = 0; t < T; ++t) iu[t] = iv[t] = 0.f;
+    for (int t = 0; t < T; ++t) {
+        tx[t] = f2_dup(x[t]);
+        ty[t] = f2_dup(y[t]);
+    }
+    uint32_t k = lo;
+    while (k < hi) {
+        const uint32_t e = min(k + (uint32_t)(kInnerT / 2), hi);
+        float2 iu[T], iv[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) iu[t] = iv[t] = make_float2(0.f, 0.f);
 #pragma unroll 1
-        for (; j + kUnroll <= e; j += kUnroll) {
+        for (; k + kUnroll <= e; k += kUnroll) {
 #pragma unroll
             for (int q = 0; q < kUnroll; ++q) {
-                const float4 src = list[j + q];
+                const float4 P0 = list[2 * (k + q)], P1 = list[2 * (k + q) + 1];
 #pragma unroll
-                for (int t = 0; t < T; ++t) one_source<kMode>(nm, src, x[t], y[t], iu[t], iv[t]);
+                for (int t = 0; t < T; ++t)
+                    pair_sources<kMode>(nm, P0, P1, tx[t], ty[t], iu[t], iv[t]);
             }
         }
-        for (; j < e; ++j) {
-            const float4 src = list[j];
+        for (; k < e; ++k) {
+            const float4 P0 = list[2 * k], P1 = list[2 * k + 1];
 #pragma unroll
-            for (int t = 0; t < T; ++t) one_source<kMode>(nm, src, x[t], y[t], iu[t], iv[t]);
+            for (int t = 0; t < T; ++t) pair_sources<kMode>(nm, P0, P1, tx[t], ty[t], iu[t], iv[t]);
         }
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            neumaier_add(S.su[t], S.cu[t], iu[t]);
-            neumaier_add(S.sv[t], S.cv[t], iv[t]);
+            neumaier_add(S.su[t], S.cu[t], iu[t].x + iu[t].y);
+            neumaier_add(S.sv[t], S.cv[t], iv[t].x + iv[t].y);
         }
     }
 }
+
+// Band boundaries in pairs: the near band [0, near_pairs(nn)) and the far band
+// [far_first(nf), kListCap / 2) of a buffer holding nn near and nf far sources.
+__device__ __forceinline__ uint32_t near_pairs(uint32_t nn) { return (nn + 1) >> 1; }
+__device__ __forceinline__ uint32_t far_first(uint32_t nf) {
+    return ((uint32_t)kListCap - nf - (nf & 1u)) >> 1;
+}
+// Sources gathered into a buffer at a time: room for a dummy in each band.
+constexpr uint32_t kListChunk = kListCap - 2;
 
 struct LeafCtx {
     uint32_t t0, nt;           // the leaf's targets in sorted order
@@ -455,9 +529,11 @@ __device__ __forceinline__ void l2p_add(int p, float kzeta, float inv_s, const f
     v = fmaf(-inv_s, w.y, v);
 }
 
-// Gather local-list records [cb, cb + cnt) into the warp's buffer in scaled
-// leaf-relative coordinates: near band at the front (nn records), far band
-// at the back (nf records).
+// Gather local-list records [cb, cb + cnt) (cnt <= kListChunk) into the
+// warp's buffer in scaled leaf-relative coordinates: nn near-band sources
+// from the front (sources 0, 1, ...), nf far-band sources from the back
+// (sources kListCap - 1, kListCap - 2, ...), each band completed to whole
+// pairs by a dummy.
 __device__ __forceinline__ void gather_bands(const float4* __restrict__ sp, const LeafCtx& c,
                                              const NearF32v3& nm, uint32_t cb, uint32_t cnt,
                                              float4* buf, uint32_t& nn, uint32_t& nf) {
@@ -473,30 +549,36 @@ __device__ __forceinline__ void gather_bands(const float4* __restrict__ sp, cons
         const uint32_t base = c.rbeg[r] - c.rpre[r];
         for (uint32_t g0 = lo; g0 < hi; g0 += 32) {
             const uint32_t gv = g0 + lane;
-            float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+            float rx = 0.f, ry = 0.f, rg = 0.f;
             bool ok = gv < hi, near = false;
             if (ok) {
                 float4 q = sp[base + gv];
-                rec = make_float4(((q.x - c.cxh) - c.cxl) * nm.sc, ((q.y - c.cyh) - c.cyl) * nm.sc,
-                                  q.z, 0.f);
-                float ex = fmaxf(fabsf(rec.x) - nm.half_leaf, 0.f);
-                float ey = fmaxf(fabsf(rec.y) - nm.half_leaf, 0.f);
+                rx = ((q.x - c.cxh) - c.cxl) * nm.sc;
+                ry = ((q.y - c.cyh) - c.cyl) * nm.sc;
+                rg = q.z;
+                float ex = fmaxf(fabsf(rx) - nm.half_leaf, 0.f);
+                float ey = fmaxf(fabsf(ry) - nm.half_leaf, 0.f);
                 near = fmaf(ex, ex, ey * ey) < nm.band2;
             }
             const unsigned bn = __ballot_sync(0xffffffffu, near);
             const unsigned bf = __ballot_sync(0xffffffffu, ok && !near);
-            if (near) buf[nn + __popc(bn & lt)] = rec;
-            else if (ok) buf[kListCap - 1 - (nf + __popc(bf & lt))] = rec;
+            if (near) put_source(buf, nn + __popc(bn & lt), rx, ry, rg);
+            else if (ok) put_source(buf, kListCap - 1 - (nf + __popc(bf & lt)), rx, ry, rg);
             nn += __popc(bn);
             nf += __popc(bf);
         }
     }
+    if (lane == 0) {
+        if (nn & 1u) put_dummy(buf, nn);
+        if (nf & 1u) put_dummy(buf, kListCap - 1 - nf);
+    }
     __syncwarp();
 }
 
-// Gather the ring sources [cb, cb + cnt) that lie within the cutoff of the
-// leaf square (only those can be closer than a to a target) into buf[0, nc),
-// in scaled leaf-relative coordinates.
+// Gather the ring sources [cb, cb + cnt) (cnt <= kListChunk) that lie within
+// the cutoff of the leaf square (only those can be closer than a to a
+// target) into sources [0, nc) of buf, in scaled leaf-relative coordinates,
+// completed to whole pairs by a dummy.
 __device__ __forceinline__ void gather_ring(const float4* __restrict__ sp, const LeafCtx& c,
                                             const NearF32v3& nm, uint32_t cb, uint32_t cnt,
                                             float4* buf, uint32_t& nc) {
@@ -510,21 +592,23 @@ __device__ __forceinline__ void gather_ring(const float4* __restrict__ sp, const
         const uint32_t base = c.cbeg[r] - c.cpre[r];
         for (uint32_t g0 = lo; g0 < hi; g0 += 32) {
             const uint32_t gv = g0 + lane;
-            float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+            float rx = 0.f, ry = 0.f, rg = 0.f;
             bool keep = false;
             if (gv < hi) {
                 float4 q = sp[base + gv];
-                rec = make_float4(((q.x - c.cxh) - c.cxl) * nm.sc,
-                                  ((q.y - c.cyh) - c.cyl) * nm.sc, q.z, 0.f);
-                float ex = fmaxf(fabsf(rec.x) - nm.half_leaf, 0.f);
-                float ey = fmaxf(fabsf(rec.y) - nm.half_leaf, 0.f);
+                rx = ((q.x - c.cxh) - c.cxl) * nm.sc;
+                ry = ((q.y - c.cyh) - c.cyl) * nm.sc;
+                rg = q.z;
+                float ex = fmaxf(fabsf(rx) - nm.half_leaf, 0.f);
+                float ey = fmaxf(fabsf(ry) - nm.half_leaf, 0.f);
                 keep = fmaf(ex, ex, ey * ey) < nm.band_a2;
             }
             const unsigned bk = __ballot_sync(0xffffffffu, keep);
-            if (keep) buf[nc + __popc(bk & lt)] = rec;
+            if (keep) put_source(buf, nc + __popc(bk & lt), rx, ry, rg);
             nc += __popc(bk);
         }
     }
+    if (lane == 0 && (nc & 1u)) put_dummy(buf, nc);
     __syncwarp();
 }
 
@@ -620,7 +704,7 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
         c.le_leaf = reinterpret_cast<const float*>(leaf_le);
     }
     const uint32_t total = rpre[9];
-    const bool one_chunk = total <= kListCap && (!kCut || c.ctotal == 0);  // ring reuses buf
+    const bool one_chunk = total <= kListChunk && (!kCut || c.ctotal == 0);  // ring reuses buf
     uint32_t nn = 0, nf = 0;
     if (one_chunk) gather_bands(sp, c, nm, 0, total, buf, nn, nf);
 
@@ -652,17 +736,17 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
             y[t] = ((rec[t].y - c.cyh) - c.cyl) * nm.sc;
             S.su[t] = S.sv[t] = S.cu[t] = S.cv[t] = 0.f;
         }
-        for (uint32_t cb = 0; cb < total; cb += kListCap) {
+        for (uint32_t cb = 0; cb < total; cb += kListChunk) {
             if (!one_chunk)
-                gather_bands(sp, c, nm, cb, min((uint32_t)kListCap, total - cb), buf, nn, nf);
-            band_loopT<kNearBand, T>(buf, 0, nn, nm, x, y, S);
-            band_loopT<kFar, T>(buf, kListCap - nf, kListCap, nm, x, y, S);
+                gather_bands(sp, c, nm, cb, min(kListChunk, total - cb), buf, nn, nf);
+            band_loopT<kNearBand, T>(buf, 0, near_pairs(nn), nm, x, y, S);
+            band_loopT<kFar, T>(buf, far_first(nf), kListCap / 2, nm, x, y, S);
         }
         if (kCut)
-            for (uint32_t cb = 0; cb < c.ctotal; cb += kListCap) {  // cutoff ring
+            for (uint32_t cb = 0; cb < c.ctotal; cb += kListChunk) {  // cutoff ring
                 uint32_t nc;
-                gather_ring(sp, c, nm, cb, min((uint32_t)kListCap, c.ctotal - cb), buf, nc);
-                band_loopT<kRing, T>(buf, 0, nc, nm, x, y, S);
+                gather_ring(sp, c, nm, cb, min(kListChunk, c.ctotal - cb), buf, nc);
+                band_loopT<kRing, T>(buf, 0, near_pairs(nc), nm, x, y, S);
             }
 #pragma unroll
         for (int t = 0; t < T; ++t)
@@ -692,18 +776,18 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
         const float4 rec = sp[c.t0 + tb + (active ? tl : 0)];
         const float x = ((rec.x - c.cxh) - c.cxl) * nm.sc, y = ((rec.y - c.cyh) - c.cyl) * nm.sc;
         float su = 0.f, sv = 0.f, cu = 0.f, cv = 0.f;
-        for (uint32_t cb = 0; cb < total; cb += kListCap) {
+        for (uint32_t cb = 0; cb < total; cb += kListChunk) {
             if (!one_chunk)
-                gather_bands(sp, c, nm, cb, min((uint32_t)kListCap, total - cb), buf, nn, nf);
-            band_loop_split<kNearBand>(buf, 0, nn, ns, sl, nm, x, y, su, sv, cu, cv);
-            band_loop_split<kFar>(buf, kListCap - nf, kListCap, ns, sl, nm, x, y, su, sv, cu,
+                gather_bands(sp, c, nm, cb, min(kListChunk, total - cb), buf, nn, nf);
+            band_loop_split<kNearBand>(buf, 0, near_pairs(nn), ns, sl, nm, x, y, su, sv, cu, cv);
+            band_loop_split<kFar>(buf, far_first(nf), kListCap / 2, ns, sl, nm, x, y, su, sv, cu,
                                   cv);
         }
         if (kCut)
-            for (uint32_t cb = 0; cb < c.ctotal; cb += kListCap) {  // cutoff ring
+            for (uint32_t cb = 0; cb < c.ctotal; cb += kListChunk) {  // cutoff ring
                 uint32_t nc;
-                gather_ring(sp, c, nm, cb, min((uint32_t)kListCap, c.ctotal - cb), buf, nc);
-                band_loop_split<kRing>(buf, 0, nc, ns, sl, nm, x, y, su, sv, cu, cv);
+                gather_ring(sp, c, nm, cb, min(kListChunk, c.ctotal - cb), buf, nc);
+                band_loop_split<kRing>(buf, 0, near_pairs(nc), ns, sl, nm, x, y, su, sv, cu, cv);
             }
         su += cu;
         sv += cv;
