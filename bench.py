@@ -53,12 +53,15 @@ TOL = 1e-6
 VERIFY_TARGETS = 2048  # particles at which the proposal is judged (other seed than ACC_TARGETS)
 ACC_TARGETS = 8192
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
-# the fewest instructions one near pair of Eq. 6 takes in the 2^-q2 form:
-# on the FP32 pipe the 2 coordinate differences, dy^2, r^2 = fma(dx, dx, dy^2),
+# the fewest operations one near pair of Eq. 6 takes in the 2^-q2 form: on
+# the FP32 pipe the 2 coordinate differences, dx^2, r^2 = fma(dy, dy, dx^2),
 # Gamma (1 - 2^-q2) as one fma, the product with 1/q2 and the 2 fmas of the
-# velocity components (8); on the MUFU pipe ex2 and rcp (2)
-P2P_FP32_INSTR_PER_PAIR = 8
-P2P_MUFU_INSTR_PER_PAIR = 2
+# velocity components (8 lane operations); on the MUFU pipe ex2 and rcp (2).
+# Packed FP32 pair instructions (f32x2) do two lane operations per issue, so
+# a pair takes 4 + 2 issue slots.
+P2P_FP32_OPS_PER_PAIR = 8
+P2P_MUFU_OPS_PER_PAIR = 2
+P2P_ISSUE_PER_PAIR = 6
 
 
 # DRAM traffic of one near-field launch (dram__bytes_read.sum +
@@ -90,10 +93,65 @@ def m2l_pairs(L):
     return total
 
 
+def m2l_tiles(L):
+    """Tiles (CTAs) of the tensor-core M2L over levels 2..L: per level of G x G
+    target parents, the tw x th rectangle (th (tw + 2) <= 128 MMA rows,
+    tw <= 62) with the fewest tiles, then the smallest halo -- the choice the
+    library makes."""
+    total = 0
+    for lev in range(2, L + 1):
+        G = 1 << (lev - 1)
+        best = None
+        for tw in range(1, min(G, 62) + 1):
+            th = min(G, 128 // (tw + 2))
+            if th < 1:
+                break
+            key = (-(-G // tw) * -(-G // th), (tw + 2) * (th + 2))
+            if best is None or key < best:
+                best = key
+        total += best[0]
+    return total
+
+
+def m2l_executed_flops(p, L):
+    """Tensor flops the 3xTF32 M2L issues: per tile 8 Pk operator stages of 3
+    MMAs, each 2 x 128 x N x 8 with N = 8 Pk (Pk = p rounded up to 4)."""
+    pk = (p + 3) // 4 * 4
+    return m2l_tiles(L) * 8 * pk * 3 * 2.0 * 128 * 8 * pk * 8
+
+
 def tf32_peak_tflops(peaks):
     """Dense TF32 tensor peak: the measured bf16 figure times the nominal
     TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s dense)."""
     return float(peaks.get("bf16_tflops", 1900.0)) * 1.1 / 2.25
+
+
+def m2l_roofline(p, L, m2l_ms, peaks, peak_kind):
+    """Tensor-pipe roofline of the M2L phase (the TF32 split kernel and the
+    tensor-core contraction): useful flops 8 p^2 per interaction-list box
+    pair; executed flops what the 3 TF32 products issue over the tiles.  With
+    three products per useful one the useful rate is bounded by a third of the
+    TF32 peak: frac_of_3xtf32 measures against that bound."""
+    useful = 8.0 * p * p * m2l_pairs(L)
+    executed = m2l_executed_flops(p, L)
+    tf32 = tf32_peak_tflops(peaks)
+    ach = useful / (m2l_ms * 1e-3) / 1e12
+    return {
+        "kernel": "m2l_tc_split_kernel + m2l_parent_tc_kernel (tcgen05 3xTF32)",
+        "bound": "tensor", "unit": "TFLOP/s",
+        "achieved": ach, "peak": tf32, "frac": ach / tf32,
+        "frac_of_3xtf32": ach / (tf32 / 3.0),
+        "executed_tflops": executed / (m2l_ms * 1e-3) / 1e12,
+        "executed_frac": executed / (m2l_ms * 1e-3) / 1e12 / tf32,
+        "peak_source": f"{peak_kind} bf16 {float(peaks.get('bf16_tflops', 1900.0)):.0f} TFLOP/s "
+                       "x nominal TF32/BF16 1.1/2.25",
+        "flops_per_launch": useful, "executed_flops_per_launch": executed,
+        "flops_counted": "achieved: 8 p^2 per interaction-list box pair, levels 2..L (useful "
+                         "complex MACs); executed: 3 TF32 products x 2 x 128 x 8 Pk x 8 per "
+                         "MMA over every tile (zero blocks of adjacent children, MMA rows on "
+                         "halo columns and the rounding of p up to Pk included)",
+        "avg_launch_ms": m2l_ms,
+    }
 
 
 def p2p_traffic(p, L, cutoff):
@@ -116,12 +174,12 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# P2P unit rates per SM per clock (Blackwell SM: 128 FP32 lanes, 16 MUFU lanes).
+# P2P unit rates per SM per clock, measured on GB300 by chains of independent
+# instructions (CUDA events, 152 x 8 CTAs of 256 threads): scalar fma 117 and
+# packed f32x2 fma 120 lane operations per SM per clock (one 128-lane FP32
+# pipe either way: packing halves issue slots, not pipe time), ex2 30 (a
+# 32-lane MUFU pipe, twice the 16 lanes of earlier parts).
 FP32_LANES_PER_SM = 128
-# ex2 / rcp lanes per SM: the near-field capture has the XU pipe 36% of its
-# peak while issuing at least 0.31 MUFU warp instructions per SM cycle
-# (2 per evaluated pair), which needs a peak of about one warp instruction
-# per SM cycle: 32 lanes, twice the 16 of earlier parts
 MUFU_LANES_PER_SM = 32
 ISSUE_LANES_PER_SM = 128  # 4 schedulers x one warp instruction per cycle
 N_SMS = 152
@@ -129,11 +187,12 @@ N_SMS = 152
 
 def p2p_peak_pairs_per_s(sm_mhz: float) -> float:
     """ALU roofline of the near-field pair: the least of the FP32 pipe
-    (8 instructions), the MUFU pipe (2) and instruction issue (all 10) per SM
-    per clock, times SMs and clock."""
-    fp32 = FP32_LANES_PER_SM / P2P_FP32_INSTR_PER_PAIR
-    mufu = MUFU_LANES_PER_SM / P2P_MUFU_INSTR_PER_PAIR
-    issue = ISSUE_LANES_PER_SM / (P2P_FP32_INSTR_PER_PAIR + P2P_MUFU_INSTR_PER_PAIR)
+    (8 lane operations), the MUFU pipe (2) and instruction issue (6 with
+    packed FP32 pairs) per SM per clock, times SMs and clock: 16 pairs per SM
+    per clock, the FP32 and MUFU pipes together."""
+    fp32 = FP32_LANES_PER_SM / P2P_FP32_OPS_PER_PAIR
+    mufu = MUFU_LANES_PER_SM / P2P_MUFU_OPS_PER_PAIR
+    issue = ISSUE_LANES_PER_SM / P2P_ISSUE_PER_PAIR
     return min(fp32, mufu, issue) * N_SMS * sm_mhz * 1e6
 
 
@@ -400,15 +459,7 @@ def run_clustered(torch, dev, flush, steps=5):
         plan.check()
     ph = {k: float(np.mean([q[k] for q in phases])) for k in phases[0]}
     peaks, peak_kind = _peaks()
-    m2l_flops = 8.0 * w.p * w.p * m2l_pairs(w.L)
-    tf32 = tf32_peak_tflops(peaks)
-    P = 16 if w.p <= 16 else 32
-    m2l = {"bound": "tensor", "unit": "TFLOP/s", "peak": tf32,
-           "achieved": m2l_flops / (ph["m2l"] * 1e-3) / 1e12,
-           "frac": m2l_flops / (ph["m2l"] * 1e-3) / 1e12 / tf32,
-           "executed_frac": 3.0 * (P / w.p) ** 2 * m2l_flops / (ph["m2l"] * 1e-3) / 1e12 / tf32,
-           "note": "achieved counts useful flops (8 p^2 per box pair); executed_frac adds the "
-                   "3xTF32 split and the zero padding of p to P"}
+    m2l = m2l_roofline(w.p, w.L, ph["m2l"], peaks, peak_kind)
     return {"workload": "clustered_16m: N=2^24, 64 Gaussian patches (std 0.02-0.2), signed "
                         "patch circulations h^2 N(0,1), sigma=h=2/4096, p=20, L=9, fp32_tc",
             "roofline_m2l": m2l,
@@ -485,6 +536,33 @@ def _ring_pairs(torch, xy, L, root, a, targets):
     return int(round(float(torch.cat(counts).mean()) * n))
 
 
+def _pointwise_rel(uv, t, ref):
+    """max_i |du_i| / |u_i| over the sampled particles (|u_i| > 0)."""
+    got = uv[t].double()
+    du = (got - ref).norm(dim=1)
+    ru = ref.norm(dim=1)
+    keep = ru > 0
+    return float((du[keep] / ru[keep]).max().item()) if bool(keep.any()) else 0.0
+
+
+def _dgemm_tflops(torch, dev, n=4096, reps=5):
+    """Measured FP64 rate of this GPU: cuBLAS DGEMM n^3 (2 n^3 flops), best of reps."""
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    best = None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
 def _near_pairs(plan, n, L):
     """sum over leaves of n_leaf * n_3x3 minus the self pairs."""
     _, _, start = plan.tree(n)
@@ -501,6 +579,106 @@ def _near_pairs(plan, n, L):
     padg = np.pad(grid, 1)
     nb = sum(padg[1 + dy:1 + dy + nl, 1 + dx:1 + dx + nl] for dy in (-1, 0, 1) for dx in (-1, 0, 1))
     return int((grid * nb).sum()) - n
+
+
+def run_split(args):
+    """One uniform_1m evaluation split over the N ranks by contiguous Morton
+    ranges of leaves (paper_0809_1810_gb300.partition): each rank holds only
+    its own particles; per step it forms their multipoles, the partial
+    multipoles are summed over the ranks (NCCL all-reduce of the multipole
+    array: the interaction-list exchange as one collective), the particles of
+    the halo leaves move by a variable-size all-to-all, and each rank
+    evaluates its own particles from the summed multipoles.  Strong scaling
+    (the total work is fixed); unmeasured on hardware so far."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_0809_1810_gb300 import Plan
+    from paper_0809_1810_gb300 import partition as PT
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = W.uniform_1m()
+    p, L = w.p, w.L
+    from paper_0809_1810_gb300 import cutoff_for
+
+    a = cutoff_for(w.sigma, w.root[2] / 2 ** L, TOL)
+    reach = 2 if a > 0 else 1
+    # the partition and the exchange plan (host, once per particle set)
+    x0, y0, W_ = w.root
+    side = 1 << L
+    lx = np.clip(np.floor((w.x.astype(np.float64) - x0) * side / W_), 0, side - 1).astype(np.int64)
+    ly = np.clip(np.floor((w.y.astype(np.float64) - y0) * side / W_), 0, side - 1).astype(np.int64)
+    leaf = PT.morton_key(lx, ly).astype(np.int64)
+    bounds = PT.leaf_bounds(np.bincount(leaf, minlength=side * side), world)
+    own = PT.owner_of(leaf, bounds)
+    xplan = PT.exchange_plan(bounds, L, reach)
+    mine = np.nonzero(own == rank)[0]
+    # this rank's particles only; what it sends to each rank, in its own order
+    xy = torch.tensor(np.stack([w.x[mine], w.y[mine]], 1), device=dev)
+    g = torch.tensor(w.gamma[mine], device=dev)
+    leaf_mine = leaf[mine]
+    send_idx = [torch.as_tensor(np.nonzero(np.isin(leaf_mine, xplan[(rank, r)]["leaves"]))[0]
+                                if r != rank else np.zeros(0, dtype=np.int64), device=dev)
+                for r in range(world)]
+    send_sizes = [int(t.numel()) for t in send_idx]
+    recv_sizes = [int(np.isin(leaf[own == q], xplan[(q, rank)]["leaves"]).sum())
+                  if q != rank else 0 for q in range(world)]
+    send_order = torch.cat(send_idx) if sum(send_sizes) else torch.zeros(0, dtype=torch.long,
+                                                                         device=dev)
+    n_local = int(mine.size + sum(recv_sizes))
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    with Plan(p, L, w.sigma, "fp32_tc", root=w.root, max_n=max(n_local, 1), cutoff=a) as plan:
+        me = torch.zeros(max(plan.multipole_reals(), 1), dtype=torch.float32, device=dev)
+        buf_xy = torch.empty((n_local, 2), dtype=torch.float32, device=dev)
+        buf_g = torch.empty(n_local, dtype=torch.float32, device=dev)
+        uv = torch.empty((n_local, 2), dtype=torch.float32, device=dev)
+
+        def step():
+            plan.multipoles(xy, g, out=me)
+            dist.all_reduce(me)
+            packed = torch.cat([xy[send_order], g[send_order, None]], 1).contiguous()
+            recv = torch.empty((sum(recv_sizes), 3), dtype=torch.float32, device=dev)
+            dist.all_to_all_single(recv, packed, recv_sizes, send_sizes)
+            buf_xy[: mine.size] = xy
+            buf_g[: mine.size] = g
+            buf_xy[mine.size:] = recv[:, :2]
+            buf_g[mine.size:] = recv[:, 2]
+            plan.velocity_from_multipoles(buf_xy, buf_g, me, out=uv)
+
+        for _ in range(args.warmup):
+            step()
+        plan.check()
+        barrier(pg, torch)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for e0, e1 in ev:
+            flush.zero_()
+            barrier(pg, torch)
+            e0.record()
+            step()
+            e1.record()
+        torch.cuda.synchronize()
+        ms = max_over_ranks(pg, float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev])), torch,
+                            dev)
+        plan.check()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": w.n / (ms * 1e-3), "unit": "particles/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "p": p, "L": L, "cutoff": a,
+                       "precision": "fp32_tc", "parallelism": f"Morton-range split x{world}",
+                       "exchange": "NCCL all-reduce of the multipoles, all-to-all of the halo "
+                                   "particles, inside every timed step",
+                       "l2": "flushed between timed steps (512 MiB write outside the events)"},
+            "halo_particles_received_rank0": sum(recv_sizes),
+            "note": "unmeasured on hardware until a multi-GPU run exists",
+        }))
+    if pg is not None:
+        pg.destroy_process_group()
 
 
 def run_ours(args):
@@ -538,10 +716,14 @@ def run_ours(args):
     accuracy = {
         "targets": ACC_TARGETS, "tolerance": TOL,
         "max_rel_err_vs_fp64_direct": err, "meets_tolerance": bool(err <= TOL),
+        "normalisation": "max_i |du_i| / max_j |u_j| over the sampled particles (Sec. 5.1: "
+                         "errors normalised by the maximum velocity)",
+        "max_pointwise_rel_err_vs_fp64_direct": _pointwise_rel(uv, t, ref_direct),
         "max_rel_err_vs_fp64_fmm_limit": float(s_hyb[0] / s_hyb[1]),
-        "note": "FP64 direct = regularised sum (Eq. 7), max |du| / max |u| over the "
-                "sampled particles; FMM limit = Eq. 6 near (and closer than the cutoff) / "
-                "singular far (Eq. 10, Sec. 4.1)",
+        "note": "FP64 direct = regularised sum (Eq. 7); FMM limit = Eq. 6 near (and closer "
+                "than the cutoff) / singular far (Eq. 10, Sec. 4.1); the pointwise figure "
+                "max_i |du_i| / |u_i| is not the metric (particles of small |u_i| carry "
+                "large relative errors) and is reported for context",
     }
 
     # timed region: the evaluation graph as a user runs it (no event nodes)
@@ -580,11 +762,11 @@ def run_ours(args):
                   + ") then l2p_f32_kernel (far part), timed together from the end of the tree",
         "bound": "alu", "unit": "Gpair/s",
         "achieved": achieved / 1e9, "peak": peak / 1e9, "frac": achieved / peak,
-        "peak_source": f"derived: min(128 FP32 lanes / {P2P_FP32_INSTR_PER_PAIR}, "
-                       f"{MUFU_LANES_PER_SM} MUFU lanes / {P2P_MUFU_INSTR_PER_PAIR}, 128 issue "
-                       f"lanes / {P2P_FP32_INSTR_PER_PAIR + P2P_MUFU_INSTR_PER_PAIR} "
-                       f"instructions) pairs per SM per clock x 152 SMs x "
-                       f"{sm_max:.0f} MHz ({peak_kind} sm_max_mhz)",
+        "peak_source": f"derived: min(128 FP32 lanes / {P2P_FP32_OPS_PER_PAIR}, "
+                       f"{MUFU_LANES_PER_SM} MUFU lanes / {P2P_MUFU_OPS_PER_PAIR}, 128 issue "
+                       f"lanes / {P2P_ISSUE_PER_PAIR} instructions with packed FP32) pairs per "
+                       f"SM per clock x 152 SMs x {sm_max:.0f} MHz ({peak_kind} sm_max_mhz); "
+                       "lane rates measured on GB300 (fma, f32x2 fma, ex2 chains)",
         "pairs_per_launch": pairs, "near_pairs": near_pairs,
         "ring_pairs": ring_pairs,
         "pairs_counted": "3x3-neighbour pairs exactly; cutoff pairs (closer than a, leaves "
@@ -599,22 +781,10 @@ def run_ours(args):
     }
 
     m2l_ms = phase_avg["m2l"]
-    m2l_flops = 8.0 * p * p * m2l_pairs(L)
-    tf32 = tf32_peak_tflops(peaks)
-    roofline_m2l = {
-        "kernel": "m2l_split_kernel + m2l_tc_kernel (tcgen05 3xTF32)",
-        "bound": "tensor", "unit": "TFLOP/s",
-        "achieved": m2l_flops / (m2l_ms * 1e-3) / 1e12, "peak": tf32,
-        "frac": m2l_flops / (m2l_ms * 1e-3) / 1e12 / tf32,
-        "peak_source": f"{peak_kind} bf16 {float(peaks.get('bf16_tflops', 1900.0)):.0f} TFLOP/s "
-                       "x nominal TF32/BF16 1.1/2.25",
-        "flops_per_launch": m2l_flops,
-        "flops_counted": "8 p^2 per interaction-list box pair, levels 2..L (useful complex "
-                         "MACs; the 3xTF32 split and the zero padding to P = 16/32 run more)",
-        "note": "the far field runs beside the near field in the graph: its phase times "
-                "include waiting for SM room while the near field holds the GPU",
-        "avg_launch_ms": m2l_ms,
-    }
+    roofline_m2l = m2l_roofline(p, L, m2l_ms, peaks, peak_kind)
+    roofline_m2l["note"] = ("the far field runs beside the near field in the graph: its phase "
+                            "times include waiting for SM room while the near field holds "
+                            "the GPU")
 
     # end to end through the host-buffer entry point
     hxy = xy.cpu().pin_memory()
@@ -674,10 +844,31 @@ def run_ours(args):
         plan64.check()
         fp64_ms = float(np.mean(_time_steps(torch, plan64, xy64, g64, uv64, 3, flush)))
         s64 = plan64.error_stats(xy64, uv64, t, ref_direct).cpu().numpy()
+        plan64.set_timing(3)
+        for _ in range(3):
+            plan64.velocity(xy64, g64, out=uv64)
+        torch.cuda.synchronize()
+        ph64 = [plan64.phase_ms(a) for a in range(3)]
+        ph64 = {k: float(np.mean([q[k] for q in ph64])) for k in ph64[0]}
+        pairs64 = _near_pairs(plan64, n, Lf)
+        plan64.set_timing(0)
+    dgemm = _dgemm_tflops(torch, dev)
+    near64 = pairs64 / (ph64["p2p_l2p"] * 1e-3)
     plain_fp64 = {"p": pf, "L": Lf, "value": n / (fp64_ms * 1e-3), "unit": "particles/s",
                   "ms_per_step": fp64_ms, "max_rel_err_vs_fp64_direct": float(s64[0] / s64[1]),
                   "meets_tolerance": bool(s64[0] / s64[1] <= TOL),
-                  "speedup_of_value": fp64_ms / ms_per_step}
+                  "speedup_of_value": fp64_ms / ms_per_step,
+                  "phase_ms": ph64,
+                  "near_field": {
+                      "pairs": pairs64, "gpair_per_s": near64 / 1e9,
+                      "fp64_tflops_at_25_flops_per_pair": 25.0 * near64 / 1e12,
+                      "measured_fp64_tflops": dgemm,
+                      "frac": 25.0 * near64 / 1e12 / dgemm,
+                      "peak_source": "measured here: cuBLAS DGEMM 4096^3 through torch.matmul, "
+                                     "best of 5",
+                      "note": "25 FP64 flops per pair is the pair formula without exp and "
+                              "the division, which GB300 runs as further FP64 instructions; "
+                              "the near field holds most of the step"}}
 
     batch = None if args.no_batch else run_batch_sweep(torch, dev, flush, rank, pg)
     large = None if args.no_large else run_clustered(torch, dev, flush)
@@ -724,6 +915,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep line item")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 2^24-particle clustered line item")
+    ap.add_argument("--split", action="store_true",
+                    help="with N > 1 ranks: split one evaluation over them (Morton ranges, "
+                         "multipole all-reduce, halo all-to-all) instead of replicas")
     ap.add_argument("--setting", default="proposer",
                     choices=["proposer", "cutoff", "configured", "fallback"],
                     help="the trained proposer's verified choice for 1e-6 (default), the "
@@ -732,6 +926,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.split and args.impl == "ours" and int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        run_split(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
