@@ -233,6 +233,8 @@ typedef struct {
     int L;            /* quadtree depth, 0..12 */
     double sigma;     /* core size, > 0 */
     double x0, y0, W; /* root box, W > 0 */
+    double cutoff;    /* the distance a of Sec. 4.1 as in fmm2d_params (0: the plain
+                         3x3 rule; at L >= 2 at most 2 W / 2^L) */
 } fmm2d_instance;
 
 typedef struct fmm2d_batch_plan fmm2d_batch_plan;
@@ -245,6 +247,14 @@ const char* fmm2d_batch_last_error(void);
  * current device and builds the translation tables.  Synchronous. */
 fmm2d_status fmm2d_batch_plan_create(fmm2d_batch_plan** out, int count,
                                      const fmm2d_instance* instances);
+/* The same with a precision: FMM2D_FP32 (as fmm2d_batch_plan_create: float
+ * storage and arithmetic, M2L on the CUDA cores) or FMM2D_FP32_TC (M2L as the
+ * 3xTF32 tensor-core contraction of every instance with L >= 2, one launch
+ * per class of equal p rounded up to 4).  Every other step is the same in
+ * both, and a batched instance gives bit for bit what a single plan of the
+ * same precision gives. */
+fmm2d_status fmm2d_batch_plan_create_ex(fmm2d_batch_plan** out, int count,
+                                        const fmm2d_instance* instances, int precision);
 void fmm2d_batch_plan_destroy(fmm2d_batch_plan* plan);
 
 /* Velocities of every instance (packed xy: 2 sum(n) floats, gamma: sum(n),
@@ -259,7 +269,10 @@ fmm2d_status fmm2d_batch_velocity(fmm2d_batch_plan* plan, const float* xy_dev,
 fmm2d_status fmm2d_batch_check(fmm2d_batch_plan* plan, cudaStream_t stream);
 
 /* Autotuner: times candidate launch shapes of the two heaviest steps on the
- * given batch (persistent near-field CTAs per SM in {2..6}; M2L block size in
+ * given batch (persistent near-field CTAs per SM in {2..6}; for FP32_TC
+ * batches the tensor-core M2L's operator stages in flight, 2, 3, 4 or as many
+ * as shared memory holds, and its tile policy, the fewest tiles per level or
+ * the widest rows; for FP32 batches the CUDA-core M2L block size in
  * {64, 128, 256}), keeps the fastest and leaves uv_dev holding the
  * velocities.  Synchronous; later fmm2d_batch_velocity calls use the
  * choices. */
@@ -288,6 +301,13 @@ fmm2d_status fmm2d_batch_error_stats(fmm2d_batch_plan* plan, const float* xy_dev
 fmm2d_status fmm2d_batch_info(const fmm2d_batch_plan* plan, int64_t* n_total,
                               int64_t* leaves_total, int* kernels_per_call, int* p2p_ctas_per_sm,
                               int* m2l_threads);
+
+/* FP32_TC batches: tensor-core M2L classes (one per p rounded up to 4),
+ * their tiles in all, the operator stages in flight (of the first class)
+ * and the tile policy the autotuner chose (0: fewest tiles per level, 1:
+ * widest rows).  Each output may be NULL; zeros for FP32 batches. */
+fmm2d_status fmm2d_batch_info_tc(const fmm2d_batch_plan* plan, int* classes, int* tiles,
+                                 int* b_stages, int* tile_policy);
 
 /* Quadtree of the last batch evaluation in the global leaf order (keys are
  * leaf_base_i + Morton key): as fmm2d_tree_debug, leaf_start has

@@ -266,24 +266,27 @@ class Plan:
 
 
 class BatchPlan:
-    """Many independent instances evaluated together (fmm2d_batch_*): FP32,
-    one CUDA graph per call.  ``instances`` is a list of dicts with keys n, p,
-    L, sigma and optionally root=(x0, y0, W)."""
+    """Many independent instances evaluated together (fmm2d_batch_*): FP32
+    or FP32_TC (``precision``), one CUDA graph per call.  ``instances`` is a
+    list of dicts with keys n, p, L, sigma and optionally root=(x0, y0, W) and
+    cutoff (the distance a of Sec. 4.1, 0 by default)."""
 
-    def __init__(self, instances):
+    def __init__(self, instances, precision="fp32"):
         self._lib = _native.load()
         arr = (_native.Instance * len(instances))()
         for k, d in enumerate(instances):
             root = d.get("root", (-1.0, -1.0, 2.0))
             arr[k] = _native.Instance(int(d["n"]), int(d["p"]), int(d["L"]), float(d["sigma"]),
-                                      float(root[0]), float(root[1]), float(root[2]))
+                                      float(root[0]), float(root[1]), float(root[2]),
+                                      float(d.get("cutoff", 0.0)))
+        self.precision = precision
         self.instances = [dict(d) for d in instances]
         self.offsets = [0]
         for d in instances:
             self.offsets.append(self.offsets[-1] + int(d["n"]))
         h = ctypes.c_void_p()
-        _check(self._lib.fmm2d_batch_plan_create(ctypes.byref(h), len(instances), arr),
-               "batch_plan_create")
+        _check(self._lib.fmm2d_batch_plan_create_ex(ctypes.byref(h), len(instances), arr,
+                                                    _PREC[precision]), "batch_plan_create")
         self._h = h
 
     def close(self):
@@ -336,8 +339,17 @@ class BatchPlan:
         _check(self._lib.fmm2d_batch_info(self._h, ctypes.byref(n), ctypes.byref(leaves),
                                           ctypes.byref(k), ctypes.byref(cps), ctypes.byref(th)),
                "batch_info")
+        cls = ctypes.c_int()
+        tiles = ctypes.c_int()
+        st = ctypes.c_int()
+        pol = ctypes.c_int()
+        _check(self._lib.fmm2d_batch_info_tc(self._h, ctypes.byref(cls), ctypes.byref(tiles),
+                                             ctypes.byref(st), ctypes.byref(pol)),
+               "batch_info_tc")
         return {"n_total": n.value, "leaves_total": leaves.value, "kernels_per_call": k.value,
-                "p2p_ctas_per_sm": cps.value, "m2l_threads": th.value}
+                "p2p_ctas_per_sm": cps.value, "m2l_threads": th.value,
+                "precision": self.precision, "tc_classes": cls.value, "tc_tiles": tiles.value,
+                "tc_b_stages": st.value, "tc_tile_policy": pol.value}
 
     def direct_sampled(self, xy, gamma, targets, kernel=0, stream=None):
         targets = targets.to(device=xy.device, dtype=torch.int64).contiguous()

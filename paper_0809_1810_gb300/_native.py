@@ -27,7 +27,7 @@ class Params(ctypes.Structure):
 class Instance(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("p", ctypes.c_int), ("L", ctypes.c_int),
                 ("sigma", ctypes.c_double), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
-                ("W", ctypes.c_double)]
+                ("W", ctypes.c_double), ("cutoff", ctypes.c_double)]
 
 
 _lib = None
@@ -79,6 +79,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "fmm2d_tree_build_noalloc": ([i32, i64, vp, vp, i32, d, d, d, vp, vp, vp, vp, vp], i32),
         "fmm2d_batch_last_error": ([], ctypes.c_char_p),
         "fmm2d_batch_plan_create": ([ctypes.POINTER(vp), i32, vp], i32),
+        "fmm2d_batch_plan_create_ex": ([ctypes.POINTER(vp), i32, vp, i32], i32),
         "fmm2d_batch_plan_destroy": ([vp], None),
         "fmm2d_batch_velocity": ([vp, vp, vp, vp, vp], i32),
         "fmm2d_batch_check": ([vp, vp], i32),
@@ -86,6 +87,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "fmm2d_batch_direct_sampled": ([vp, i32, vp, vp, i64, vp, vp, vp], i32),
         "fmm2d_batch_error_stats": ([vp, vp, vp, i64, vp, vp, vp, vp, vp], i32),
         "fmm2d_batch_info": ([vp, vp, vp, vp, vp, vp], i32),
+        "fmm2d_batch_info_tc": ([vp, vp, vp, vp, vp], i32),
         "fmm2d_batch_tree_debug": ([vp, vp, vp, vp, vp], i32),
         "fmm2d_mlp_last_error": ([], ctypes.c_char_p),
         "fmm2d_mlp_create": ([ctypes.POINTER(vp), i32, ctypes.c_uint64], i32),

@@ -543,11 +543,11 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
             configured = true;
         }
         M2LTcConfig cfg = m2l_tc_plan(g, nullptr);  // tile count first (no device work)
-        std::vector<int4> tiles(cfg.ntiles);
+        std::vector<int4> tiles(2 * (size_t)cfg.ntiles);  // two records per tile
         cfg = m2l_tc_plan(g, tiles.data());
         size_t me_floats = (size_t)g.nboxes * 2 * cfg.Pk;
         size_t bytes = align256(me_floats * 4) * 2 + align256((size_t)cfg.b_floats * 4) +
-                       align256((size_t)cfg.ntiles * sizeof(int4));
+                       align256((size_t)cfg.ntiles * 2 * sizeof(int4));
         e = cudaMalloc(&pl->tc_ws, bytes);
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "tensor-core workspace cudaMalloc"));
         char* q = static_cast<char*>(pl->tc_ws);
@@ -563,7 +563,7 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
         e = m2l_tc_prepare(g, cfg, pl->tab64 + 8 * per, pl->me_hi, pl->me_lo, pl->bimg, pl->maps,
                            pl->cap);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(pl->tiles, tiles.data(), (size_t)cfg.ntiles * sizeof(int4),
+            e = cudaMemcpyAsync(pl->tiles, tiles.data(), (size_t)cfg.ntiles * 2 * sizeof(int4),
                                 cudaMemcpyHostToDevice, pl->cap);
         if (e == cudaSuccess) e = cudaStreamSynchronize(pl->cap);
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "tensor-core M2L set-up"));

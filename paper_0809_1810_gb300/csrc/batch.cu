@@ -69,6 +69,13 @@ struct fmm2d_batch_plan {
     // launch shapes (autotuned)
     int p2p_ctas_per_sm = 4;
     int m2l_threads = 128;
+    // FP32_TC: one tensor-core M2L class per Pk (operator stages and tile
+    // policy autotuned); FP32: M2L on the CUDA cores
+    int precision = FMM2D_FP32;
+    std::vector<M2LTcBatchClass> tc;
+    int tc_b_stages = 0;  // 0: as many as shared memory holds
+    int tc_policy = 0;
+    bool any_cutoff = false;
     // graph
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
@@ -109,10 +116,15 @@ cudaError_t enqueue_batch(fmm2d_batch_plan* b, const float* xy, const float* gam
             if (b->has_class[c])
                 BSTEP(launch_batch_m2m(b->d_inst, b->lists[c], c ? 32 : 16, l, tab_m2m(b, c),
                                        b->me, s));
-    for (int c = 0; c < 2; ++c)
-        if (b->has_class[c])
-            BSTEP(launch_batch_m2l(b->d_inst, b->lists[c], c ? 32 : 16, b->m2l_threads,
-                                   tab_m2l(b, c), b->me, b->le, s));
+    if (b->precision == FMM2D_FP32_TC) {
+        for (const M2LTcBatchClass& c : b->tc)
+            BSTEP(launch_m2l_tc_batch(c, b->d_inst, b->me, b->le, b->d_status, 0, s));
+    } else {
+        for (int c = 0; c < 2; ++c)
+            if (b->has_class[c])
+                BSTEP(launch_batch_m2l(b->d_inst, b->lists[c], c ? 32 : 16, b->m2l_threads,
+                                       tab_m2l(b, c), b->me, b->le, s));
+    }
     for (int l = 3; l <= b->max_L - 1; ++l)
         for (int c = 0; c < 2; ++c)
             if (b->has_class[c])
@@ -122,7 +134,7 @@ cudaError_t enqueue_batch(fmm2d_batch_plan* b, const float* xy, const float* gam
                            b->d_counter, b->p2p_ctas_per_sm, b->particles,
                            b->sb.keys[sort_passes(b->key_bits) & 1], b->sb.leaf_start, b->le,
                            b->has_class[0] ? tab_l2l(b, 0) : nullptr,
-                           b->has_class[1] ? tab_l2l(b, 1) : nullptr, uv, s));
+                           b->has_class[1] ? tab_l2l(b, 1) : nullptr, uv, b->any_cutoff, s));
 #undef BSTEP
     return cudaSuccess;
 }
@@ -174,7 +186,38 @@ bool valid_instance(const fmm2d_instance& in, std::string* why) {
     if (!(in.sigma > 0.0) || !std::isfinite(in.sigma)) return *why = "instance sigma", false;
     if (!(in.W > 0.0) || !std::isfinite(in.W) || !std::isfinite(in.x0) || !std::isfinite(in.y0))
         return *why = "instance root box", false;
+    // the kernels correct the ring of leaves at Chebyshev distance 2 only
+    if (!(in.cutoff >= 0.0) || !std::isfinite(in.cutoff) ||
+        (in.L >= 2 && in.cutoff > 2.0 * in.W / ldexp(1.0, in.L)))
+        return *why = "instance cutoff must be in [0, 2 W / 2^L]", false;
     return true;
+}
+
+// (Re)build the tensor-core M2L classes with the given operator stages and
+// tile policy: the instances with L >= 2 grouped by Pk = p rounded up to 4.
+cudaError_t build_tc_classes(fmm2d_batch_plan* b, int b_stages, int policy) {
+    for (auto& c : b->tc) m2l_tc_batch_destroy(&c);
+    b->tc.clear();
+    for (int Pk = 4; Pk <= kMaxP; Pk += 4) {
+        std::vector<int> ids;
+        for (int i = 0; i < b->count; ++i) {
+            const Geometry& g = b->inst[i].g;
+            if (g.L >= 2 && ((g.p + 3) & ~3) == Pk) ids.push_back(i);
+        }
+        if (ids.empty()) continue;
+        const int P = Pk <= 16 ? 16 : 32;
+        const int c = class_of(P);
+        const int64_t per = (int64_t)P * P * 2;
+        M2LTcBatchClass cls;
+        cudaError_t e = m2l_tc_batch_create(b->inst.data(), ids.data(), (int)ids.size(), Pk, P,
+                                            b->tab64[c] + 8 * per, b_stages, policy, &cls,
+                                            b->cap);
+        if (e != cudaSuccess) return e;
+        b->tc.push_back(cls);
+    }
+    b->tc_b_stages = b_stages;
+    b->tc_policy = policy;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -185,7 +228,14 @@ const char* fmm2d_batch_last_error(void) { return g_batch_error.c_str(); }
 
 fmm2d_status fmm2d_batch_plan_create(fmm2d_batch_plan** out, int count,
                                      const fmm2d_instance* in) {
+    return fmm2d_batch_plan_create_ex(out, count, in, FMM2D_FP32);
+}
+
+fmm2d_status fmm2d_batch_plan_create_ex(fmm2d_batch_plan** out, int count,
+                                        const fmm2d_instance* in, int precision) {
     if (!out) return bfail(FMM2D_INVALID_ARG, "null output pointer");
+    if (precision != FMM2D_FP32 && precision != FMM2D_FP32_TC)
+        return bfail(FMM2D_INVALID_ARG, "batch precision must be FMM2D_FP32 or FMM2D_FP32_TC");
     *out = nullptr;
     if (count < 1 || !in) return bfail(FMM2D_INVALID_ARG, "count must be >= 1 with instances");
     std::string why;
@@ -207,6 +257,7 @@ fmm2d_status fmm2d_batch_plan_create(fmm2d_batch_plan** out, int count,
     };
     cudaGetDevice(&b->device);
     b->count = count;
+    b->precision = precision;
     b->ntotal = ntotal;
     b->nleaf_total = (uint32_t)nleaf;
     while ((1ull << b->key_bits) < nleaf) ++b->key_bits;
@@ -231,7 +282,8 @@ fmm2d_status fmm2d_batch_plan_create(fmm2d_batch_plan** out, int count,
         }
         g.nboxes = acc;
         g.scale = ldexp(1.0, g.L) / g.W;
-        g.cutoff = 0.0;  // batched instances use the plain 3x3 rule
+        g.cutoff = g.L >= 2 ? in[i].cutoff : 0.0;  // Sec. 4.1 (0: the plain 3x3 rule)
+        if (g.cutoff > 0.0) b->any_cutoff = true;
         bi.offset = off;
         bi.n = in[i].n;
         bi.exp_off = exp_total;
@@ -373,6 +425,14 @@ fmm2d_status fmm2d_batch_plan_create(fmm2d_batch_plan** out, int count,
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = batch_key_params(b->inst.data(), count, b->d_keyparams, s);
     if (e == cudaSuccess) e = batch_near_fill(b->inst.data(), count, b->d_near, s);
+    if (e == cudaSuccess && precision == FMM2D_FP32_TC) {
+        static bool configured = false;
+        if (!configured) {
+            e = m2l_tc_configure();
+            configured = e == cudaSuccess;
+        }
+        if (e == cudaSuccess) e = build_tc_classes(b, 0, 0);
+    }
     if (e != cudaSuccess)
         return cleanup(bfail(FMM2D_CUDA_ERROR, std::string("batch set-up: ") +
                                                    cudaGetErrorString(e)));
@@ -387,6 +447,7 @@ void fmm2d_batch_plan_destroy(fmm2d_batch_plan* b) {
     cudaSetDevice(b->device);
     cudaDeviceSynchronize();
     drop_batch_graph(b);
+    for (auto& c : b->tc) m2l_tc_batch_destroy(&c);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->h_status) cudaFreeHost(b->h_status);
     if (b->ws) cudaFree(b->ws);
@@ -455,12 +516,39 @@ fmm2d_status fmm2d_batch_autotune(fmm2d_batch_plan* b, const float* xy, const fl
                                     b->sb.keys[sort_passes(b->key_bits) & 1],
                                     b->sb.leaf_start, b->le,
                                     b->has_class[0] ? tab_l2l(b, 0) : nullptr,
-                                    b->has_class[1] ? tab_l2l(b, 1) : nullptr, uv, s);
+                                    b->has_class[1] ? tab_l2l(b, 1) : nullptr, uv,
+                                    b->any_cutoff, s);
         });
         if (ms < best) {
             best = ms;
             best_cps = cps;
         }
+    }
+    // FP32_TC: the tensor-core M2L's shapes -- operator stages in flight
+    // (2, 3, 4 or as many as shared memory holds) and the tile policy (the
+    // fewest tiles, or the widest rows) -- timed over every class
+    if (b->precision == FMM2D_FP32_TC) {
+        float tbest = 1e30f;
+        int bst = 0, bpol = 0;
+        for (int pol : {0, 1})
+            for (int st : {2, 3, 4, 0}) {
+                if (build_tc_classes(b, st, pol) != cudaSuccess) continue;
+                float ms = time_it([&] {
+                    cudaError_t r = cudaSuccess;
+                    for (const M2LTcBatchClass& c : b->tc)
+                        if (r == cudaSuccess)
+                            r = launch_m2l_tc_batch(c, b->d_inst, b->me, b->le, b->d_status, 0,
+                                                    s);
+                    return r;
+                });
+                if (ms < tbest) {
+                    tbest = ms;
+                    bst = st;
+                    bpol = pol;
+                }
+            }
+        if (build_tc_classes(b, bst, bpol) != cudaSuccess)
+            return bfail(FMM2D_CUDA_ERROR, "tensor-core M2L classes");
     }
     // M2L: block size of the box-parallel contraction
     best = 1e30f;
@@ -524,6 +612,18 @@ fmm2d_status fmm2d_batch_info(const fmm2d_batch_plan* b, int64_t* n_total, int64
     if (kernels_per_call) *kernels_per_call = b->kernel_nodes;
     if (p2p_ctas_per_sm) *p2p_ctas_per_sm = b->p2p_ctas_per_sm;
     if (m2l_threads) *m2l_threads = b->m2l_threads;
+    return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_batch_info_tc(const fmm2d_batch_plan* b, int* classes, int* tiles,
+                                 int* b_stages, int* tile_policy) {
+    if (!b) return bfail(FMM2D_INVALID_ARG, "null plan");
+    int t = 0;
+    for (const M2LTcBatchClass& c : b->tc) t += c.cfg.ntiles;
+    if (classes) *classes = (int)b->tc.size();
+    if (tiles) *tiles = t;
+    if (b_stages) *b_stages = b->tc.empty() ? 0 : b->tc[0].cfg.b_stages;
+    if (tile_policy) *tile_policy = b->tc_policy;
     return FMM2D_OK;
 }
 

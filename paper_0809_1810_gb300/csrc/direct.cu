@@ -192,7 +192,8 @@ batch_direct_kernel(const BatchInst* __restrict__ inst, const int64_t* __restric
         if (!near) {
             const int lj = leaf_index(x, b.g.x0, b.g.scale, top);
             const int mj = leaf_index(y, b.g.y0, b.g.scale, top);
-            near = abs(lj - li) <= 1 && abs(mj - mi) <= 1;
+            near = (abs(lj - li) <= 1 && abs(mj - mi) <= 1) ||
+                   (b.g.L >= 2 && r2 < b.g.cutoff * b.g.cutoff);  // Sec. 4.1 cutoff
         }
         const double f = near ? -expm1(-r2 * inv2s2) / r2 : 1.0 / r2;
         const double w = (double)gamma[j] * f;

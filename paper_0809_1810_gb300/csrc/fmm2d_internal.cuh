@@ -230,7 +230,7 @@ cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
                              const int32_t* leaf_inst, uint32_t ntotal, uint32_t* counter,
                              int ctas_per_sm, const void* particles, const uint32_t* skeys,
                              const uint32_t* leaf_start, const float* le, const float* l2l16,
-                             const float* l2l32, float* uv, cudaStream_t s);
+                             const float* l2l32, float* uv, bool cut, cudaStream_t s);
 cudaError_t launch_batch_direct(const BatchInst* inst, const int64_t* dev_offsets, int count,
                                 int kernel, const float* xy, const float* gamma, int64_t s_count,
                                 const int64_t* targets, double* uv_ref, int* status,
@@ -267,13 +267,43 @@ struct M2LTcConfig {
 // returns FMM2D_TIMEOUT instead of holding the GPU.
 constexpr uint32_t kSpinDefault = 1u << 26;
 cudaError_t m2l_tc_configure();
-// Host-side plan of the tiles and shared memory (no device work).
+// Host-side plan of the tiles and shared memory (no device work); tiles_host
+// (optional) receives two int4 records per tile.
 M2LTcConfig m2l_tc_plan(const Geometry& g, int4* tiles_host);
 // Tensor maps, tile list upload and the operator image (FP64 tables split
 // into TF32 hi/lo, laid out as the kernel's shared-memory stages).
 cudaError_t m2l_tc_prepare(const Geometry& g, const M2LTcConfig& cfg, const double* m2l64,
                            float* me_hi, float* me_lo, float* bimg, M2LTcMaps* maps,
                            cudaStream_t s);
+// The tensor-core M2L of a batch: one class per Pk (p rounded up to 4) over
+// every instance of the batch with that Pk and L >= 2.  Its multipole hi/lo
+// parts are stacked per level over the instances deep enough (an instance
+// slot dimension in the level's tensor map), so one launch serves them all.
+struct M2LTcBatchClass {
+    int Pk = 0, P = 0;
+    M2LTcConfig cfg{};
+    M2LTcMaps* maps = nullptr;
+    void* ws = nullptr;          // one device allocation for everything below
+    int4* tiles = nullptr;       // two records per tile
+    float* hi = nullptr;
+    float* lo = nullptr;
+    float* bimg = nullptr;
+    int32_t* inst = nullptr;     // the class's instances
+    int64_t* box_prefix = nullptr;  // prefix of their box counts
+    int64_t* dst_base = nullptr;    // per instance and level: float4 offset in hi / lo
+    int count = 0;
+    int64_t boxes = 0;
+};
+// ids: the class's instances (L >= 2, Pk = (p + 3) & ~3); m2l64 the FP64
+// M2L table of stride P built for p = P.  `tile_policy` 0: the fewest tiles
+// per level; 1: the widest rows (the autotuner's alternative).
+cudaError_t m2l_tc_batch_create(const BatchInst* host_inst, const int* ids, int nids, int Pk,
+                                int P, const double* m2l64, int b_stages, int tile_policy,
+                                M2LTcBatchClass* out, cudaStream_t s);
+void m2l_tc_batch_destroy(M2LTcBatchClass* c);
+cudaError_t launch_m2l_tc_batch(const M2LTcBatchClass& c, const BatchInst* d_inst,
+                                const float* me, float* le, int* status, uint32_t spin,
+                                cudaStream_t s);
 cudaError_t launch_m2l_tc(const Geometry& g, const M2LTcConfig& cfg, const M2LTcMaps& maps,
                           const int4* tiles, const float* me, float* me_hi, float* me_lo,
                           const float* bimg, float* le, int* status, uint32_t spin,

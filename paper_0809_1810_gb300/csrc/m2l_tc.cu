@@ -50,6 +50,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <vector>
 
 #include "fmm2d_internal.cuh"
 
@@ -117,12 +118,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t phase, uint32_t 
     }
     return false;
 }
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, uint64_t* bar) {
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint64_t* bar) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
         : "memory");
 }
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
@@ -192,11 +193,15 @@ __host__ __device__ inline void parent_offset(int d, int* dx, int* dy) {
 }
 
 struct M2LTcArgs {
-    const int4* tiles;  // (level, X0, Y0, tw | th << 8) per CTA
+    // two records per CTA: (level, X0, Y0, tw | th << 8) and (slot, LE offset
+    // low, high word, p): the instance slot of the level's halo map, the
+    // first real of the level's local expansions in `le`, and the instance's
+    // expansion terms (local-expansion coefficients from p up are stored as
+    // zero, as an operator built for that p gives them)
+    const int4* tiles;
     const float* bimg;  // operator stages
     float* le;
     int* status;
-    int64_t level_base[kMaxL + 2];
     int P;           // terms per box in the expansion arrays
     int halo_bytes;  // one halo slot (hi or lo part)
     int b_stages;    // operator slots
@@ -221,6 +226,53 @@ m2l_tc_split_kernel(const float* __restrict__ me, float4* __restrict__ hi,
         const int64_t out0 = g.level_base[l] * KG + (plane * KG * G) * G + rem;
         for (int kg = 0; kg < KG; ++kg) {
             const float4 v = src[kg];
+            float4 h, o;
+            h.x = tf32_rna(v.x);
+            h.y = tf32_rna(v.y);
+            h.z = tf32_rna(v.z);
+            h.w = tf32_rna(v.w);
+            o.x = tf32_rna(v.x - h.x);
+            o.y = tf32_rna(v.y - h.y);
+            o.z = tf32_rna(v.z - h.z);
+            o.w = tf32_rna(v.w - h.w);
+            const int64_t at = out0 + (int64_t)kg * G * G;
+            hi[at] = h;
+            lo[at] = o;
+        }
+    }
+}
+
+// The batch form: box r of class instance j (instance inst[j]) goes to its
+// instance slot's block of the level's stacked arrays, dst_base[j][level].
+__global__ void __launch_bounds__(256)
+m2l_tc_split_batch_kernel(const BatchInst* __restrict__ insts, const int32_t* __restrict__ ids,
+                          const int64_t* __restrict__ prefix, const int64_t* __restrict__ dst_base,
+                          int count, int64_t boxes, int Pk, const float* __restrict__ me,
+                          float4* __restrict__ hi, float4* __restrict__ lo) {
+    const int KG = Pk / 2;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < boxes;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        int lo_j = 0, hi_j = count;  // prefix[lo_j] <= b < prefix[hi_j]
+        while (hi_j - lo_j > 1) {
+            const int mid = (lo_j + hi_j) >> 1;
+            if (prefix[mid] <= b) lo_j = mid;
+            else hi_j = mid;
+        }
+        const BatchInst& in = insts[ids[lo_j]];
+        const int64_t r = b - prefix[lo_j];
+        const int l = slot_level(in.g.level_base, in.g.L, r);
+        const int64_t G = (int64_t)1 << (l - 1);
+        const int64_t q = r - in.g.level_base[l];
+        const int64_t plane = q / (G * G), rem = q % (G * G);
+        const float4* src = reinterpret_cast<const float4*>(me + in.exp_off + r * (2 * in.g.P));
+        const int64_t out0 = dst_base[(int64_t)lo_j * (kMaxL + 1) + l] + (plane * KG * G) * G + rem;
+        const int nr = 2 * in.g.p;  // reals of the instance's p terms; the rest read as zero
+        for (int kg = 0; kg < KG; ++kg) {
+            float4 v = src[kg];
+            if (4 * kg >= nr) v.x = 0.f;
+            if (4 * kg + 1 >= nr) v.y = 0.f;
+            if (4 * kg + 2 >= nr) v.z = 0.f;
+            if (4 * kg + 3 >= nr) v.w = 0.f;
             float4 h, o;
             h.x = tf32_rna(v.x);
             h.y = tf32_rna(v.y);
@@ -308,9 +360,11 @@ m2l_parent_tc_kernel(const __grid_constant__ M2LTcMaps maps, const M2LTcArgs a) 
     const uint32_t s_b = s_halo + 2u * kHaloSlots * (uint32_t)a.halo_bytes;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int4 tile = a.tiles[blockIdx.x];
+    const int4 tile = a.tiles[2 * blockIdx.x], tile2 = a.tiles[2 * blockIdx.x + 1];
     const int level = tile.x, X0 = tile.y, Y0 = tile.z;
     const int tw = tile.w & 0xFF, th = (tile.w >> 8) & 0xFF;
+    const int slot = tile2.x, p_terms = tile2.w;
+    const int64_t le_off = (int64_t)(uint32_t)tile2.y | ((int64_t)(uint32_t)tile2.z << 32);
     const int Hw = tw + 2, Hh = th + 2;
     const int G = 1 << (level - 1);
     const uint32_t box_bytes = 32u * (uint32_t)(Hw * Hh);  // 2 k-groups x Hw x Hh x 16 B
@@ -361,10 +415,10 @@ m2l_parent_tc_kernel(const __grid_constant__ M2LTcMaps maps, const M2LTcArgs a) 
                 const uint32_t dst = s_halo + (uint32_t)(2 * hs) * (uint32_t)a.halo_bytes;
                 // the halo's columns X0 - 1 .. X0 + tw as one run of 4 Hw reals
                 // (a multiple of 4: 16-byte aligned; -4 reads the zero fill)
-                tma_load_3d(dst, &maps.me_hi[level], 4 * (X0 - 1), Y0 - 1, sp * KG + 2 * kc,
-                            &halo_full[hs]);
-                tma_load_3d(dst + (uint32_t)a.halo_bytes, &maps.me_lo[level], 4 * (X0 - 1),
-                            Y0 - 1, sp * KG + 2 * kc, &halo_full[hs]);
+                tma_load_4d(dst, &maps.me_hi[level], 4 * (X0 - 1), Y0 - 1, sp * KG + 2 * kc,
+                            slot, &halo_full[hs]);
+                tma_load_4d(dst + (uint32_t)a.halo_bytes, &maps.me_lo[level], 4 * (X0 - 1),
+                            Y0 - 1, sp * KG + 2 * kc, slot, &halo_full[hs]);
                 ++h_issued;
                 for (int j = 0; j < kSPH; ++j) {
                     const int b = h * kSPH + j, bs = b % a.b_stages;
@@ -505,12 +559,15 @@ m2l_parent_tc_kernel(const __grid_constant__ M2LTcMaps maps, const M2LTcArgs a) 
                 for (int t2 = 0; t2 < 2; ++t2) {
                     const int tp = 2 * hh + t2;  // target child (parity plane)
                     float4* d4 = reinterpret_cast<float4*>(
-                        a.le + (a.level_base[level] + ((int64_t)(tp * G + Y) * G + X)) * (2 * a.P));
+                        a.le + le_off + ((int64_t)(tp * G + Y) * G + X) * (2 * a.P));
+                    const int nr = 2 * p_terms;  // reals kept
 #pragma unroll
-                    for (int j = 0; j < Pk / 2; ++j)
-                        d4[j] = make_float4(sum[t2 * 2 * Pk + 4 * j], sum[t2 * 2 * Pk + 4 * j + 1],
-                                            sum[t2 * 2 * Pk + 4 * j + 2],
-                                            sum[t2 * 2 * Pk + 4 * j + 3]);
+                    for (int j = 0; j < Pk / 2; ++j) {
+                        const float* v = &sum[t2 * 2 * Pk + 4 * j];
+                        d4[j] = make_float4(4 * j < nr ? v[0] : 0.f, 4 * j + 1 < nr ? v[1] : 0.f,
+                                            4 * j + 2 < nr ? v[2] : 0.f,
+                                            4 * j + 3 < nr ? v[3] : 0.f);
+                    }
                     for (int j = Pk / 2; j < a.P / 2; ++j) d4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
@@ -544,7 +601,13 @@ EncodeTiledFn encoder() {
 // Tile of target parents at a level of G x G parents: the tw x th rectangle
 // (th (tw + 2) <= 128 MMA rows, tw <= 62) with the fewest tiles, then the
 // smallest halo.
-void choose_tile(int G, int* tw_out, int* th_out) {
+// Policy 1 (an autotuner candidate) takes the widest rows instead.
+void choose_tile(int G, int* tw_out, int* th_out, int policy = 0) {
+    if (policy == 1) {
+        *tw_out = std::min(G, 62);
+        *th_out = std::min(G, 128 / (*tw_out + 2));
+        return;
+    }
     long best = LONG_MAX, best_halo = LONG_MAX;
     int btw = 1, bth = 1;
     for (int tw = 1; tw <= G && tw <= 62; ++tw) {  // box inner extent 4 (tw + 2) <= 256
@@ -579,32 +642,50 @@ cudaError_t configure_pk() {
 
 }  // namespace
 
+namespace {
+// Shared memory of a configuration whose largest halo needs `halo_rows`
+// 16-byte rows per slot: the halo ring, then as many operator stages as fit
+// (at most `want` when want > 0).
+void finish_config(M2LTcConfig* c, int halo_rows, int want) {
+    const int N = 8 * c->Pk;
+    c->halo_bytes = ((halo_rows * 16) + 127) & ~127;
+    const int stage = 64 * N * offsets_per_stage(N);
+    const int budget = kSmemLimit - 1024 - 2 * kHaloSlots * c->halo_bytes;
+    c->b_stages = std::min(kMaxBStages, budget / stage);
+    if (want > 0) c->b_stages = std::min(c->b_stages, want);
+    c->smem = 2 * kHaloSlots * c->halo_bytes + c->b_stages * stage + 1024;
+    c->b_floats = (int64_t)4 * (c->Pk / 4) * 8 * 16 * N;
+}
+// rows one halo slot must hold for tiles tw x th: the TMA box (2 k-groups)
+// and the furthest row an MMA reads (k-group 1, offset (1, 1), row 127)
+int halo_rows_of(int tw, int th) {
+    const int Hw = tw + 2, Hh = th + 2;
+    return std::max(2 * Hw * Hh, Hw * Hh + 2 * Hw + 130);
+}
+}  // namespace
+
 M2LTcConfig m2l_tc_plan(const Geometry& g, int4* tiles_host) {
     M2LTcConfig c{};
     c.Pk = (g.p + 3) & ~3;
-    const int N = 8 * c.Pk;
     int count = 0, halo_rows = 0;
     for (int l = 2; l <= g.L; ++l) {
         const int G = 1 << (l - 1);
         int tw, th;
         choose_tile(G, &tw, &th);
-        const int Hw = tw + 2, Hh = th + 2;
-        // rows one slot must hold: the TMA box (2 k-groups) and the furthest
-        // row an MMA reads (k-group 1, offset (1, 1), row 127)
-        halo_rows = std::max(halo_rows, std::max(2 * Hw * Hh, Hw * Hh + 2 * Hw + 130));
+        halo_rows = std::max(halo_rows, halo_rows_of(tw, th));
+        const int64_t le_off = g.level_base[l] * 2 * g.P;
         for (int y = 0; y < G; y += th)
             for (int x = 0; x < G; x += tw) {
-                if (tiles_host) tiles_host[count] = make_int4(l, x, y, tw | (th << 8));
+                if (tiles_host) {
+                    tiles_host[2 * count] = make_int4(l, x, y, tw | (th << 8));
+                    tiles_host[2 * count + 1] =
+                        make_int4(0, (int)(uint32_t)le_off, (int)(uint32_t)(le_off >> 32), g.p);
+                }
                 ++count;
             }
     }
     c.ntiles = count;
-    c.halo_bytes = ((halo_rows * 16) + 127) & ~127;
-    const int stage = 64 * N * offsets_per_stage(N);
-    const int budget = kSmemLimit - 1024 - 2 * kHaloSlots * c.halo_bytes;
-    c.b_stages = std::min(kMaxBStages, budget / stage);
-    c.smem = 2 * kHaloSlots * c.halo_bytes + c.b_stages * stage + 1024;
-    c.b_floats = (int64_t)4 * (c.Pk / 4) * 8 * 16 * N;
+    finish_config(&c, halo_rows, 0);
     return c;
 }
 
@@ -636,13 +717,13 @@ cudaError_t m2l_tc_prepare(const Geometry& g, const M2LTcConfig& cfg, const doub
         // a row of the level's plane (G columns x 4 reals) is one contiguous
         // run: the box's inner extent is the halo's 4 Hw reals (16 Hw bytes),
         // landing as [k-group][row][column][4 reals] like the 4-D view would
-        const cuuint64_t dims[3] = {4 * G, G, (cuuint64_t)4 * KG};
-        const cuuint64_t strides[2] = {16 * G, 16 * G * G};
-        const cuuint32_t box[3] = {(cuuint32_t)(4 * (tw + 2)), (cuuint32_t)(th + 2), 2};
+        const cuuint64_t dims[4] = {4 * G, G, (cuuint64_t)4 * KG, 1};
+        const cuuint64_t strides[3] = {16 * G, 16 * G * G, 16 * G * G * 4 * KG};
+        const cuuint32_t box[4] = {(cuuint32_t)(4 * (tw + 2)), (cuuint32_t)(th + 2), 2, 1};
         for (int which = 0; which < 2; ++which) {
             float* base = (which ? me_lo : me_hi) + g.level_base[l] * 2 * cfg.Pk;
             CUresult r = enc(which ? &maps->me_lo[l] : &maps->me_hi[l],
-                             CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                             CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -668,7 +749,6 @@ cudaError_t launch_m2l_tc(const Geometry& g, const M2LTcConfig& cfg, const M2LTc
     a.bimg = bimg;
     a.le = le;
     a.status = status;
-    for (int l = 0; l <= kMaxL + 1; ++l) a.level_base[l] = g.level_base[l];
     a.P = g.P;
     a.halo_bytes = cfg.halo_bytes;
     a.b_stages = cfg.b_stages;
@@ -682,6 +762,168 @@ cudaError_t launch_m2l_tc(const Geometry& g, const M2LTcConfig& cfg, const M2LTc
         case 6: return launch_pk<6>(cfg, maps, a, s);
         case 7: return launch_pk<7>(cfg, maps, a, s);
         case 8: return launch_pk<8>(cfg, maps, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t m2l_tc_batch_create(const BatchInst* host_inst, const int* ids, int nids, int Pk,
+                                int P, const double* m2l64, int b_stages, int tile_policy,
+                                M2LTcBatchClass* out, cudaStream_t s) {
+    EncodeTiledFn enc = encoder();
+    if (!enc) return cudaErrorNotSupported;
+    if (nids < 1 || Pk < 4 || Pk > kMaxP || (Pk & 3)) return cudaErrorInvalidValue;
+    M2LTcBatchClass c;
+    c.Pk = Pk;
+    c.P = P;
+    c.count = nids;
+    c.cfg.Pk = Pk;
+    const int KG = Pk / 2;
+    int maxL = 0;
+    for (int j = 0; j < nids; ++j) maxL = std::max(maxL, host_inst[ids[j]].g.L);
+    // stacked layout: level l holds one block of KG x 4^l float4 per instance
+    // with L >= l, in class order
+    std::vector<int> nslot(kMaxL + 1, 0);
+    for (int l = 2; l <= maxL; ++l)
+        for (int j = 0; j < nids; ++j) nslot[l] += host_inst[ids[j]].g.L >= l;
+    std::vector<int64_t> lvl(kMaxL + 2, 0);
+    for (int l = 2; l <= maxL; ++l) lvl[l + 1] = lvl[l] + (int64_t)nslot[l] * KG * (1ll << (2 * l));
+    const int64_t total4 = lvl[maxL + 1];
+    std::vector<int64_t> dst((size_t)nids * (kMaxL + 1), 0), prefix(nids + 1, 0);
+    std::vector<int> next(kMaxL + 1, 0);
+    std::vector<std::vector<int>> slot_inst(kMaxL + 1);
+    for (int j = 0; j < nids; ++j) {
+        const BatchInst& in = host_inst[ids[j]];
+        prefix[j + 1] = prefix[j] + in.g.nboxes;
+        for (int l = 2; l <= in.g.L; ++l) {
+            dst[(size_t)j * (kMaxL + 1) + l] = lvl[l] + (int64_t)next[l] * KG * (1ll << (2 * l));
+            slot_inst[l].push_back(ids[j]);
+            ++next[l];
+        }
+    }
+    c.boxes = prefix[nids];
+    std::vector<int4> tiles;
+    int halo_rows = 0;
+    std::vector<int> tws(kMaxL + 1, 0), ths(kMaxL + 1, 0);
+    for (int l = 2; l <= maxL; ++l) {
+        if (!nslot[l]) continue;
+        const int G = 1 << (l - 1);
+        choose_tile(G, &tws[l], &ths[l], tile_policy);
+        halo_rows = std::max(halo_rows, halo_rows_of(tws[l], ths[l]));
+        for (int sl = 0; sl < nslot[l]; ++sl) {
+            const BatchInst& in = host_inst[slot_inst[l][sl]];
+            const int64_t le_off = in.exp_off + in.g.level_base[l] * 2 * P;
+            for (int y = 0; y < G; y += ths[l])
+                for (int x = 0; x < G; x += tws[l]) {
+                    tiles.push_back(make_int4(l, x, y, tws[l] | (ths[l] << 8)));
+                    tiles.push_back(make_int4(sl, (int)(uint32_t)le_off,
+                                              (int)(uint32_t)(le_off >> 32), in.g.p));
+                }
+        }
+    }
+    c.cfg.ntiles = (int)(tiles.size() / 2);
+    finish_config(&c.cfg, halo_rows, b_stages);
+    if (c.cfg.b_stages < 2) return cudaErrorInvalidValue;
+    auto a256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const size_t sz[] = {a256(tiles.size() * sizeof(int4)), a256((size_t)total4 * 16),
+                         a256((size_t)total4 * 16), a256((size_t)c.cfg.b_floats * 4),
+                         a256(4 * (size_t)nids), a256(8 * (size_t)(nids + 1)),
+                         a256(dst.size() * 8)};
+    size_t bytes = 0;
+    for (size_t v : sz) bytes += v;
+    cudaError_t e = cudaMalloc(&c.ws, bytes);
+    if (e != cudaSuccess) return e;
+    char* q = static_cast<char*>(c.ws);
+    c.tiles = (int4*)q;
+    q += sz[0];
+    c.hi = (float*)q;
+    q += sz[1];
+    c.lo = (float*)q;
+    q += sz[2];
+    c.bimg = (float*)q;
+    q += sz[3];
+    c.inst = (int32_t*)q;
+    q += sz[4];
+    c.box_prefix = (int64_t*)q;
+    q += sz[5];
+    c.dst_base = (int64_t*)q;
+    e = cudaMemcpyAsync(c.tiles, tiles.data(), tiles.size() * sizeof(int4),
+                        cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c.inst, ids, 4 * (size_t)nids, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c.box_prefix, prefix.data(), 8 * (size_t)(nids + 1),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c.dst_base, dst.data(), dst.size() * 8, cudaMemcpyHostToDevice, s);
+    c.maps = new M2LTcMaps();
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int l = 2; l <= maxL && e == cudaSuccess; ++l) {
+        if (!nslot[l]) continue;
+        const cuuint64_t G = 1ull << (l - 1);
+        const cuuint64_t dims[4] = {4 * G, G, (cuuint64_t)4 * KG, (cuuint64_t)nslot[l]};
+        const cuuint64_t strides[3] = {16 * G, 16 * G * G, 16 * G * G * 4 * KG};
+        const cuuint32_t box[4] = {(cuuint32_t)(4 * (tws[l] + 2)), (cuuint32_t)(ths[l] + 2), 2,
+                                   1};
+        for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
+            float* base = (which ? c.lo : c.hi) + lvl[l] * 4;
+            CUresult r = enc(which ? &c.maps->me_lo[l] : &c.maps->me_hi[l],
+                             CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) e = cudaErrorInvalidValue;
+        }
+    }
+    if (e == cudaSuccess) {
+        const int64_t entries = c.cfg.b_floats / 2;
+        const int blocks = (int)std::min<int64_t>((entries + 255) / 256, 8192);
+        // the full operator (p = Pk): coefficients from the instance's p up
+        // are zero in its multipoles and masked in its local expansions
+        m2l_tc_bimg_kernel<<<blocks, 256, 0, s>>>(m2l64, P, Pk, Pk, c.bimg);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        m2l_tc_batch_destroy(&c);
+        return e;
+    }
+    *out = c;
+    return cudaSuccess;
+}
+
+void m2l_tc_batch_destroy(M2LTcBatchClass* c) {
+    if (c->ws) cudaFree(c->ws);
+    delete c->maps;
+    *c = M2LTcBatchClass();
+}
+
+cudaError_t launch_m2l_tc_batch(const M2LTcBatchClass& c, const BatchInst* d_inst,
+                                const float* me, float* le, int* status, uint32_t spin,
+                                cudaStream_t s) {
+    if (c.count == 0 || c.cfg.ntiles == 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>((c.boxes + 255) / 256, 4096);
+    m2l_tc_split_batch_kernel<<<blocks, 256, 0, s>>>(d_inst, c.inst, c.box_prefix, c.dst_base,
+                                                      c.count, c.boxes, c.Pk, me,
+                                                      reinterpret_cast<float4*>(c.hi),
+                                                      reinterpret_cast<float4*>(c.lo));
+    M2LTcArgs a{};
+    a.tiles = c.tiles;
+    a.bimg = c.bimg;
+    a.le = le;
+    a.status = status;
+    a.P = c.P;
+    a.halo_bytes = c.cfg.halo_bytes;
+    a.b_stages = c.cfg.b_stages;
+    a.spin = spin ? spin : kSpinDefault;
+    switch (c.Pk / 4) {
+        case 1: return launch_pk<1>(c.cfg, *c.maps, a, s);
+        case 2: return launch_pk<2>(c.cfg, *c.maps, a, s);
+        case 3: return launch_pk<3>(c.cfg, *c.maps, a, s);
+        case 4: return launch_pk<4>(c.cfg, *c.maps, a, s);
+        case 5: return launch_pk<5>(c.cfg, *c.maps, a, s);
+        case 6: return launch_pk<6>(c.cfg, *c.maps, a, s);
+        case 7: return launch_pk<7>(c.cfg, *c.maps, a, s);
+        case 8: return launch_pk<8>(c.cfg, *c.maps, a, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -899,10 +899,15 @@ p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ s
 // Per-instance near-field constants of a batched evaluation.
 struct NearInst {
     float sc, kvel, kzeta, inv_s, half_leaf;
+    float qa, band_a2;   // the instance's cutoff of Sec. 4.1 (0: none)
+    uint32_t ring_mask;  // its ring leaves nearer than a
 };
 
 // Batched and persistent: warps pull work items over the global sorted order
-// (all instances, packed) from a work counter.
+// (all instances, packed) from a work counter.  kCut compiles in the cutoff
+// ring of Sec. 4.1 for batches where some instance has a cutoff (the others
+// have an empty ring and skip it).
+template <bool kCut>
 __global__ void __launch_bounds__(kLeafWarps * 32, 6)
 p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skeys,
                  const uint32_t* __restrict__ leaf_start, const BatchInst* __restrict__ inst,
@@ -911,7 +916,7 @@ p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ ske
                  const float* __restrict__ le, const float* __restrict__ l2l16,
                  const float* __restrict__ l2l32, float* __restrict__ uv) {
     __shared__ float4 lists[kLeafWarps][kListCap];
-    __shared__ uint32_t ranges[kLeafWarps][20];
+    __shared__ uint32_t ranges[kLeafWarps][kCut ? 52 : 20];
     __shared__ float2 leaf_le[kLeafWarps][kMaxP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
@@ -929,9 +934,13 @@ p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ ske
             nm.kzeta = ni.kzeta;
             nm.inv_s = ni.inv_s;
             nm.half_leaf = ni.half_leaf;
-            p2p_chunk_f32<false>(sp, leaf_start, b.leaf_base, gleaf - b.leaf_base, a, e, b.g,
-                                 nm, le + b.exp_off, b.g.P <= 16 ? l2l16 : l2l32, uv,
-                                 lists[warp], ranges[warp], leaf_le[warp]);
+            nm.qa = ni.qa;
+            nm.band_a2 = ni.band_a2;
+            nm.ring_mask = ni.ring_mask;
+            p2p_chunk_f32<kCut, kCut ? 2 : 4>(sp, leaf_start, b.leaf_base, gleaf - b.leaf_base, a,
+                                              e, b.g, nm, le + b.exp_off,
+                                              b.g.P <= 16 ? l2l16 : l2l32, uv, lists[warp],
+                                              ranges[warp], leaf_le[warp]);
         });
     }
 }
@@ -1199,7 +1208,8 @@ cudaError_t batch_near_fill(const BatchInst* host_inst, int count, void* dev_nea
         bool oki;
         NearF32v3 nm = near_constants(host_inst[i].sigma, host_inst[i].g, &oki);
         ok = ok && oki;
-        h[i] = NearInst{nm.sc, nm.kvel, nm.kzeta, nm.inv_s, nm.half_leaf};
+        h[i] = NearInst{nm.sc,        nm.kvel, nm.kzeta,  nm.inv_s,
+                        nm.half_leaf, nm.qa,   nm.band_a2, nm.ring_mask};
     }
     cudaError_t e = ok ? cudaMemcpyAsync(dev_near, h, sizeof(NearInst) * count,
                                          cudaMemcpyHostToDevice, s)
@@ -1213,7 +1223,7 @@ cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
                              const int32_t* leaf_inst, uint32_t ntotal, uint32_t* counter,
                              int ctas_per_sm, const void* particles, const uint32_t* skeys,
                              const uint32_t* leaf_start, const float* le, const float* l2l16,
-                             const float* l2l32, float* uv, cudaStream_t s) {
+                             const float* l2l32, float* uv, bool cut, cudaStream_t s) {
     if (ntotal == 0) return cudaSuccess;
     Geometry g1{};
     g1.W = 2.0;
@@ -1227,11 +1237,18 @@ cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
     unsigned blocks = (unsigned)(sms * ctas_per_sm);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    p2p_batch_kernel<<<blocks, kLeafWarps * 32, 0, s>>>(
-        reinterpret_cast<const float4*>(particles), skeys, leaf_start, inst,
-        static_cast<const NearInst*>(near_inst), leaf_inst,
-        work_split(ntotal, (uint64_t)blocks * kLeafWarps), counter,
-        shared_nm, le, l2l16, l2l32, uv);
+    if (cut)
+        p2p_batch_kernel<true><<<blocks, kLeafWarps * 32, 0, s>>>(
+            reinterpret_cast<const float4*>(particles), skeys, leaf_start, inst,
+            static_cast<const NearInst*>(near_inst), leaf_inst,
+            work_split(ntotal, (uint64_t)blocks * kLeafWarps), counter, shared_nm, le, l2l16,
+            l2l32, uv);
+    else
+        p2p_batch_kernel<false><<<blocks, kLeafWarps * 32, 0, s>>>(
+            reinterpret_cast<const float4*>(particles), skeys, leaf_start, inst,
+            static_cast<const NearInst*>(near_inst), leaf_inst,
+            work_split(ntotal, (uint64_t)blocks * kLeafWarps), counter, shared_nm, le, l2l16,
+            l2l32, uv);
     return cudaGetLastError();
 }
 

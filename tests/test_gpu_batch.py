@@ -193,3 +193,110 @@ def test_sweep_512_instances_against_oracle():
         got = uvn[offs[k]:offs[k + 1]]
         err = np.abs(got - ref).max() / np.abs(ref).max()
         assert err <= FP32_TOL, (k, w.n, w.p, w.L, err)
+
+
+def _cut(w, tol=1e-6):
+    """The Sec. 4.1 cutoff for the tolerance where the instance's leaves are
+    narrower than it (at most two leaf widths, 0 below L = 2)."""
+    from paper_0809_1810_gb300 import cutoff_for
+
+    return cutoff_for(w.sigma, w.root[2] / 2 ** w.L, tol) if w.L >= 2 else 0.0
+
+
+def _batch_p(ws, precision, cut=True):
+    from paper_0809_1810_gb300 import BatchPlan
+
+    return BatchPlan([{"n": w.n, "p": w.p, "L": w.L, "sigma": w.sigma, "root": w.root,
+                       "cutoff": _cut(w) if cut else 0.0} for w in ws], precision=precision)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_tc"])
+def test_batch_with_cutoff_equals_single_plans(prec):
+    """Batched instances with the Sec. 4.1 cutoff (where their leaves are
+    narrower than it) and, for FP32_TC, the tensor-core M2L per class of p
+    rounded up to 4: bit for bit the single plans of the same settings."""
+    from paper_0809_1810_gb300 import Plan
+
+    ws = _mixed_instances()
+    assert sum(_cut(w) > 0 for w in ws) >= 3  # several instances take the cutoff
+    xy, g = _pack(ws)
+    with _batch_p(ws, prec) as bp:
+        uv = bp.velocity(xy, g)
+        uv2 = bp.velocity(xy, g)
+        bp.check()
+        info = bp.info()
+    assert torch.equal(uv, uv2)
+    if prec == "fp32_tc":
+        assert info["tc_classes"] >= 4 and info["tc_tiles"] > 0
+    off = 0
+    for w in ws:
+        if w.n:
+            with Plan(w.p, w.L, w.sigma, prec, root=w.root, max_n=w.n, cutoff=_cut(w)) as plan:
+                xyi = torch.tensor(np.stack([w.x, w.y], 1), device="cuda")
+                gi = torch.tensor(w.gamma, device="cuda")
+                single = plan.velocity(xyi, gi, check=True)
+            assert torch.equal(uv[off:off + w.n], single), (w.name, w.p, w.L, _cut(w))
+        off += w.n
+
+
+def test_batch_tc_autotune_keeps_results():
+    ws = _mixed_instances()
+    xy, g = _pack(ws)
+    with _batch_p(ws, "fp32_tc") as bp:
+        a = bp.velocity(xy, g).clone()
+        out = torch.empty_like(a)
+        info = bp.autotune(xy, g, out)
+        b = bp.velocity(xy, g)
+        bp.check()
+    assert info["tc_tile_policy"] in (0, 1) and info["tc_b_stages"] >= 2
+    assert torch.equal(a, out) and torch.equal(a, b)
+
+
+def test_batch_cutoff_yardstick():
+    """The batched FMM-limit yardstick honours each instance's cutoff."""
+    ws = _mixed_instances()
+    xy, g = _pack(ws)
+    rng = np.random.default_rng(13)
+    off, targets, want = 0, [], []
+    for w in ws:
+        if w.n:
+            t = np.sort(rng.choice(w.n, size=min(30, w.n), replace=False))
+            targets.append(t + off)
+            want.append(oracle.hybrid(w.x, w.y, w.gamma, w.sigma, w.root, w.L, targets=t,
+                                      a=_cut(w)))
+        off += w.n
+    targets = np.concatenate(targets)
+    want = np.concatenate(want)
+    with _batch_p(ws, "fp32_tc") as bp:
+        got = bp.direct_sampled(xy, g, torch.tensor(targets, device="cuda"), kernel=1)
+        bp.check()
+    np.testing.assert_allclose(got.cpu().numpy(), want, rtol=0, atol=1e-13 * np.abs(want).max())
+
+
+def test_sweep_512_tc_with_cutoff_against_oracle():
+    """The 512-instance sweep as FP32_TC with each instance's cutoff: sampled
+    instances against the oracle's cut FMM within 1e-6."""
+    specs = W.batch_instances(512)
+    ws = [W.make_instance(s) for s in specs]
+    xy, g = _pack(ws)
+    with _batch_p(ws, "fp32_tc") as bp:
+        uv = bp.velocity(xy, g)
+        bp.check()
+        uvn = uv.double().cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum([w.n for w in ws])])
+    rng = np.random.default_rng(2)
+    cut_seen = 0
+    # FP32 parity with a cutoff needs the correction's jump at r = a,
+    # exp(-a^2 / 2 sigma^2) of a pair's value, far below the tolerance: a pair
+    # within rounding of r = a is decided either way in FP32 and in FP64
+    # (a >= 4.4 sigma, as in the single-plan cutoff tests)
+    ok = [k for k, w in enumerate(ws) if _cut(w) == 0.0 or _cut(w) >= 4.4 * w.sigma]
+    for k in rng.choice(ok, size=8, replace=False):
+        w = ws[k]
+        a = _cut(w)
+        cut_seen += a > 0
+        ref = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.p, w.L, w.root, a=a)
+        got = uvn[offs[k]:offs[k + 1]]
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err <= FP32_TOL, (k, w.n, w.p, w.L, a / w.sigma, err)
+    assert cut_seen > 0
