@@ -93,7 +93,7 @@ def m2l_pairs(L):
     return total
 
 
-def m2l_tiles(L):
+def m2l_tiles(L, policy=0):
     """Tiles (CTAs) of the tensor-core M2L over levels 2..L: per level of G x G
     target parents, the tw x th rectangle (th (tw + 2) <= 128 MMA rows,
     tw <= 62) with the fewest tiles, then the smallest halo -- the choice the
@@ -101,6 +101,11 @@ def m2l_tiles(L):
     total = 0
     for lev in range(2, L + 1):
         G = 1 << (lev - 1)
+        if policy == 1:  # the widest rows
+            tw = min(G, 62)
+            th = min(G, 128 // (tw + 2))
+            total += -(-G // tw) * -(-G // th)
+            continue
         best = None
         for tw in range(1, min(G, 62) + 1):
             th = min(G, 128 // (tw + 2))
@@ -113,11 +118,11 @@ def m2l_tiles(L):
     return total
 
 
-def m2l_executed_flops(p, L):
+def m2l_executed_flops(p, L, policy=0):
     """Tensor flops the 3xTF32 M2L issues: per tile 8 Pk operator stages of 3
     MMAs, each 2 x 128 x N x 8 with N = 8 Pk (Pk = p rounded up to 4)."""
     pk = (p + 3) // 4 * 4
-    return m2l_tiles(L) * 8 * pk * 3 * 2.0 * 128 * 8 * pk * 8
+    return m2l_tiles(L, policy) * 8 * pk * 3 * 2.0 * 128 * 8 * pk * 8
 
 
 def tf32_peak_tflops(peaks):
@@ -399,17 +404,45 @@ def run_reference(args):
     }))
 
 
+def _leaf_grid_pairs(counts, L):
+    """Pairs of the 3x3 near field of one quadtree, from its leaf counts in
+    Morton order: sum over leaves of n_leaf n_3x3 minus the self pairs."""
+    nl = 1 << L
+    ks = np.arange(nl * nl, dtype=np.uint32)
+    ixs = np.zeros(nl * nl, dtype=np.int64)
+    iys = np.zeros(nl * nl, dtype=np.int64)
+    for b in range(L):
+        ixs |= ((ks >> (2 * b)) & 1).astype(np.int64) << b
+        iys |= ((ks >> (2 * b + 1)) & 1).astype(np.int64) << b
+    grid = np.zeros((nl, nl), dtype=np.int64)
+    grid[iys, ixs] = counts
+    padg = np.pad(grid, 1)
+    nb = sum(padg[1 + dy:1 + dy + nl, 1 + dx:1 + dx + nl] for dy in (-1, 0, 1)
+             for dx in (-1, 0, 1))
+    return int((grid * nb).sum()) - int(counts.sum())
+
+
 def run_batch_sweep(torch, dev, flush, rank, pg, steps=10):
     """The 512-instance sweep (N log-uniform in [2^12, 2^17], p in {4..24},
     L in {3..7}, sigma/h in {0.8, 1, 1.5, 2}, half Lamb-Oseen lattices) as one
-    batched graph launch, after the autotuner has chosen launch shapes."""
-    from paper_0809_1810_gb300 import BatchPlan
+    batched graph launch in the FP32_TC form, every instance with the Sec. 4.1
+    cutoff for 1e-6 where its leaves are narrower than it, after the autotuner
+    has chosen launch shapes; per-phase rooflines from one step-by-step run."""
+    import ctypes
+
+    from paper_0809_1810_gb300 import BatchPlan, _native, cutoff_for
 
     specs = W.batch_instances(512, seed=3 + rank)
     ws = [W.make_instance(s) for s in specs]
     xy = torch.tensor(np.concatenate([np.stack([w.x, w.y], 1) for w in ws]), device=dev)
     g = torch.tensor(np.concatenate([w.gamma for w in ws]), device=dev)
-    with BatchPlan([{"n": w.n, "p": w.p, "L": w.L, "sigma": w.sigma} for w in ws]) as bp:
+
+    def cut(w):
+        return cutoff_for(w.sigma, w.root[2] / 2 ** w.L, TOL) if w.L >= 2 else 0.0
+
+    insts = [{"n": w.n, "p": w.p, "L": w.L, "sigma": w.sigma, "root": w.root, "cutoff": cut(w)}
+             for w in ws]
+    with BatchPlan(insts, precision="fp32_tc") as bp:
         uv = torch.empty((bp.n_total, 2), dtype=torch.float32, device=dev)
         tuned = bp.autotune(xy, g, uv)
         for _ in range(3):
@@ -426,13 +459,66 @@ def run_batch_sweep(torch, dev, flush, rank, pg, steps=10):
         ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
         ms = max_over_ranks(pg, ms, torch, dev)
         info = bp.info()
+        phases = [bp.profile(xy, g, uv) for _ in range(3)]
+        ph = {k: float(np.median([q[k] for q in phases])) for k in phases[0]}
+        # accuracy: every instance against the FP64 direct sum at 64 sampled particles
+        offs = np.concatenate([[0], np.cumsum([w.n for w in ws])])
+        t = np.concatenate([o + W.sample_targets(w.n, min(64, w.n), 77 + k)
+                            for k, (w, o) in enumerate(zip(ws, offs[:-1])) if w.n])
+        tt = torch.tensor(t, device=dev)
+        ref = bp.direct_sampled(xy, g, tt, kernel=0)
+        bp.velocity(xy, g, out=uv)
+        stats = bp.error_stats(xy, uv, tt, ref).cpu().numpy()
+        bp.check()
+        # leaf occupancy of every instance for the near-field pair count
+        lib = _native.load()
+        start = torch.empty(info["leaves_total"] + 1, dtype=torch.int32, device=dev)
+        lib.fmm2d_batch_tree_debug(bp._h, None, None, ctypes.c_void_p(start.data_ptr()),
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        torch.cuda.synchronize()
+        start = start.cpu().numpy().astype(np.int64)
     n = int(sum(w.n for w in ws))
+    pairs, lb = 0, 0
+    for w in ws:
+        nl = 1 << (2 * w.L)
+        pairs += _leaf_grid_pairs(np.diff(start[lb:lb + nl + 1]), w.L)
+        lb += nl
+    err = stats[:, 0] / np.maximum(stats[:, 1], 1e-300)
+    peaks, peak_kind = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    near_peak = p2p_peak_pairs_per_s(sm_max)
+    pol = info["tc_tile_policy"]
+    useful = sum(8.0 * w.p * w.p * m2l_pairs(w.L) for w in ws if w.L >= 2)
+    executed = sum(m2l_executed_flops(w.p, w.L, pol) for w in ws if w.L >= 2)
+    tf32 = tf32_peak_tflops(peaks)
     return {"instances": len(ws), "particles": n, "value": n / (ms * 1e-3),
             "unit": "particles/s", "ms_per_batch": ms, "steps": steps,
             "kernels_per_call": info["kernels_per_call"],
+            "precision": "fp32_tc (M2L 3xTF32 on the tensor cores, one launch per class of p "
+                         "rounded up to 4)",
+            "cutoff": "Sec. 4.1 cutoff for 1e-6 on the "
+                      f"{sum(cut(w) > 0 for w in ws)} instances whose leaves are narrower",
             "autotuned": {"p2p_ctas_per_sm": tuned["p2p_ctas_per_sm"],
-                          "m2l_threads": tuned["m2l_threads"]},
-            "precision": "fp32 (M2L on CUDA cores)"}
+                          "tc_b_stages": tuned["tc_b_stages"],
+                          "tc_tile_policy": tuned["tc_tile_policy"],
+                          "tc_classes": tuned["tc_classes"], "tc_tiles": tuned["tc_tiles"]},
+            "phase_ms": ph,
+            "phase_timing": "one evaluation launched step by step with CUDA events between "
+                            "the phases (median of 3)",
+            "roofline_near": {"bound": "alu", "unit": "Gpair/s", "pairs": pairs,
+                              "achieved": pairs / (ph["near"] * 1e-3) / 1e9,
+                              "peak": near_peak / 1e9,
+                              "frac": pairs / (ph["near"] * 1e-3) / near_peak,
+                              "pairs_counted": "3x3-neighbour pairs of every instance exactly "
+                                               "(cutoff-ring pairs not counted)"},
+            "roofline_m2l": {"bound": "tensor", "unit": "TFLOP/s", "peak": tf32,
+                             "achieved": useful / (ph["m2l"] * 1e-3) / 1e12,
+                             "frac": useful / (ph["m2l"] * 1e-3) / 1e12 / tf32,
+                             "executed_frac": executed / (ph["m2l"] * 1e-3) / 1e12 / tf32},
+            "accuracy": {"targets_per_instance": 64,
+                         "median_max_rel_err_vs_fp64_direct": float(np.median(err)),
+                         "instances_within_1e-6": int((err <= TOL).sum()),
+                         "note": "p in {4..24}: the low orders are truncation-limited"}}
 
 
 def run_clustered(torch, dev, flush, steps=5):

@@ -302,6 +302,14 @@ fmm2d_status fmm2d_batch_info(const fmm2d_batch_plan* plan, int64_t* n_total,
                               int64_t* leaves_total, int* kernels_per_call, int* p2p_ctas_per_sm,
                               int* m2l_threads);
 
+/* Tracing: one evaluation of the batch, its steps launched one after another
+ * on the plan's stream with CUDA events between them (not the recorded
+ * graph), then the durations in ms (5 doubles): tree build, P2M and M2M, M2L,
+ * L2L, near field with L2P.  Synchronous; uv_dev receives the velocities. */
+fmm2d_status fmm2d_batch_profile(fmm2d_batch_plan* plan, const float* xy_dev,
+                                 const float* gamma_dev, float* uv_dev, double* ms_host,
+                                 cudaStream_t stream);
+
 /* FP32_TC batches: tensor-core M2L classes (one per p rounded up to 4),
  * their tiles in all, the operator stages in flight (of the first class)
  * and the tile policy the autotuner chose (0: fewest tiles per level, 1:

@@ -351,6 +351,13 @@ class BatchPlan:
                 "precision": self.precision, "tc_classes": cls.value, "tc_tiles": tiles.value,
                 "tc_b_stages": st.value, "tc_tile_policy": pol.value}
 
+    def profile(self, xy, gamma, out, stream=None):
+        """Phase durations (ms) of one evaluation run step by step."""
+        buf = (ctypes.c_double * 5)()
+        _check(self._lib.fmm2d_batch_profile(self._h, _ptr(xy), _ptr(gamma), _ptr(out), buf,
+                                             _stream(stream)), "batch_profile")
+        return dict(zip(("tree", "upward", "m2l", "l2l", "near"), list(buf)))
+
     def direct_sampled(self, xy, gamma, targets, kernel=0, stream=None):
         targets = targets.to(device=xy.device, dtype=torch.int64).contiguous()
         out = torch.empty((targets.shape[0], 2), dtype=torch.float64, device=xy.device)

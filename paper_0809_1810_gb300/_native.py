@@ -88,6 +88,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "fmm2d_batch_error_stats": ([vp, vp, vp, i64, vp, vp, vp, vp, vp], i32),
         "fmm2d_batch_info": ([vp, vp, vp, vp, vp, vp], i32),
         "fmm2d_batch_info_tc": ([vp, vp, vp, vp, vp], i32),
+        "fmm2d_batch_profile": ([vp, vp, vp, vp, vp, vp], i32),
         "fmm2d_batch_tree_debug": ([vp, vp, vp, vp, vp], i32),
         "fmm2d_mlp_last_error": ([], ctypes.c_char_p),
         "fmm2d_mlp_create": ([ctypes.POINTER(vp), i32, ctypes.c_uint64], i32),

@@ -100,13 +100,19 @@ const float* tab_m2l(const fmm2d_batch_plan* b, int c) {
     return b->tab32[c] + (int64_t)8 * P * P * 2;
 }
 
+// The batch's steps on stream s; with `ev` (6 events) each phase boundary is
+// recorded: tree, P2M + M2M, M2L, L2L, near field with L2P.
 cudaError_t enqueue_batch(fmm2d_batch_plan* b, const float* xy, const float* gamma, float* uv,
-                          cudaStream_t s) {
+                          cudaStream_t s, cudaEvent_t* ev = nullptr) {
     cudaError_t e;
 #define BSTEP(x) \
     if ((e = (x)) != cudaSuccess) return e;
+#define BMARK(k) \
+    if (ev) BSTEP(cudaEventRecord(ev[k], s));
+    BMARK(0);
     BSTEP(launch_batch_tree(b->d_keyparams, b->d_offsets, b->count, b->ntotal, b->key_bits,
                             b->nleaf_total, xy, gamma, b->sb, b->particles, s));
+    BMARK(1);
     for (int c = 0; c < 2; ++c)
         if (b->has_class[c])
             BSTEP(launch_batch_p2m(b->d_inst, b->lists[c], c ? 32 : 16, b->particles,
@@ -116,6 +122,7 @@ cudaError_t enqueue_batch(fmm2d_batch_plan* b, const float* xy, const float* gam
             if (b->has_class[c])
                 BSTEP(launch_batch_m2m(b->d_inst, b->lists[c], c ? 32 : 16, l, tab_m2m(b, c),
                                        b->me, s));
+    BMARK(2);
     if (b->precision == FMM2D_FP32_TC) {
         for (const M2LTcBatchClass& c : b->tc)
             BSTEP(launch_m2l_tc_batch(c, b->d_inst, b->me, b->le, b->d_status, 0, s));
@@ -125,16 +132,20 @@ cudaError_t enqueue_batch(fmm2d_batch_plan* b, const float* xy, const float* gam
                 BSTEP(launch_batch_m2l(b->d_inst, b->lists[c], c ? 32 : 16, b->m2l_threads,
                                        tab_m2l(b, c), b->me, b->le, s));
     }
+    BMARK(3);
     for (int l = 3; l <= b->max_L - 1; ++l)
         for (int c = 0; c < 2; ++c)
             if (b->has_class[c])
                 BSTEP(launch_batch_l2l(b->d_inst, b->lists[c], c ? 32 : 16, l, tab_l2l(b, c),
                                        b->le, s));
+    BMARK(4);
     BSTEP(launch_batch_p2p(b->d_inst, b->d_near, b->d_leaf_inst, (uint32_t)b->ntotal,
                            b->d_counter, b->p2p_ctas_per_sm, b->particles,
                            b->sb.keys[sort_passes(b->key_bits) & 1], b->sb.leaf_start, b->le,
                            b->has_class[0] ? tab_l2l(b, 0) : nullptr,
                            b->has_class[1] ? tab_l2l(b, 1) : nullptr, uv, b->any_cutoff, s));
+    BMARK(5);
+#undef BMARK
 #undef BSTEP
     return cudaSuccess;
 }
@@ -612,6 +623,25 @@ fmm2d_status fmm2d_batch_info(const fmm2d_batch_plan* b, int64_t* n_total, int64
     if (kernels_per_call) *kernels_per_call = b->kernel_nodes;
     if (p2p_ctas_per_sm) *p2p_ctas_per_sm = b->p2p_ctas_per_sm;
     if (m2l_threads) *m2l_threads = b->m2l_threads;
+    return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_batch_profile(fmm2d_batch_plan* b, const float* xy, const float* gamma,
+                                 float* uv, double* ms, cudaStream_t stream) {
+    if (!b || !ms) return bfail(FMM2D_INVALID_ARG, "null argument");
+    if (b->ntotal > 0 && (!xy || !gamma || !uv)) return bfail(FMM2D_INVALID_ARG, "null buffer");
+    cudaEvent_t ev[6] = {};
+    for (auto& x : ev) BCK(cudaEventCreate(&x));
+    BCK(cudaStreamSynchronize(stream));
+    cudaError_t e = enqueue_batch(b, xy, gamma, uv, b->cap, ev);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap);
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+        ms[k] = t;
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    BCK(e);
     return FMM2D_OK;
 }
 
