@@ -377,7 +377,7 @@ __device__ __forceinline__ void band_loop_split(const float4* list, uint32_t lo,
 // One shared-memory read of a pair serves 2 T source-target pairs.  Each
 // target sees the same sequence of operations whatever T is, so a target's
 // velocity does not depend on how its rounds were grouped into passes.
-constexpr int kInnerT = 32;
+constexpr int kInnerT = 64;
 
 template <int T>
 struct SumT {
