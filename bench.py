@@ -56,11 +56,11 @@ FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # the fewest operations one near pair of Eq. 6 takes in the 2^-q2 form: on
 # the FP32 pipe the 2 coordinate differences, dx^2, r^2 = fma(dy, dy, dx^2),
 # Gamma (1 - 2^-q2) as one fma, the product with 1/q2 and the 2 fmas of the
-# velocity components (8 lane operations); on the MUFU pipe ex2 and rcp (2).
+# velocity components (8 lane operations); on the MUFU pipe one ex2 and one
+# rcp.
 # Packed FP32 pair instructions (f32x2) do two lane operations per issue, so
 # a pair takes 4 + 2 issue slots.
 P2P_FP32_OPS_PER_PAIR = 8
-P2P_MUFU_OPS_PER_PAIR = 2
 P2P_ISSUE_PER_PAIR = 6
 
 
@@ -180,23 +180,27 @@ def _peaks():
 
 
 # P2P unit rates per SM per clock, measured on GB300 by chains of independent
-# instructions (CUDA events, 152 x 8 CTAs of 256 threads): scalar fma 117 and
-# packed f32x2 fma 120 lane operations per SM per clock (one 128-lane FP32
-# pipe either way: packing halves issue slots, not pipe time), ex2 30 (a
-# 32-lane MUFU pipe, twice the 16 lanes of earlier parts).
+# instructions (CUDA events, the whole GPU): scalar fma 117 and packed f32x2
+# fma 120 lane operations per SM per clock (one 128-lane FP32 pipe either
+# way: packing halves issue slots, not pipe time); on the MUFU pipe
+# ex2.approx 29.7 and rcp.approx 14.9 lanes per SM per clock (the reciprocal
+# runs at half the rate of the exponential).  A pair's ex2 and rcp take
+# 1/30 + 1/15 SM-clocks of the MUFU pipe: 10 pairs per SM per clock.
 FP32_LANES_PER_SM = 128
-MUFU_LANES_PER_SM = 32
+EX2_LANES_PER_SM = 30
+RCP_LANES_PER_SM = 15
 ISSUE_LANES_PER_SM = 128  # 4 schedulers x one warp instruction per cycle
 N_SMS = 152
 
 
 def p2p_peak_pairs_per_s(sm_mhz: float) -> float:
     """ALU roofline of the near-field pair: the least of the FP32 pipe
-    (8 lane operations), the MUFU pipe (2) and instruction issue (6 with
-    packed FP32 pairs) per SM per clock, times SMs and clock: 16 pairs per SM
-    per clock, the FP32 and MUFU pipes together."""
+    (8 lane operations), the MUFU pipe (one ex2 at 30 and one rcp at 15
+    lanes per SM per clock) and instruction issue (6 with packed FP32 pairs)
+    per SM per clock, times SMs and clock: the MUFU pipe binds at 10 pairs
+    per SM per clock."""
     fp32 = FP32_LANES_PER_SM / P2P_FP32_OPS_PER_PAIR
-    mufu = MUFU_LANES_PER_SM / P2P_MUFU_OPS_PER_PAIR
+    mufu = 1.0 / (1.0 / EX2_LANES_PER_SM + 1.0 / RCP_LANES_PER_SM)
     issue = ISSUE_LANES_PER_SM / P2P_ISSUE_PER_PAIR
     return min(fp32, mufu, issue) * N_SMS * sm_mhz * 1e6
 
@@ -849,10 +853,11 @@ def run_ours(args):
         "bound": "alu", "unit": "Gpair/s",
         "achieved": achieved / 1e9, "peak": peak / 1e9, "frac": achieved / peak,
         "peak_source": f"derived: min(128 FP32 lanes / {P2P_FP32_OPS_PER_PAIR}, "
-                       f"{MUFU_LANES_PER_SM} MUFU lanes / {P2P_MUFU_OPS_PER_PAIR}, 128 issue "
-                       f"lanes / {P2P_ISSUE_PER_PAIR} instructions with packed FP32) pairs per "
-                       f"SM per clock x 152 SMs x {sm_max:.0f} MHz ({peak_kind} sm_max_mhz); "
-                       "lane rates measured on GB300 (fma, f32x2 fma, ex2 chains)",
+                       f"MUFU 1 / (1/{EX2_LANES_PER_SM} + 1/{RCP_LANES_PER_SM}) for one ex2 and "
+                       f"one rcp, 128 issue lanes / {P2P_ISSUE_PER_PAIR} instructions with packed "
+                       f"FP32) pairs per SM per clock x 152 SMs x {sm_max:.0f} MHz ({peak_kind} "
+                       "sm_max_mhz); lane rates measured on GB300 (fma, f32x2 fma, ex2 and rcp "
+                       "chains)",
         "pairs_per_launch": pairs, "near_pairs": near_pairs,
         "ring_pairs": ring_pairs,
         "pairs_counted": "3x3-neighbour pairs exactly; cutoff pairs (closer than a, leaves "

@@ -63,14 +63,14 @@ def test_single_process_needs_no_group():
 
 
 def test_near_field_peak_is_the_pipe_bound():
-    """The near-field roofline: 8 FP32 lane operations and 2 MUFU operations
+    """The near-field roofline: 8 FP32 lane operations, one ex2 and one rcp
     per pair (Eq. 6 in the 2^-q2 form), 6 issue slots with packed FP32 pairs,
-    on 128 FP32, 32 MUFU and 128 issue lanes per SM: the FP32 and MUFU pipes
-    bind together at 16 pairs per SM per clock, 5034 Gpair/s at 2070 MHz on
-    152 SMs."""
+    on 128 FP32 lanes, a MUFU pipe of 30 ex2 or 15 rcp lanes and 128 issue
+    lanes per SM: the MUFU pipe binds at 1 / (1/30 + 1/15) = 10 pairs per SM
+    per clock, 3146 Gpair/s at 2070 MHz on 152 SMs."""
     sys.path.insert(0, ROOT)
     import bench
 
     per_sm_clock = bench.p2p_peak_pairs_per_s(1.0) / (bench.N_SMS * 1e6)
-    assert abs(per_sm_clock - 16.0) < 1e-12
-    assert abs(bench.p2p_peak_pairs_per_s(2070.0) / 1e9 - 5034.24) < 1e-6
+    assert abs(per_sm_clock - 10.0) < 1e-12
+    assert abs(bench.p2p_peak_pairs_per_s(2070.0) / 1e9 - 3146.4) < 1e-6
