@@ -259,6 +259,12 @@ class Plan:
         a small limit makes them run out (FMM2D_TIMEOUT at the next check)."""
         _check(self._lib.fmm2d_plan_set_spin_limit(self._h, int(polls)), "set_spin_limit")
 
+    def set_ring_strips(self, enable: bool):
+        """Gather the FP32 near field's cutoff ring from per-side strips of
+        the ring leaves (True, the default) or from the whole leaves."""
+        _check(self._lib.fmm2d_plan_set_ring_strips(self._h, 1 if enable else 0),
+               "set_ring_strips")
+
     def phase_ms(self, age: int = 0):
         buf = (ctypes.c_double * NUM_PHASES)()
         _check(self._lib.fmm2d_plan_phase_ms(self._h, int(age), buf), "phase_ms")

@@ -73,6 +73,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "fmm2d_plan_phase_ms": ([vp, i32, vp], i32),
         "fmm2d_plan_kernels_per_call": ([vp], i32),
         "fmm2d_plan_set_spin_limit": ([vp, ctypes.c_uint32], i32),
+        "fmm2d_plan_set_ring_strips": ([vp, i32], i32),
         "fmm2d_plan_multipole_reals": ([vp], i64),
         "fmm2d_multipoles": ([vp, i64, vp, vp, vp, vp], i32),
         "fmm2d_velocity_from_multipoles": ([vp, i64, vp, vp, vp, vp, vp], i32),

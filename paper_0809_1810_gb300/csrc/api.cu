@@ -70,6 +70,8 @@ struct fmm2d_plan {
     // FP32 forms: the far field's branch of the graph and its fork/join events
     cudaStream_t cap2 = nullptr;
     float* uv_sorted = nullptr;  // FP32 forms: near-field velocities in sorted order
+    RingStrips strips{};         // FP32 forms with a cutoff: the ring strips (else null)
+    bool use_strips = true;      // gather the ring from them (else from whole leaves)
     uint64_t l2_bytes = 0;       // the device's L2 size
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool overlapped = false;  // the recorded graph runs far and near fields side by side
@@ -99,6 +101,11 @@ struct fmm2d_plan {
 };
 
 namespace {
+
+// The ring strips the near field uses (null: whole leaves).
+RingStrips strips_of(const fmm2d_plan* pl) {
+    return pl->use_strips ? pl->strips : RingStrips{nullptr, nullptr};
+}
 
 // out = x + dt u (u2 null) or x + dt (u + u2) / 2, over m reals: the
 // position updates of a convection step.
@@ -183,7 +190,7 @@ cudaError_t enqueue(fmm2d_plan* pl, int64_t n, const R* xy, const R* gamma, R* u
         auto near_only = [&]() {
             return launch_near_only_f32(g, pl->prm.sigma, n, pl->particles, skeys,
                                         pl->sb.leaf_start, pl->p2p_counter,
-                                        sorted ? pl->uv_sorted : uvf, sorted, s);
+                                        sorted ? pl->uv_sorted : uvf, sorted, strips_of(pl), s);
         };
         cudaStream_t s2 = s;
         if (fork) {
@@ -285,7 +292,8 @@ cudaError_t enqueue_partial(fmm2d_plan* pl, bool upward, int64_t n, const R* xy,
         float* uvf = reinterpret_cast<float*>(uv);
         const bool sorted = (uint64_t)n * 4 * sizeof(float) <= pl->l2_bytes / 2;
         STEP(launch_near_only_f32(g, pl->prm.sigma, n, pl->particles, skeys, pl->sb.leaf_start,
-                                  pl->p2p_counter, sorted ? pl->uv_sorted : uvf, sorted, s));
+                                  pl->p2p_counter, sorted ? pl->uv_sorted : uvf, sorted,
+                                  strips_of(pl), s));
         STEP(launch_l2p_f32(g, pl->prm.sigma, pl->particles, pl->sb.leaf_start,
                             reinterpret_cast<const float*>(le),
                             reinterpret_cast<const float*>(t.l2l),
@@ -459,6 +467,9 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
     int64_t nblocks = (nmax + kSortTile - 1) / kSortTile;
     int64_t nleaf = (int64_t)1 << (2 * g.L);
     size_t psize = pl->elem == 8 ? sizeof(ParticleD) : sizeof(float4);
+    // the FP32 near field gathers its cutoff ring from per-side strips of the
+    // ring leaves (4 records per particle; positions below 2^32)
+    const bool strips = pl->elem == 4 && prm->cutoff > 0.0 && g.L >= 2 && nmax < ((int64_t)1 << 30);
     size_t tab_count = (size_t)(8 + kOffsetSlots) * g.P * g.P * 2;
     size_t sizes[] = {
         align256(nmax * 4), align256(nmax * 4), align256(nmax * 4), align256(nmax * 4),
@@ -474,14 +485,16 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
         256,                                                  // status, work counter
         align256(((size_t)1 << g.L) * sizeof(float4)),        // leaf-centre table
         align256(pl->elem == 4 ? nmax * 2 * sizeof(float) : 0),  // near field, sorted order
+        align256(strips ? (size_t)nmax * 4 * sizeof(float4) : 0),  // ring strips
+        align256(strips ? (size_t)nleaf * 4 * 4 : 0),               // their counts
     };
     size_t total = 0;
     for (size_t s : sizes) total += s;
     cudaError_t e = cudaMalloc(&pl->ws, total);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "workspace cudaMalloc"));
     char* p = static_cast<char*>(pl->ws);
-    void* slots[16];
-    for (int i = 0; i < 16; ++i) {
+    void* slots[18];
+    for (int i = 0; i < 18; ++i) {
         slots[i] = p;
         p += sizes[i];
     }
@@ -503,6 +516,7 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
     pl->sb.status = pl->d_status;
     float4* centres = (float4*)slots[14];
     pl->uv_sorted = (float*)slots[15];
+    if (strips) pl->strips = RingStrips{(float4*)slots[16], (uint32_t*)slots[17]};
 
     e = cudaHostAlloc((void**)&pl->h_status, sizeof(int), cudaHostAllocDefault);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaHostAlloc"));
@@ -843,6 +857,13 @@ fmm2d_status fmm2d_plan_phase_ms(fmm2d_plan* pl, int age, double* ms) {
 }
 
 int fmm2d_plan_kernels_per_call(const fmm2d_plan* pl) { return pl ? pl->kernel_nodes : -1; }
+
+fmm2d_status fmm2d_plan_set_ring_strips(fmm2d_plan* pl, int enable) {
+    if (!pl) return fail(FMM2D_INVALID_ARG, "null plan");
+    pl->use_strips = enable != 0;
+    drop_graph(pl);  // the strips are kernel arguments recorded in the graph
+    return FMM2D_OK;
+}
 
 fmm2d_status fmm2d_plan_set_spin_limit(fmm2d_plan* pl, uint32_t polls) {
     if (!pl) return fail(FMM2D_INVALID_ARG, "null plan");

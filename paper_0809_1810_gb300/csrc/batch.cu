@@ -76,6 +76,7 @@ struct fmm2d_batch_plan {
     int tc_b_stages = 0;  // 0: as many as shared memory holds
     int tc_policy = 0;
     bool any_cutoff = false;
+    RingStrips strips{};  // with a cutoff: the near field's ring strips
     // graph
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
@@ -143,7 +144,8 @@ cudaError_t enqueue_batch(fmm2d_batch_plan* b, const float* xy, const float* gam
                            b->d_counter, b->p2p_ctas_per_sm, b->particles,
                            b->sb.keys[sort_passes(b->key_bits) & 1], b->sb.leaf_start, b->le,
                            b->has_class[0] ? tab_l2l(b, 0) : nullptr,
-                           b->has_class[1] ? tab_l2l(b, 1) : nullptr, uv, b->any_cutoff, s));
+                           b->has_class[1] ? tab_l2l(b, 1) : nullptr, uv, b->any_cutoff, b->strips,
+                           b->nleaf_total, s));
     BMARK(5);
 #undef BMARK
 #undef BSTEP
@@ -344,6 +346,10 @@ fmm2d_status fmm2d_batch_plan_create_ex(fmm2d_batch_plan** out, int count,
         a256(4 * (size_t)std::max<int64_t>(exp_total, 1)), a256(8 * tab_count[0]),
         a256(8 * tab_count[1]), a256(4 * tab_count[0]), a256(4 * tab_count[1]),
         a256(8 * 65 * 65)};  // binomial scratch
+    // ring strips of the cutoff: 4 records per particle, 4 counts per leaf
+    const bool want_strips = b->any_cutoff && nmax < ((int64_t)1 << 30);
+    sizes.push_back(a256(want_strips ? 16 * 4 * (size_t)nmax : 0));
+    sizes.push_back(a256(want_strips ? 16 * (size_t)nleaf : 0));
     size_t lists_bytes = 0;
     for (int c = 0; c < 2; ++c) {
         lists_bytes += a256(4 * quad_inst[c].size() + 4) * 2 + a256(4 * m2l_inst[c].size() + 4) +
@@ -384,6 +390,11 @@ fmm2d_status fmm2d_batch_plan_create_ex(fmm2d_batch_plan** out, int count,
     b->tab32[0] = (float*)take(sizes[k++]);
     b->tab32[1] = (float*)take(sizes[k++]);
     double* binom = (double*)take(sizes[k++]);
+    {
+        float4* rec = (float4*)take(sizes[k++]);
+        uint32_t* cnt = (uint32_t*)take(sizes[k++]);
+        if (want_strips) b->strips = RingStrips{rec, cnt};
+    }
     b->sb.status = b->d_status;
 
     e = cudaHostAlloc((void**)&b->h_status, sizeof(int), cudaHostAllocDefault);
@@ -528,7 +539,7 @@ fmm2d_status fmm2d_batch_autotune(fmm2d_batch_plan* b, const float* xy, const fl
                                     b->sb.leaf_start, b->le,
                                     b->has_class[0] ? tab_l2l(b, 0) : nullptr,
                                     b->has_class[1] ? tab_l2l(b, 1) : nullptr, uv,
-                                    b->any_cutoff, s);
+                                    b->any_cutoff, b->strips, b->nleaf_total, s);
         });
         if (ms < best) {
             best = ms;

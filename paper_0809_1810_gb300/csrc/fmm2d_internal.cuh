@@ -166,10 +166,22 @@ cudaError_t launch_p2p_l2p(const Geometry& g, double sigma, int64_t n, const voi
 // that adds the far part afterwards -- reading the near parts in sorted order
 // from uv_sorted, or from uv itself when uv_sorted is null -- and writes the
 // velocities to uv at the input indices (the fused kernel's sum, bit for bit).
+// Ring strips of the cutoff (Sec. 4.1) for the FP32 near field: per leaf
+// and side (0 left, 1 right, 2 bottom, 3 top), the leaf's records within
+// reach of the leaf two leaves away on that side, in sorted order, at
+// rec[4 t0 + side n_leaf ...] (t0 the leaf's first sorted position), their
+// counts at n[4 leaf + side].  rec holds 4 records per particle, n 4 counts
+// per leaf.  Null rec: the ring is gathered from whole leaves (the same
+// sources, in the same order).
+struct RingStrips {
+    float4* rec;
+    uint32_t* n;
+};
+
 cudaError_t launch_near_only_f32(const Geometry& g, double sigma, int64_t n,
                                  const void* particles, const uint32_t* skeys,
                                  const uint32_t* leaf_start, uint32_t* counter, float* out,
-                                 bool sorted_out,
+                                 bool sorted_out, RingStrips strips,
                                  cudaStream_t s);
 cudaError_t launch_l2p_f32(const Geometry& g, double sigma, const void* particles,
                            const uint32_t* leaf_start, const float* le, const float* l2l,
@@ -230,7 +242,8 @@ cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
                              const int32_t* leaf_inst, uint32_t ntotal, uint32_t* counter,
                              int ctas_per_sm, const void* particles, const uint32_t* skeys,
                              const uint32_t* leaf_start, const float* le, const float* l2l16,
-                             const float* l2l32, float* uv, bool cut, cudaStream_t s);
+                             const float* l2l32, float* uv, bool cut, RingStrips strips,
+                             uint32_t nleaf_total, cudaStream_t s);
 cudaError_t launch_batch_direct(const BatchInst* inst, const int64_t* dev_offsets, int count,
                                 int kernel, const float* xy, const float* gamma, int64_t s_count,
                                 const int64_t* targets, double* uv_ref, int* status,

@@ -245,6 +245,9 @@ struct NearF32v3 {
                               // which a source may be at q2 < qthr of a target
     float qa;                 // cutoff a^2 in scaled units, a^2 sc^2 (0: none)
     float band_a2;            // qa with a margin: ring sources nearer the leaf square
+    float wstrip;             // ring strips: the band along a side of a leaf (scaled
+                              // width) holding every source the leaf two leaves away
+                              // on that side keeps (0: no cutoff)
     uint32_t ring_mask;       // ring leaves (bit r, ring_offset order) nearer than a
     float coef[kF32Deg + 1];  // g(q2) ~ sum_k coef[k] q2^k on [0, qthr)
 };
@@ -632,7 +635,8 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
                                              const NearF32v3& nm, const float* __restrict__ le,
                                              const float* __restrict__ l2l,
                                              float* __restrict__ uv, float4* buf,
-                                             uint32_t* ranges, float2* leaf_le) {
+                                             uint32_t* ranges, float2* leaf_le,
+                                             const RingStrips& rs) {
     const int lane = threadIdx.x & 31;
     const int nl = 1 << g.L;
     const uint32_t lx = morton_compact(leaf), ly = morton_compact(leaf >> 1);
@@ -680,6 +684,11 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
                 uint32_t k = leaf_base + morton_key((uint32_t)sx, (uint32_t)sy);
                 b = leaf_start[k];
                 len = leaf_start[k + 1] - b;
+                if (rs.rec) {  // the ring leaf's strip on the side facing this leaf
+                    const uint32_t sd = dx == 2 ? 0u : dx == -2 ? 1u : dy == 2 ? 2u : 3u;
+                    b = 4u * b + sd * len;
+                    len = rs.n[4u * k + sd];
+                }
             }
         }
         uint32_t incl = len;
@@ -703,6 +712,7 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
         leaf_le_build(g, le, l2l, lx, ly, leaf_le);
         c.le_leaf = reinterpret_cast<const float*>(leaf_le);
     }
+    const float4* rsrc = rs.rec ? rs.rec : sp;  // where the ring ranges point
     const uint32_t total = rpre[9];
     const bool one_chunk = total <= kListChunk && (!kCut || c.ctotal == 0);  // ring reuses buf
     uint32_t nn = 0, nf = 0;
@@ -745,7 +755,7 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
         if (kCut)
             for (uint32_t cb = 0; cb < c.ctotal; cb += kListChunk) {  // cutoff ring
                 uint32_t nc;
-                gather_ring(sp, c, nm, cb, min(kListChunk, c.ctotal - cb), buf, nc);
+                gather_ring(rsrc, c, nm, cb, min(kListChunk, c.ctotal - cb), buf, nc);
                 band_loopT<kRing, T>(buf, 0, near_pairs(nc), nm, x, y, S);
             }
 #pragma unroll
@@ -786,7 +796,7 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
         if (kCut)
             for (uint32_t cb = 0; cb < c.ctotal; cb += kListChunk) {  // cutoff ring
                 uint32_t nc;
-                gather_ring(sp, c, nm, cb, min(kListChunk, c.ctotal - cb), buf, nc);
+                gather_ring(rsrc, c, nm, cb, min(kListChunk, c.ctotal - cb), buf, nc);
                 band_loop_split<kRing>(buf, 0, near_pairs(nc), ns, sl, nm, x, y, su, sv, cu, cv);
             }
         su += cu;
@@ -879,7 +889,7 @@ __global__ void __launch_bounds__(kLeafWarps * 32, 6)
 p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skeys,
                    const uint32_t* __restrict__ leaf_start, WorkSplit ws, uint32_t* counter,
                    Geometry g, NearF32v3 nm, const float* __restrict__ le,
-                   const float* __restrict__ l2l, float* __restrict__ uv) {
+                   const float* __restrict__ l2l, float* __restrict__ uv, RingStrips rs) {
     __shared__ float4 lists[kLeafWarps][kListCap];
     __shared__ uint32_t ranges[kLeafWarps][kCut ? 52 : 20];
     __shared__ float2 leaf_le[kLeafWarps][kMaxP];
@@ -891,7 +901,7 @@ p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ s
         if (w >= ws.items) break;
         for_each_piece(skeys, leaf_start, ws, w, [&](uint32_t leaf, uint32_t a, uint32_t b) {
             p2p_chunk_f32<kCut, kMaxT, kSorted>(sp, leaf_start, 0, leaf, a, b, g, nm, le, l2l,
-                                                uv, lists[warp], ranges[warp], leaf_le[warp]);
+                                                uv, lists[warp], ranges[warp], leaf_le[warp], rs);
         });
     }
 }
@@ -900,8 +910,71 @@ p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ s
 struct NearInst {
     float sc, kvel, kzeta, inv_s, half_leaf;
     float qa, band_a2;   // the instance's cutoff of Sec. 4.1 (0: none)
+    float wstrip;        // its ring strips' width
     uint32_t ring_mask;  // its ring leaves nearer than a
 };
+
+// Ring strips of the cutoff (Sec. 4.1), one warp per leaf: the leaf's
+// records within wstrip of each side (scaled leaf-relative coordinates; 0
+// left, 1 right, 2 bottom, 3 top), compacted in sorted order to
+// rs.rec[4 t0 + side n ...], their counts to rs.n[4 leaf + side].  A ring leaf
+// two leaves away can keep (closer than the cutoff to its square, with the
+// near-field kernel's margin) only sources of this leaf's strip on the side
+// facing it, so the near field gathers the strip instead of the whole leaf:
+// the same kept sources in the same order.  kBatch: leaf is a global leaf of
+// a batch (its instance's geometry and constants); otherwise of one tree.
+template <bool kBatch>
+__global__ void __launch_bounds__(kLeafWarps * 32)
+ring_strips_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
+                   uint32_t nleaf, Geometry g1, NearF32v3 nm1,
+                   const BatchInst* __restrict__ inst, const NearInst* __restrict__ near_inst,
+                   const int32_t* __restrict__ leaf_inst, RingStrips rs) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t leaf = blockIdx.x * kLeafWarps + warp;
+    if (leaf >= nleaf) return;  // warp-uniform
+    const unsigned lt = (1u << lane) - 1u;
+    float sc = nm1.sc, hl = nm1.half_leaf, w = nm1.wstrip;
+    uint32_t local = leaf;
+    const Geometry* g = &g1;
+    if (kBatch) {
+        const int i = leaf_inst[leaf];
+        const NearInst ni = near_inst[i];
+        if (ni.ring_mask == 0) return;  // no ring: its strips are never read
+        sc = ni.sc;
+        hl = ni.half_leaf;
+        w = ni.wstrip;
+        g = &inst[i].g;
+        local = leaf - inst[i].leaf_base;
+    }
+    const uint32_t t0 = leaf_start[leaf], n = leaf_start[leaf + 1] - t0;
+    float cxh, cxl, cyh, cyl;
+    leaf_centre_hilo(*g, morton_compact(local), morton_compact(local >> 1), &cxh, &cxl, &cyh,
+                     &cyl);
+    const float lo = w - hl, hi = hl - w;  // X < lo: left strip; X > hi: right strip
+    uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    float4* out = rs.rec + 4 * (int64_t)t0;
+    for (uint32_t g0 = 0; g0 < n; g0 += 32) {
+        const uint32_t k = g0 + lane;
+        const bool in = k < n;
+        float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+        float X = 0.f, Y = 0.f;
+        if (in) {
+            rec = sp[t0 + k];
+            X = ((rec.x - cxh) - cxl) * sc;
+            Y = ((rec.y - cyh) - cyl) * sc;
+        }
+        auto put = [&](bool f, uint32_t side, uint32_t& cnt) {
+            const unsigned m = __ballot_sync(0xffffffffu, f);
+            if (f) out[side * n + cnt + __popc(m & lt)] = rec;
+            cnt += __popc(m);
+        };
+        put(in && X < lo, 0u, c0);
+        put(in && X > hi, 1u, c1);
+        put(in && Y < lo, 2u, c2);
+        put(in && Y > hi, 3u, c3);
+    }
+    if (lane < 4) rs.n[4 * leaf + lane] = lane == 0 ? c0 : lane == 1 ? c1 : lane == 2 ? c2 : c3;
+}
 
 // Batched and persistent: warps pull work items over the global sorted order
 // (all instances, packed) from a work counter.  kCut compiles in the cutoff
@@ -914,7 +987,7 @@ p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ ske
                  const NearInst* __restrict__ near_inst, const int32_t* __restrict__ leaf_inst,
                  WorkSplit ws, uint32_t* counter, NearF32v3 shared_nm,
                  const float* __restrict__ le, const float* __restrict__ l2l16,
-                 const float* __restrict__ l2l32, float* __restrict__ uv) {
+                 const float* __restrict__ l2l32, float* __restrict__ uv, RingStrips rs) {
     __shared__ float4 lists[kLeafWarps][kListCap];
     __shared__ uint32_t ranges[kLeafWarps][kCut ? 52 : 20];
     __shared__ float2 leaf_le[kLeafWarps][kMaxP];
@@ -936,11 +1009,12 @@ p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ ske
             nm.half_leaf = ni.half_leaf;
             nm.qa = ni.qa;
             nm.band_a2 = ni.band_a2;
+            nm.wstrip = ni.wstrip;
             nm.ring_mask = ni.ring_mask;
             p2p_chunk_f32<kCut, kCut ? 2 : 4>(sp, leaf_start, b.leaf_base, gleaf - b.leaf_base, a,
                                               e, b.g, nm, le + b.exp_off,
                                               b.g.P <= 16 ? l2l16 : l2l32, uv, lists[warp],
-                                              ranges[warp], leaf_le[warp]);
+                                              ranges[warp], leaf_le[warp], rs);
         });
     }
 }
@@ -1027,6 +1101,13 @@ static NearF32v3 near_constants(double sigma, const Geometry& g, bool* ok) {
     const double qa = g.L >= 2 ? g.cutoff * g.cutoff * (double)nm.sc * (double)nm.sc : 0.0;
     nm.qa = (float)qa;
     nm.band_a2 = (float)(qa * 1.02);
+    // a source of a ring leaf two leaves to the right is kept when its
+    // distance to the target leaf's square, at least its distance from its
+    // own leaf's left side plus one leaf width, is below sqrt(band_a2): the
+    // strip is sqrt(band_a2) less a leaf wide (a margin of 1e-3 half-leaves
+    // covers the rounding of the two leaves' frames)
+    const double hl = 0.5 * box * (double)nm.sc;
+    nm.wstrip = qa > 0.0 ? (float)(sqrt(qa * 1.02) - 2.0 * hl + 1e-3 * hl) : 0.f;
     nm.ring_mask = ring_mask(g);
     double coef[kF32Deg + 1];
     *ok = fit_near_polynomial(qthr, coef) <= 1e-8;
@@ -1051,7 +1132,7 @@ static cudaError_t launch_near_f32(const Geometry& g, double sigma, int64_t n,
                                    const void* particles, const uint32_t* skeys,
                                    const uint32_t* leaf_start, uint32_t* counter,
                                    const float* le, const float* l2l, float* uv, bool sorted_out,
-                                   cudaStream_t s) {
+                                   RingStrips rs, cudaStream_t s) {
     bool ok;
     NearF32v3 nm = near_constants(sigma, g, &ok);
     if (!ok) return cudaErrorInvalidValue;
@@ -1072,11 +1153,19 @@ static cudaError_t launch_near_f32(const Geometry& g, double sigma, int64_t n,
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const float4* sp = reinterpret_cast<const float4*>(particles);
+    if (!cut || !rs.n) rs.rec = nullptr;
+    if (rs.rec) {
+        const uint32_t nleaf = 1u << (2 * g.L);
+        ring_strips_kernel<false><<<(nleaf + kLeafWarps - 1) / kLeafWarps, kLeafWarps * 32, 0, s>>>(
+            sp, leaf_start, nleaf, g, nm, nullptr, nullptr, nullptr, rs);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     auto go = [&](auto kernel) {
         if (resident_ctas(reinterpret_cast<const void*>(kernel)) != resident)
             return cudaErrorInvalidConfiguration;
         kernel<<<dim3(blocks), dim3(kLeafWarps * 32), 0, s>>>(sp, skeys, leaf_start, ws, counter,
-                                                              g, nm, le, l2l, uv);
+                                                              g, nm, le, l2l, uv, rs);
         return cudaGetLastError();
     };
     if (cut && max_t >= 4)
@@ -1095,15 +1184,15 @@ cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, int64_t n,
                                   const uint32_t* leaf_start, uint32_t* counter, const float* le,
                                   const float* l2l, float* uv, cudaStream_t s) {
     return launch_near_f32(g, sigma, n, particles, skeys, leaf_start, counter, le, l2l, uv, false,
-                           s);
+                           RingStrips{nullptr, nullptr}, s);
 }
 
 cudaError_t launch_near_only_f32(const Geometry& g, double sigma, int64_t n,
                                  const void* particles, const uint32_t* skeys,
                                  const uint32_t* leaf_start, uint32_t* counter, float* out,
-                                 bool sorted_out, cudaStream_t s) {
+                                 bool sorted_out, RingStrips strips, cudaStream_t s) {
     return launch_near_f32(g, sigma, n, particles, skeys, leaf_start, counter, nullptr, nullptr,
-                           out, sorted_out, s);
+                           out, sorted_out, strips, s);
 }
 
 // L2P after a near-field-only pass: one warp per leaf adds the leaf's local
@@ -1208,8 +1297,8 @@ cudaError_t batch_near_fill(const BatchInst* host_inst, int count, void* dev_nea
         bool oki;
         NearF32v3 nm = near_constants(host_inst[i].sigma, host_inst[i].g, &oki);
         ok = ok && oki;
-        h[i] = NearInst{nm.sc,        nm.kvel, nm.kzeta,  nm.inv_s,
-                        nm.half_leaf, nm.qa,   nm.band_a2, nm.ring_mask};
+        h[i] = NearInst{nm.sc,        nm.kvel,    nm.kzeta,  nm.inv_s,    nm.half_leaf,
+                        nm.qa,        nm.band_a2, nm.wstrip, nm.ring_mask};
     }
     cudaError_t e = ok ? cudaMemcpyAsync(dev_near, h, sizeof(NearInst) * count,
                                          cudaMemcpyHostToDevice, s)
@@ -1223,7 +1312,8 @@ cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
                              const int32_t* leaf_inst, uint32_t ntotal, uint32_t* counter,
                              int ctas_per_sm, const void* particles, const uint32_t* skeys,
                              const uint32_t* leaf_start, const float* le, const float* l2l16,
-                             const float* l2l32, float* uv, bool cut, cudaStream_t s) {
+                             const float* l2l32, float* uv, bool cut, RingStrips strips,
+                             uint32_t nleaf_total, cudaStream_t s) {
     if (ntotal == 0) return cudaSuccess;
     Geometry g1{};
     g1.W = 2.0;
@@ -1237,18 +1327,27 @@ cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
     unsigned blocks = (unsigned)(sms * ctas_per_sm);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
+    if (!cut || !strips.n) strips.rec = nullptr;
+    if (strips.rec) {
+        ring_strips_kernel<true><<<(nleaf_total + kLeafWarps - 1) / kLeafWarps, kLeafWarps * 32, 0,
+                                   s>>>(reinterpret_cast<const float4*>(particles), leaf_start,
+                                        nleaf_total, Geometry{}, shared_nm, inst,
+                                        static_cast<const NearInst*>(near_inst), leaf_inst, strips);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     if (cut)
         p2p_batch_kernel<true><<<blocks, kLeafWarps * 32, 0, s>>>(
             reinterpret_cast<const float4*>(particles), skeys, leaf_start, inst,
             static_cast<const NearInst*>(near_inst), leaf_inst,
             work_split(ntotal, (uint64_t)blocks * kLeafWarps), counter, shared_nm, le, l2l16,
-            l2l32, uv);
+            l2l32, uv, strips);
     else
         p2p_batch_kernel<false><<<blocks, kLeafWarps * 32, 0, s>>>(
             reinterpret_cast<const float4*>(particles), skeys, leaf_start, inst,
             static_cast<const NearInst*>(near_inst), leaf_inst,
             work_split(ntotal, (uint64_t)blocks * kLeafWarps), counter, shared_nm, le, l2l16,
-            l2l32, uv);
+            l2l32, uv, strips);
     return cudaGetLastError();
 }
 

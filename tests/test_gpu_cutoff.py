@@ -111,6 +111,34 @@ def test_fp32_cutoff_matches_oracle(name, make, af, prec):
     assert _rel(plain, ref) > 10 * FP32_TOL, _rel(plain, ref)
 
 
+# (n, L, sigma / h, a / leaf width): the ring sources of every leaf fit one
+# shared-memory chunk (at most 558) from whole leaves and from strips alike
+STRIP_CASES = [(6007, 4, 2.0, 1.9), (8191, 5, 1.1, 1.8), (12000, 6, 0.7, 1.9),
+               (24000, 5, 2.0, 1.99)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_tc"])
+@pytest.mark.parametrize("n,L,soh,af", STRIP_CASES)
+def test_ring_strips_keep_the_whole_leaves_sources(n, L, soh, af, prec):
+    """The FP32 near field gathers each ring leaf's strip on the side facing
+    the target leaf instead of the whole leaf: the strip must hold every
+    source the whole leaf would give (closer than a, with the kernel's
+    margin, to the target leaf's square), in the same order, so the
+    velocities agree bit for bit.  A strip too narrow would drop the ring
+    pairs nearest the cutoff, whose corrections are below the FP32 bar."""
+    w = W.uniform_random(n, n + 7, 2.0 / np.sqrt(n), sigma_over_h=soh, p=10, L=L,
+                         dtype=np.float32)
+    xy, g = _dev(w, torch.float32)
+    with _plan(w, prec, af * _leaf(w)) as plan:
+        strips = plan.velocity(xy, g, check=True).clone()
+        plan.set_ring_strips(False)
+        whole = plan.velocity(xy, g, check=True).clone()
+        plan.set_ring_strips(True)
+        again = plan.velocity(xy, g, check=True)
+    assert torch.equal(strips, whole)
+    assert torch.equal(strips, again)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_tc"])
 def test_cutoff_within_a_leaf_changes_nothing(prec):
     """Leaves two apart are at least a leaf width apart: a cutoff below one
