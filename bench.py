@@ -68,8 +68,8 @@ P2P_ISSUE_PER_PAIR = 6
 # dram__bytes_write.sum) from one ncu capture of the kernel on the benchmark
 # workload and setting; reported only while the kernel source is the one
 # captured (its SHA-256) and the setting matches.
-P2P_TRAFFIC = {"sha256_p2p_cu": "4f395963ddf6f903521fd4863454386c2b51ed28c2f13823ba3f266665e63dfd",
-               "p": 15, "L": 7, "cutoff": True, "bytes": 21111040}
+P2P_TRAFFIC = {"sha256_p2p_cu": "495b4de6deedae435ad90244e93b8afbe93430b544ad20defedf25d98944c234",
+               "p": 15, "L": 7, "cutoff": True, "bytes": 50927360}
 
 
 def m2l_pairs(L):
@@ -864,7 +864,9 @@ def run_ours(args):
                          "not neighbours) as N x their mean over the accuracy targets",
         "avg_launch_ms": p2p_ms,
         "traffic": p2p_traffic(p, L, cutoff),
-        "traffic_unit": "bytes per launch (ncu DRAM read + write)",
+        "traffic_unit": "bytes per launch (ncu DRAM read + write; ncu flushes the caches "
+                        "before the launch, so the ring strips and the sorted records, L2-resident "
+                        "inside a step, are read from DRAM there)",
         "phase_ms": phase_avg,
         "phase_timing": f"in-graph events over a second timed run of the same {args.steps} "
                         f"steps ({float(np.mean(phase_step_ms)):.4f} ms/step with the event "
