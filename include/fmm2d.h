@@ -516,7 +516,8 @@ fmm2d_status fmm2d_plan_set_spin_limit(fmm2d_plan* plan, uint32_t polls);
  * sources of its ring (the leaves two leaves away) from.  enable != 0 (the
  * default): from per-side strips of those leaves, built each evaluation
  * (the sources within reach of the leaf on that side, about a third of the
- * leaf at a = 1.3 leaf widths); 0: from the whole leaves.  Both keep the
+ * leaf at a = 1.3 leaf widths), while a strip is at most half a leaf wide
+ * (a <= 1.5 leaf widths); 0, or a wider cutoff: from the whole leaves.  Both keep the
  * same sources in the same order, so the velocities agree bit for bit while
  * a leaf's ring sources fit one shared-memory chunk (558 records).  Plans
  * without a cutoff, FP64 plans and L < 2 ignore it.  The next fmm2d_velocity

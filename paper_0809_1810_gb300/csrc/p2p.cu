@@ -684,7 +684,7 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
                 uint32_t k = leaf_base + morton_key((uint32_t)sx, (uint32_t)sy);
                 b = leaf_start[k];
                 len = leaf_start[k + 1] - b;
-                if (rs.rec) {  // the ring leaf's strip on the side facing this leaf
+                if (rs.rec && nm.wstrip > 0.f) {  // the ring leaf's strip facing this leaf
                     const uint32_t sd = dx == 2 ? 0u : dx == -2 ? 1u : dy == 2 ? 2u : 3u;
                     b = 4u * b + sd * len;
                     len = rs.n[4u * k + sd];
@@ -712,7 +712,7 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
         leaf_le_build(g, le, l2l, lx, ly, leaf_le);
         c.le_leaf = reinterpret_cast<const float*>(leaf_le);
     }
-    const float4* rsrc = rs.rec ? rs.rec : sp;  // where the ring ranges point
+    const float4* rsrc = rs.rec && nm.wstrip > 0.f ? rs.rec : sp;  // where the ring ranges point
     const uint32_t total = rpre[9];
     const bool one_chunk = total <= kListChunk && (!kCut || c.ctotal == 0);  // ring reuses buf
     uint32_t nn = 0, nf = 0;
@@ -939,7 +939,7 @@ ring_strips_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ l
     if (kBatch) {
         const int i = leaf_inst[leaf];
         const NearInst ni = near_inst[i];
-        if (ni.ring_mask == 0) return;  // no ring: its strips are never read
+        if (ni.ring_mask == 0 || !(ni.wstrip > 0.f)) return;  // its strips are never read
         sc = ni.sc;
         hl = ni.half_leaf;
         w = ni.wstrip;
@@ -1107,7 +1107,11 @@ static NearF32v3 near_constants(double sigma, const Geometry& g, bool* ok) {
     // strip is sqrt(band_a2) less a leaf wide (a margin of 1e-3 half-leaves
     // covers the rounding of the two leaves' frames)
     const double hl = 0.5 * box * (double)nm.sc;
-    nm.wstrip = qa > 0.0 ? (float)(sqrt(qa * 1.02) - 2.0 * hl + 1e-3 * hl) : 0.f;
+    const double wstrip = sqrt(qa * 1.02) - 2.0 * hl + 1e-3 * hl;
+    // strips pay while they are narrow: at most half a leaf (a up to 1.5 leaf
+    // widths); wider, their writes cost more than the gathers they save, and
+    // the ring is gathered from whole leaves (wstrip 0)
+    nm.wstrip = qa > 0.0 && wstrip <= hl ? (float)wstrip : 0.f;
     nm.ring_mask = ring_mask(g);
     double coef[kF32Deg + 1];
     *ok = fit_near_polynomial(qthr, coef) <= 1e-8;
@@ -1153,7 +1157,7 @@ static cudaError_t launch_near_f32(const Geometry& g, double sigma, int64_t n,
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const float4* sp = reinterpret_cast<const float4*>(particles);
-    if (!cut || !rs.n) rs.rec = nullptr;
+    if (!cut || !rs.n || !(nm.wstrip > 0.f)) rs.rec = nullptr;
     if (rs.rec) {
         const uint32_t nleaf = 1u << (2 * g.L);
         ring_strips_kernel<false><<<(nleaf + kLeafWarps - 1) / kLeafWarps, kLeafWarps * 32, 0, s>>>(

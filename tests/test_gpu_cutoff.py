@@ -112,9 +112,10 @@ def test_fp32_cutoff_matches_oracle(name, make, af, prec):
 
 
 # (n, L, sigma / h, a / leaf width): the ring sources of every leaf fit one
-# shared-memory chunk (at most 558) from whole leaves and from strips alike
-STRIP_CASES = [(6007, 4, 2.0, 1.9), (8191, 5, 1.1, 1.8), (12000, 6, 0.7, 1.9),
-               (24000, 5, 2.0, 1.99)]
+# shared-memory chunk (at most 558) from whole leaves and from strips alike;
+# strips are used up to a = 1.5 leaf widths (half-leaf strips)
+STRIP_CASES = [(6007, 4, 2.0, 1.2), (8191, 5, 1.1, 1.31), (12000, 6, 0.7, 1.45),
+               (24000, 5, 2.0, 1.499)]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp32_tc"])
