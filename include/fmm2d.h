@@ -115,6 +115,24 @@ fmm2d_status fmm2d_velocity(fmm2d_plan* plan, int64_t n, const void* xy_dev,
 fmm2d_status fmm2d_velocity_host(fmm2d_plan* plan, int64_t n, const void* xy_host,
                                  const void* gamma_host, void* uv_host, cudaStream_t stream);
 
+/* count independent particle sets of n particles each, from host buffers,
+ * pipelined: set k + 1's inputs are copied to the device (on a copy stream
+ * of the plan) while set k is evaluated on `stream`, and set k's velocities
+ * are copied back (on a second copy stream) while set k + 1 is evaluated.
+ * Each set is evaluated exactly as fmm2d_velocity_host evaluates it, so
+ * every set's velocities are the same bit for bit.
+ *   xy_host[k], gamma_host[k], uv_host[k]   the host buffers of set k, as in
+ *              fmm2d_velocity_host (page-locked, or the copies cannot overlap)
+ * Allocates on first use two more staging sets of max_n particles, two
+ * streams and eight events, kept until the plan is destroyed.  Returns after
+ * the last set's velocities are in host memory, with the device-detected
+ * status of all sets (fmm2d_plan_check).  Errors: FMM2D_INVALID_ARG for
+ * count < 0, n outside [0, max_n] or a null buffer. */
+fmm2d_status fmm2d_velocity_host_many(fmm2d_plan* plan, int count, int64_t n,
+                                      const void* const* xy_host,
+                                      const void* const* gamma_host, void* const* uv_host,
+                                      cudaStream_t stream);
+
 /* One explicit step of the convection part of the vortex method, Eq. 5
  * (dx_i/dt = u(x_i) with u from the FMM of this plan), in place:
  *   order 1  forward Euler, x' = x + dt u(x)                 (one evaluation)

@@ -183,6 +183,30 @@ class Plan:
                                              _stream(stream)), "velocity_host")
         return out
 
+    def velocity_host_many(self, xys, gammas, outs, stream=None):
+        """count independent sets from host buffers, pipelined
+        (fmm2d_velocity_host_many): xys[k], gammas[k], outs[k] are CPU tensors
+        of set k (page-locked for the copies to overlap), all sets of the
+        same size; synchronous."""
+        count = len(xys)
+        if len(gammas) != count or len(outs) != count:
+            raise ValueError("xys, gammas and outs must have the same length")
+        n = gammas[0].shape[0] if count else 0
+        for t in list(xys) + list(gammas) + list(outs):
+            if t.is_cuda or t.dtype != self.dtype or not t.is_contiguous():
+                raise TypeError("host tensors of the plan dtype, contiguous")
+        for k in range(count):
+            if gammas[k].shape[0] != n or tuple(xys[k].shape) != (n, 2) or \
+                    tuple(outs[k].shape) != (n, 2):
+                raise ValueError("every set must hold the same number of particles")
+        arr = ctypes.c_void_p * max(count, 1)
+        pxy = arr(*[_ptr(t) for t in xys])
+        pg = arr(*[_ptr(t) for t in gammas])
+        pout = arr(*[_ptr(t) for t in outs])
+        _check(self._lib.fmm2d_velocity_host_many(self._h, count, n, pxy, pg, pout,
+                                                  _stream(stream)), "velocity_host_many")
+        return outs
+
     def check(self, stream=None):
         """Raise if the device recorded an input error (fmm2d_plan_check)."""
         _check(self._lib.fmm2d_plan_check(self._h, _stream(stream)), "plan_check")

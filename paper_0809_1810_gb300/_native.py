@@ -63,6 +63,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "fmm2d_plan_destroy": ([vp], None),
         "fmm2d_velocity": ([vp, i64, vp, vp, vp, vp], i32),
         "fmm2d_velocity_host": ([vp, i64, vp, vp, vp, vp], i32),
+        "fmm2d_velocity_host_many": ([vp, i32, i64, vp, vp, vp, vp], i32),
         "fmm2d_velocity_targets": ([vp, i64, vp, vp, i64, vp, vp, vp], i32),
         "fmm2d_convect": ([vp, i64, vp, vp, d, i32, vp], i32),
         "fmm2d_plan_check": ([vp, vp], i32),

@@ -65,6 +65,12 @@ struct fmm2d_plan {
     void* st_gamma = nullptr;
     void* st_uv = nullptr;
     void* st_u1 = nullptr;  // first-stage velocities of a convection step
+    // pipelined host evaluations (fmm2d_velocity_host_many), allocated on first use:
+    // two input and two output staging sets, copy streams and their events
+    void* pipe_buf = nullptr;
+    void* pipe_in_xy[2]{}, *pipe_in_g[2]{}, *pipe_out[2]{};
+    cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr;
+    cudaEvent_t pipe_staged[2]{}, pipe_consumed[2]{}, pipe_result[2]{}, pipe_drained[2]{};
     // graph cache
     cudaStream_t cap = nullptr;
     // FP32 forms: the far field's branch of the graph and its fork/join events
@@ -603,6 +609,13 @@ void fmm2d_plan_destroy(fmm2d_plan* pl) {
     if (pl->ev_join) cudaEventDestroy(pl->ev_join);
     if (pl->h_status) cudaFreeHost(pl->h_status);
     if (pl->st_xy) cudaFree(pl->st_xy);
+    if (pl->pipe_buf) cudaFree(pl->pipe_buf);
+    if (pl->pipe_h2d) cudaStreamDestroy(pl->pipe_h2d);
+    if (pl->pipe_d2h) cudaStreamDestroy(pl->pipe_d2h);
+    for (int b = 0; b < 2; ++b)
+        for (cudaEvent_t ev : {pl->pipe_staged[b], pl->pipe_consumed[b], pl->pipe_result[b],
+                               pl->pipe_drained[b]})
+            if (ev) cudaEventDestroy(ev);
     if (pl->tc_ws) cudaFree(pl->tc_ws);
     delete pl->maps;
     if (pl->ws) cudaFree(pl->ws);
@@ -698,6 +711,91 @@ fmm2d_status fmm2d_velocity_host(fmm2d_plan* pl, int64_t n, const void* xy_host,
     if (st != FMM2D_OK) return st;
     if (n > 0)
         CK(cudaMemcpyAsync(uv_host, pl->st_uv, 2 * n * pl->elem, cudaMemcpyDeviceToHost, stream));
+    return fmm2d_plan_check(pl, stream);
+}
+
+// Staging sets, streams and events of the pipelined host evaluations.
+static fmm2d_status ensure_pipe(fmm2d_plan* pl) {
+    if (pl->pipe_buf) return FMM2D_OK;
+    size_t nm = (size_t)(pl->prm.max_n > 0 ? pl->prm.max_n : 1);
+    size_t bxy = align256(2 * nm * pl->elem), bg = align256(nm * pl->elem);
+    void* buf = nullptr;
+    CK(cudaMalloc(&buf, 2 * (2 * bxy + bg)));
+    pl->pipe_buf = buf;
+    char* p = static_cast<char*>(buf);
+    for (int b = 0; b < 2; ++b) {
+        pl->pipe_in_xy[b] = p;
+        pl->pipe_in_g[b] = p + bxy;
+        pl->pipe_out[b] = p + bxy + bg;
+        p += 2 * bxy + bg;
+    }
+    CK(cudaStreamCreateWithFlags(&pl->pipe_h2d, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&pl->pipe_d2h, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+        CK(cudaEventCreateWithFlags(&pl->pipe_staged[b], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&pl->pipe_consumed[b], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&pl->pipe_result[b], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&pl->pipe_drained[b], cudaEventDisableTiming));
+    }
+    return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_velocity_host_many(fmm2d_plan* pl, int count, int64_t n,
+                                      const void* const* xy_host, const void* const* gamma_host,
+                                      void* const* uv_host, cudaStream_t stream) {
+    if (!pl) return fail(FMM2D_INVALID_ARG, "null plan");
+    if (count < 0) return fail(FMM2D_INVALID_ARG, "count < 0");
+    if (n < 0 || n > pl->prm.max_n) return fail(FMM2D_INVALID_ARG, "n out of [0, max_n]");
+    if (count > 0 && n > 0) {
+        if (!xy_host || !gamma_host || !uv_host) return fail(FMM2D_INVALID_ARG, "null buffer");
+        for (int k = 0; k < count; ++k)
+            if (!xy_host[k] || !gamma_host[k] || !uv_host[k])
+                return fail(FMM2D_INVALID_ARG, "null buffer");
+    }
+    if (count == 0 || n == 0) {
+        for (int k = 0; k < count; ++k) {
+            fmm2d_status st = run(pl, 0, nullptr, nullptr, nullptr, stream);
+            if (st != FMM2D_OK) return st;
+        }
+        return fmm2d_plan_check(pl, stream);
+    }
+    fmm2d_status sst = ensure_staging(pl);
+    if (sst != FMM2D_OK) return sst;
+    sst = ensure_pipe(pl);
+    if (sst != FMM2D_OK) return sst;
+    const size_t bxy = 2 * (size_t)n * pl->elem, bg = (size_t)n * pl->elem;
+    // the copy streams start after whatever `stream` has queued before this call
+    CK(cudaEventRecord(pl->pipe_consumed[0], stream));
+    CK(cudaEventRecord(pl->pipe_consumed[1], stream));
+    CK(cudaEventRecord(pl->pipe_drained[0], stream));
+    CK(cudaEventRecord(pl->pipe_drained[1], stream));
+    for (int k = 0; k < count; ++k) {
+        const int b = k & 1;
+        // inputs of set k into staging set b once set k - 2 has left it
+        CK(cudaStreamWaitEvent(pl->pipe_h2d, pl->pipe_consumed[b], 0));
+        CK(cudaMemcpyAsync(pl->pipe_in_xy[b], xy_host[k], bxy, cudaMemcpyHostToDevice,
+                           pl->pipe_h2d));
+        CK(cudaMemcpyAsync(pl->pipe_in_g[b], gamma_host[k], bg, cudaMemcpyHostToDevice,
+                           pl->pipe_h2d));
+        CK(cudaEventRecord(pl->pipe_staged[b], pl->pipe_h2d));
+        // the evaluation reads the plan's fixed buffers (one recorded graph)
+        CK(cudaStreamWaitEvent(stream, pl->pipe_staged[b], 0));
+        CK(cudaMemcpyAsync(pl->st_xy, pl->pipe_in_xy[b], bxy, cudaMemcpyDeviceToDevice, stream));
+        CK(cudaMemcpyAsync(pl->st_gamma, pl->pipe_in_g[b], bg, cudaMemcpyDeviceToDevice, stream));
+        CK(cudaEventRecord(pl->pipe_consumed[b], stream));
+        fmm2d_status st = run(pl, n, pl->st_xy, pl->st_gamma, pl->st_uv, stream);
+        if (st != FMM2D_OK) return st;
+        // velocities of set k into output set b once set k - 2's have been read back
+        CK(cudaStreamWaitEvent(stream, pl->pipe_drained[b], 0));
+        CK(cudaMemcpyAsync(pl->pipe_out[b], pl->st_uv, bxy, cudaMemcpyDeviceToDevice, stream));
+        CK(cudaEventRecord(pl->pipe_result[b], stream));
+        CK(cudaStreamWaitEvent(pl->pipe_d2h, pl->pipe_result[b], 0));
+        CK(cudaMemcpyAsync(uv_host[k], pl->pipe_out[b], bxy, cudaMemcpyDeviceToHost,
+                           pl->pipe_d2h));
+        CK(cudaEventRecord(pl->pipe_drained[b], pl->pipe_d2h));
+    }
+    CK(cudaStreamSynchronize(pl->pipe_d2h));
+    CK(cudaStreamSynchronize(pl->pipe_h2d));
     return fmm2d_plan_check(pl, stream);
 }
 

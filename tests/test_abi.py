@@ -51,6 +51,9 @@ def test_null_arguments_are_rejected(lib):
         _native.INVALID_ARG
     assert lib.fmm2d_convect(None, 0, None, None, 0.1, 2, None) == _native.INVALID_ARG
     assert lib.fmm2d_plan_set_timing(None, 4) == _native.INVALID_ARG
+    assert lib.fmm2d_velocity_host_many(None, 2, 10, None, None, None, None) == \
+        _native.INVALID_ARG
+    assert lib.fmm2d_plan_set_ring_strips(None, 1) == _native.INVALID_ARG
     lib.fmm2d_plan_destroy(None)  # accepted
 
 
