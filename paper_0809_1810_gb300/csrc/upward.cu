@@ -31,7 +31,8 @@ __device__ __forceinline__ void p2m_quad(const typename ParticleOf<R>::type* __r
                                          uint32_t leaf_base, uint32_t quad, const Geometry& g,
                                          const R* __restrict__ m2m, bool fuse_parent,
                                          R* __restrict__ me,
-                                         typename Cplx<R>::T (*child_me)[PMAX]) {
+                                         typename Cplx<R>::T (*child_me)[PMAX],
+                                         typename Cplx<R>::T (*part)[PMAX]) {
     using C = typename Cplx<R>::T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t leaf = quad * 4 + warp;
@@ -103,15 +104,22 @@ __device__ __forceinline__ void p2m_quad(const typename ParticleOf<R>::type* __r
     }
     if (!fuse_parent) return;  // uniform over the CTA
     __syncthreads();
-    if (warp == 0 && lane < g.P) {  // parent at level L-1; child quadrant q is warp q
-        const C* tab = reinterpret_cast<const C*>(m2m);
-        C out = cmake<C>(R(0), R(0));
-        for (int q = 0; q < 4; ++q) {
-            const C* tq = tab + (int64_t)q * g.P * g.P;
+    // parent at level L-1: warp q translates its own child quadrant q (one
+    // chain of P steps per warp instead of one of 4 P in a single warp, which
+    // held each CTA for most of its time), then warp 0 adds the four
+    // contributions in quadrant order
+    if (lane < g.P) {
+        const C* tq = reinterpret_cast<const C*>(m2m) + (int64_t)warp * g.P * g.P;
+        C acc_q = cmake<C>(R(0), R(0));
 #pragma unroll
-            for (int k = 0; k < PMAX; ++k)
-                if (k < g.P) out = cfma(tq[k * g.P + lane], child_me[q][k], out);
-        }
+        for (int k = 0; k < PMAX; ++k)
+            if (k < g.P) acc_q = cfma(tq[k * g.P + lane], child_me[warp][k], acc_q);
+        part[warp][lane] = acc_q;
+    }
+    __syncthreads();
+    if (warp == 0 && lane < g.P) {
+        C out = part[0][lane];
+        for (int q = 1; q < 4; ++q) out = cmake<C>(out.x + part[q][lane].x, out.y + part[q][lane].y);
         if (lane >= g.p) out = cmake<C>(R(0), R(0));
         reinterpret_cast<C*>(me + box_slot(g.level_base, g.L - 1, ix >> 1, iy >> 1) *
                                       (2 * g.P))[lane] = out;
@@ -123,8 +131,8 @@ __global__ void __launch_bounds__(128)
 p2m_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
            const uint32_t* __restrict__ leaf_start, Geometry g, const R* __restrict__ m2m,
            bool fuse_parent, R* __restrict__ me) {
-    __shared__ typename Cplx<R>::T child_me[4][PMAX];
-    p2m_quad<R, PMAX>(sp, leaf_start, 0, blockIdx.x, g, m2m, fuse_parent, me, child_me);
+    __shared__ typename Cplx<R>::T child_me[4][PMAX], part[4][PMAX];
+    p2m_quad<R, PMAX>(sp, leaf_start, 0, blockIdx.x, g, m2m, fuse_parent, me, child_me, part);
 }
 
 // Batched: one CTA per parent box of any instance of the class.
@@ -134,10 +142,10 @@ p2m_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ lea
                  const BatchInst* __restrict__ inst, const int32_t* __restrict__ quad_inst,
                  const uint32_t* __restrict__ quad_local, const float* __restrict__ m2m,
                  float* __restrict__ me) {
-    __shared__ float2 child_me[4][PMAX];
+    __shared__ float2 child_me[4][PMAX], part[4][PMAX];
     const BatchInst& b = inst[quad_inst[blockIdx.x]];
     p2m_quad<float, PMAX>(sp, leaf_start, b.leaf_base, quad_local[blockIdx.x], b.g, m2m,
-                          b.g.L >= 3, me + b.exp_off, child_me);
+                          b.g.L >= 3, me + b.exp_off, child_me, part);
 }
 
 // M2M of one box with G lanes (lane n computes b~_n); children read by lane k
