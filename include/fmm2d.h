@@ -87,8 +87,10 @@ const char* fmm2d_last_error(void);
 /* Create a plan: validates the parameters, allocates the device workspace
  * for up to max_n particles on the current device, and builds the
  * translation tables (M2M of Sec. 3.3.2, M2L of Eq. 22, L2L of Sec. 3.3.3)
- * in double precision on the device.  Synchronous.  On failure *out is set
- * to NULL and nothing is leaked. */
+ * in double precision on the device.  FP32 plans with a cutoff (L >= 2,
+ * max_n < 2^30) also hold the near field's ring strips: 64 bytes per
+ * particle and 16 per leaf.  Synchronous.  On failure *out is set to NULL and
+ * nothing is leaked. */
 fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm);
 
 /* Release the plan and its workspace.  Synchronises the device first.
