@@ -436,6 +436,11 @@ __device__ __forceinline__ uint32_t far_first(uint32_t nf) {
 }
 // Sources gathered into a buffer at a time: room for a dummy in each band.
 constexpr uint32_t kListChunk = kListCap - 2;
+// gathers of at most this many records walk one index space over the ranges
+// (built into the batched kernel, whose sparse instances have lists of a few
+// records per range; in the single-evaluation kernel the extra code slowed the
+// near field at 64 particles per leaf by 7%)
+constexpr uint32_t kSmallList = 64;
 
 struct LeafCtx {
     uint32_t t0, nt;           // the leaf's targets in sorted order
@@ -511,10 +516,38 @@ __device__ __forceinline__ void leaf_le_finish16(const Geometry& g, const float*
     __syncwarp();
 }
 
+// leaf_le_finish for P = 32, the loop unrolled by eight so that the table's
+// loads are issued eight at a time (the same operations in the same order).
+__device__ __forceinline__ void leaf_le_finish32(const Geometry& g, const float* __restrict__ l2l,
+                                                 uint32_t lx, uint32_t ly, const LeafLeParts& q,
+                                                 float2* out) {
+    const int lane = threadIdx.x & 31;
+    float2 v = q.own;
+    if (g.L >= 3) {
+        const float2* t = reinterpret_cast<const float2*>(l2l) +
+                          (int64_t)(((ly & 1u) << 1) | (lx & 1u)) * 32 * 32;
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            float2 pk = cshfl(q.par, k, 32);
+            v = cfma(t[k * 32 + lane], pk, v);
+        }
+    }
+    if (lane >= g.p) v = make_float2(0.f, 0.f);
+    __syncwarp();  // earlier readers of `out` are done
+    out[lane] = v;
+    __syncwarp();
+}
+
+// The leaf's local expansion by the unrolled form of its expansion width
+// (P is 16 or 32): the near-field kernels build one per leaf, and with a few
+// particles per leaf the chain of P table products is most of a leaf's time.
 __device__ __forceinline__ void leaf_le_build(const Geometry& g, const float* __restrict__ le,
                                               const float* __restrict__ l2l, uint32_t lx,
                                               uint32_t ly, float2* out) {
-    leaf_le_finish(g, l2l, lx, ly, leaf_le_load(g, le, lx, ly), out);
+    const LeafLeParts q = leaf_le_load(g, le, lx, ly);
+    if (g.P == 16) leaf_le_finish16(g, l2l, lx, ly, q, out);
+    else if (g.P == 32) leaf_le_finish32(g, l2l, lx, ly, q, out);
+    else leaf_le_finish(g, l2l, lx, ly, q, out);
 }
 
 // L2P (Eq. 12) added to a target's velocity: w = (1/s) sum_n L~_n zeta^n at
@@ -537,6 +570,7 @@ __device__ __forceinline__ void l2p_add(int p, float kzeta, float inv_s, const f
 // from the front (sources 0, 1, ...), nf far-band sources from the back
 // (sources kListCap - 1, kListCap - 2, ...), each band completed to whole
 // pairs by a dummy.
+template <bool kFlat>
 __device__ __forceinline__ void gather_bands(const float4* __restrict__ sp, const LeafCtx& c,
                                              const NearF32v3& nm, uint32_t cb, uint32_t cnt,
                                              float4* buf, uint32_t& nn, uint32_t& nf) {
@@ -545,9 +579,40 @@ __device__ __forceinline__ void gather_bands(const float4* __restrict__ sp, cons
     nn = 0;
     nf = 0;
     __syncwarp();  // earlier readers of the buffer are done
-    // range by range (no per-record range search); records keep their order
     const uint32_t ce = cb + cnt;
-    for (int r = 0; r < 9; ++r) {
+    if constexpr (kFlat) {
+        if (cnt <= kSmallList) {
+            // few records (sparse leaves): one index space over the 9 ranges,
+            // each lane finding its record's range, so that the list takes one
+            // or two batches instead of one per range; the same records in the
+            // same order
+            for (uint32_t g0 = cb; g0 < ce; g0 += 32) {
+                const uint32_t gv = g0 + lane;
+                float rx = 0.f, ry = 0.f, rg = 0.f;
+                bool ok = gv < ce, near = false;
+                if (ok) {
+                    int r = 0;
+                    while (gv >= c.rpre[r + 1]) ++r;
+                    float4 q = sp[c.rbeg[r] - c.rpre[r] + gv];
+                    rx = ((q.x - c.cxh) - c.cxl) * nm.sc;
+                    ry = ((q.y - c.cyh) - c.cyl) * nm.sc;
+                    rg = q.z;
+                    float ex = fmaxf(fabsf(rx) - nm.half_leaf, 0.f);
+                    float ey = fmaxf(fabsf(ry) - nm.half_leaf, 0.f);
+                    near = fmaf(ex, ex, ey * ey) < nm.band2;
+                }
+                const unsigned bn = __ballot_sync(0xffffffffu, near);
+                const unsigned bf = __ballot_sync(0xffffffffu, ok && !near);
+                if (near) put_source(buf, nn + __popc(bn & lt), rx, ry, rg);
+                else if (ok) put_source(buf, kListCap - 1 - (nf + __popc(bf & lt)), rx, ry, rg);
+                nn += __popc(bn);
+                nf += __popc(bf);
+            }
+            cnt = 0;  // done: the range loop below has nothing left
+        }
+    }
+    // range by range (no per-record range search); records keep their order
+    for (int r = 0; (!kFlat || cnt > 0) && r < 9; ++r) {
         const uint32_t lo = max(c.rpre[r], cb), hi = min(c.rpre[r + 1], ce);
         const uint32_t base = c.rbeg[r] - c.rpre[r];
         for (uint32_t g0 = lo; g0 < hi; g0 += 32) {
@@ -582,6 +647,7 @@ __device__ __forceinline__ void gather_bands(const float4* __restrict__ sp, cons
 // the cutoff of the leaf square (only those can be closer than a to a
 // target) into sources [0, nc) of buf, in scaled leaf-relative coordinates,
 // completed to whole pairs by a dummy.
+template <bool kFlat>
 __device__ __forceinline__ void gather_ring(const float4* __restrict__ sp, const LeafCtx& c,
                                             const NearF32v3& nm, uint32_t cb, uint32_t cnt,
                                             float4* buf, uint32_t& nc) {
@@ -590,7 +656,31 @@ __device__ __forceinline__ void gather_ring(const float4* __restrict__ sp, const
     nc = 0;
     __syncwarp();  // earlier readers of the buffer are done
     const uint32_t ce = cb + cnt;
-    for (int r = 0; r < 16; ++r) {
+    if constexpr (kFlat) {
+        if (cnt <= kSmallList) {  // few records: one index space over the 16 ranges
+            for (uint32_t g0 = cb; g0 < ce; g0 += 32) {
+                const uint32_t gv = g0 + lane;
+                float rx = 0.f, ry = 0.f, rg = 0.f;
+                bool keep = false;
+                if (gv < ce) {
+                    int r = 0;
+                    while (gv >= c.cpre[r + 1]) ++r;
+                    float4 q = sp[c.cbeg[r] - c.cpre[r] + gv];
+                    rx = ((q.x - c.cxh) - c.cxl) * nm.sc;
+                    ry = ((q.y - c.cyh) - c.cyl) * nm.sc;
+                    rg = q.z;
+                    float ex = fmaxf(fabsf(rx) - nm.half_leaf, 0.f);
+                    float ey = fmaxf(fabsf(ry) - nm.half_leaf, 0.f);
+                    keep = fmaf(ex, ex, ey * ey) < nm.band_a2;
+                }
+                const unsigned bk = __ballot_sync(0xffffffffu, keep);
+                if (keep) put_source(buf, nc + __popc(bk & lt), rx, ry, rg);
+                nc += __popc(bk);
+            }
+            cnt = 0;
+        }
+    }
+    for (int r = 0; (!kFlat || cnt > 0) && r < 16; ++r) {
         const uint32_t lo = max(c.cpre[r], cb), hi = min(c.cpre[r + 1], ce);
         const uint32_t base = c.cbeg[r] - c.cpre[r];
         for (uint32_t g0 = lo; g0 < hi; g0 += 32) {
@@ -627,7 +717,7 @@ __device__ __forceinline__ void gather_ring(const float4* __restrict__ sp, const
 // round of at most 16 targets as a one-per-lane pass, without the split
 // path: 10% faster at 64 targets per leaf.  (The plain kernel keeps both:
 // there the narrower build measured slower.)
-template <bool kCut, int kMaxT = 4, bool kSorted = false>
+template <bool kCut, int kMaxT = 4, bool kSorted = false, bool kFlat = false>
 __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
                                               const uint32_t* __restrict__ leaf_start,
                                               uint32_t leaf_base, uint32_t leaf, uint32_t a,
@@ -716,7 +806,7 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
     const uint32_t total = rpre[9];
     const bool one_chunk = total <= kListChunk && (!kCut || c.ctotal == 0);  // ring reuses buf
     uint32_t nn = 0, nf = 0;
-    if (one_chunk) gather_bands(sp, c, nm, 0, total, buf, nn, nf);
+    if (one_chunk) gather_bands<kFlat>(sp, c, nm, 0, total, buf, nn, nf);
 
     // far field (L2P, Eq. 12) plus near sum -> velocity of one target, at
     // its input index or (kSorted, near part alone) at its sorted position
@@ -748,14 +838,14 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
         }
         for (uint32_t cb = 0; cb < total; cb += kListChunk) {
             if (!one_chunk)
-                gather_bands(sp, c, nm, cb, min(kListChunk, total - cb), buf, nn, nf);
+                gather_bands<kFlat>(sp, c, nm, cb, min(kListChunk, total - cb), buf, nn, nf);
             band_loopT<kNearBand, T>(buf, 0, near_pairs(nn), nm, x, y, S);
             band_loopT<kFar, T>(buf, far_first(nf), kListCap / 2, nm, x, y, S);
         }
         if (kCut)
             for (uint32_t cb = 0; cb < c.ctotal; cb += kListChunk) {  // cutoff ring
                 uint32_t nc;
-                gather_ring(rsrc, c, nm, cb, min(kListChunk, c.ctotal - cb), buf, nc);
+                gather_ring<kFlat>(rsrc, c, nm, cb, min(kListChunk, c.ctotal - cb), buf, nc);
                 band_loopT<kRing, T>(buf, 0, near_pairs(nc), nm, x, y, S);
             }
 #pragma unroll
@@ -788,7 +878,7 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
         float su = 0.f, sv = 0.f, cu = 0.f, cv = 0.f;
         for (uint32_t cb = 0; cb < total; cb += kListChunk) {
             if (!one_chunk)
-                gather_bands(sp, c, nm, cb, min(kListChunk, total - cb), buf, nn, nf);
+                gather_bands<kFlat>(sp, c, nm, cb, min(kListChunk, total - cb), buf, nn, nf);
             band_loop_split<kNearBand>(buf, 0, near_pairs(nn), ns, sl, nm, x, y, su, sv, cu, cv);
             band_loop_split<kFar>(buf, far_first(nf), kListCap / 2, ns, sl, nm, x, y, su, sv, cu,
                                   cv);
@@ -796,7 +886,7 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
         if (kCut)
             for (uint32_t cb = 0; cb < c.ctotal; cb += kListChunk) {  // cutoff ring
                 uint32_t nc;
-                gather_ring(rsrc, c, nm, cb, min(kListChunk, c.ctotal - cb), buf, nc);
+                gather_ring<kFlat>(rsrc, c, nm, cb, min(kListChunk, c.ctotal - cb), buf, nc);
                 band_loop_split<kRing>(buf, 0, near_pairs(nc), ns, sl, nm, x, y, su, sv, cu, cv);
             }
         su += cu;
@@ -1011,7 +1101,8 @@ p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ ske
             nm.band_a2 = ni.band_a2;
             nm.wstrip = ni.wstrip;
             nm.ring_mask = ni.ring_mask;
-            p2p_chunk_f32<kCut, kCut ? 2 : 4>(sp, leaf_start, b.leaf_base, gleaf - b.leaf_base, a,
+            p2p_chunk_f32<kCut, kCut ? 2 : 4, false, true>(sp, leaf_start, b.leaf_base,
+                                                           gleaf - b.leaf_base, a,
                                               e, b.g, nm, le + b.exp_off,
                                               b.g.P <= 16 ? l2l16 : l2l32, uv, lists[warp],
                                               ranges[warp], leaf_le[warp], rs);
@@ -1262,6 +1353,8 @@ l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_
     }
     if (g.P == 16)
         leaf_le_finish16(g, l2l, lx, ly, q, leaf_le[warp]);
+    else if (g.P == 32)
+        leaf_le_finish32(g, l2l, lx, ly, q, leaf_le[warp]);
     else
         leaf_le_finish(g, l2l, lx, ly, q, leaf_le[warp]);
     if (k0 < t1) add(r0, w0.x, w0.y);
