@@ -437,9 +437,9 @@ __device__ __forceinline__ uint32_t far_first(uint32_t nf) {
 // Sources gathered into a buffer at a time: room for a dummy in each band.
 constexpr uint32_t kListChunk = kListCap - 2;
 // gathers of at most this many records walk one index space over the ranges
-// (built into the batched kernel, whose sparse instances have lists of a few
-// records per range; in the single-evaluation kernel the extra code slowed the
-// near field at 64 particles per leaf by 7%)
+// (built into the batched kernel (kFlat), whose sparse instances have lists of
+// a few records per range; in the single-evaluation kernel the extra code
+// slowed the near field at 64 particles per leaf by 7%)
 constexpr uint32_t kSmallList = 64;
 
 struct LeafCtx {
@@ -538,12 +538,20 @@ __device__ __forceinline__ void leaf_le_finish32(const Geometry& g, const float*
     __syncwarp();
 }
 
-// The leaf's local expansion by the unrolled form of its expansion width
-// (P is 16 or 32): the near-field kernels build one per leaf, and with a few
-// particles per leaf the chain of P table products is most of a leaf's time.
 __device__ __forceinline__ void leaf_le_build(const Geometry& g, const float* __restrict__ le,
                                               const float* __restrict__ l2l, uint32_t lx,
                                               uint32_t ly, float2* out) {
+    leaf_le_finish(g, l2l, lx, ly, leaf_le_load(g, le, lx, ly), out);
+}
+
+// The same by the unrolled form of its expansion width (P is 16 or 32): the
+// batched near-field kernel builds one per leaf, and with a few particles per
+// leaf the chain of P table products is most of a leaf's time.  (The
+// single-evaluation kernels leave the expansion to l2p_f32_kernel.)
+__device__ __forceinline__ void leaf_le_build_unrolled(const Geometry& g,
+                                                       const float* __restrict__ le,
+                                                       const float* __restrict__ l2l,
+                                                       uint32_t lx, uint32_t ly, float2* out) {
     const LeafLeParts q = leaf_le_load(g, le, lx, ly);
     if (g.P == 16) leaf_le_finish16(g, l2l, lx, ly, q, out);
     else if (g.P == 32) leaf_le_finish32(g, l2l, lx, ly, q, out);
@@ -799,7 +807,8 @@ __device__ __forceinline__ void p2p_chunk_f32(const float4* __restrict__ sp,
     leaf_centre_hilo(g, lx, ly, &c.cxh, &c.cxl, &c.cyh, &c.cyl);
     c.le_leaf = nullptr;
     if (g.L >= 2 && le) {  // null le: near field only, the far field is added later
-        leaf_le_build(g, le, l2l, lx, ly, leaf_le);
+        if constexpr (kFlat) leaf_le_build_unrolled(g, le, l2l, lx, ly, leaf_le);
+        else leaf_le_build(g, le, l2l, lx, ly, leaf_le);
         c.le_leaf = reinterpret_cast<const float*>(leaf_le);
     }
     const float4* rsrc = rs.rec && nm.wstrip > 0.f ? rs.rec : sp;  // where the ring ranges point
