@@ -1,10 +1,14 @@
 """Run full FMM evaluations of a named synthetic workload on cuda:0.
 
     python -m paper_0809_1810_gb300.run_workload --workload uniform_1m --steps 3 [--p P --L L]
+    python -m paper_0809_1810_gb300.run_workload --workload batch_sweep --steps 3
 
-Each step is one complete fmm2d_velocity call (tree build to velocities);
-this is the command the profiler summaries under profiles/ are taken with.
-Prints the mean step time from CUDA events.
+Each step is one complete fmm2d_velocity call (tree build to velocities),
+or for batch_sweep one fmm2d_batch_velocity call over the 512 instances of
+the batched benchmark (FP32_TC, each instance with the Sec. 4.1 cutoff for
+1e-6 where its leaves are narrower than it, default launch shapes); this is
+the command the profiler summaries under profiles/ are taken with.  Prints
+the mean step time from CUDA events.
 """
 from __future__ import annotations
 
@@ -19,7 +23,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 import workloads as W  # noqa: E402
 
-from . import Plan  # noqa: E402
+from . import BatchPlan, Plan, cutoff_for  # noqa: E402
 
 WORKLOADS = {
     "lamb_oseen_4096": lambda: W.lamb_oseen_lattice(64, p=10, L=3, dtype=np.float32),
@@ -31,9 +35,36 @@ WORKLOADS = {
 }
 
 
+def run_batch_sweep(args):
+    ws = [W.make_instance(s) for s in W.batch_instances(512, seed=3)]
+    xy = torch.tensor(np.concatenate([np.stack([w.x, w.y], 1) for w in ws]), device="cuda")
+    g = torch.tensor(np.concatenate([w.gamma for w in ws]), device="cuda")
+    insts = [{"n": w.n, "p": w.p, "L": w.L, "sigma": w.sigma, "root": w.root,
+              "cutoff": cutoff_for(w.sigma, w.root[2] / 2 ** w.L, 1e-6) if w.L >= 2 else 0.0}
+             for w in ws]
+    with BatchPlan(insts, precision="fp32_tc") as bp:
+        uv = torch.empty((bp.n_total, 2), dtype=torch.float32, device="cuda")
+        for _ in range(args.warmup):
+            bp.velocity(xy, g, out=uv)
+        bp.check()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            bp.velocity(xy, g, out=uv)
+        b.record()
+        bp.check()
+        print(f"batch_sweep fp32_tc: {len(ws)} instances, n={bp.n_total} "
+              f"{a.elapsed_time(b) / max(args.steps, 1):.4f} ms/batch")
+        if args.phases:
+            ph = bp.profile(xy, g, uv)
+            print("  phases (ms): " + ", ".join(f"{k} {v:.4f}" for k, v in ph.items()))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="uniform_1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="uniform_1m",
+                    choices=sorted(WORKLOADS) + ["batch_sweep"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_tc", "fp64"])
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
@@ -44,6 +75,9 @@ def main():
     ap.add_argument("--phases", action="store_true",
                     help="also print the mean per-phase times (events inside the graph)")
     args = ap.parse_args()
+    if args.workload == "batch_sweep":
+        run_batch_sweep(args)
+        return
     w = WORKLOADS[args.workload]()
     if args.p is not None:
         w.p = args.p
