@@ -66,8 +66,9 @@ struct fmm2d_batch_plan {
     float* tab32[2] = {nullptr, nullptr};
     bool has_class[2] = {false, false};
     BatchLists lists[2]{};
-    // launch shapes (autotuned)
-    int p2p_ctas_per_sm = 4;
+    // launch shapes (autotuned; the near field's default is the residency
+    // limit of its kernels, which the autotuner picked on every sweep measured)
+    int p2p_ctas_per_sm = 6;
     int m2l_threads = 128;
     // FP32_TC: one tensor-core M2L class per Pk (operator stages and tile
     // policy autotuned); FP32: M2L on the CUDA cores

@@ -36,7 +36,7 @@ WORKLOADS = {
 
 
 def run_batch_sweep(args):
-    ws = [W.make_instance(s) for s in W.batch_instances(512, seed=3)]
+    ws = [W.make_instance(s) for s in W.batch_instances(512, seed=3)[:args.instances]]
     xy = torch.tensor(np.concatenate([np.stack([w.x, w.y], 1) for w in ws]), device="cuda")
     g = torch.tensor(np.concatenate([w.gamma for w in ws]), device="cuda")
     insts = [{"n": w.n, "p": w.p, "L": w.L, "sigma": w.sigma, "root": w.root,
@@ -74,6 +74,8 @@ def main():
                     help="cutoff a of Sec. 4.1 in units of sigma (0: the plain 3x3 rule)")
     ap.add_argument("--phases", action="store_true",
                     help="also print the mean per-phase times (events inside the graph)")
+    ap.add_argument("--instances", type=int, default=512,
+                    help="batch_sweep: the first this many of its 512 instances")
     args = ap.parse_args()
     if args.workload == "batch_sweep":
         run_batch_sweep(args)
