@@ -78,6 +78,7 @@ struct fmm2d_batch_plan {
     int tc_policy = 0;
     bool any_cutoff = false;
     RingStrips strips{};  // with a cutoff: the near field's ring strips
+    uint32_t* lane_pos = nullptr;  // queue of the per-target-lane pass (null: no sparse instance)
     // graph
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
@@ -146,7 +147,7 @@ cudaError_t enqueue_batch(fmm2d_batch_plan* b, const float* xy, const float* gam
                            b->sb.keys[sort_passes(b->key_bits) & 1], b->sb.leaf_start, b->le,
                            b->has_class[0] ? tab_l2l(b, 0) : nullptr,
                            b->has_class[1] ? tab_l2l(b, 1) : nullptr, uv, b->any_cutoff, b->strips,
-                           b->nleaf_total, s));
+                           b->nleaf_total, b->lane_pos, s));
     BMARK(5);
 #undef BMARK
 #undef BSTEP
@@ -351,6 +352,10 @@ fmm2d_status fmm2d_batch_plan_create_ex(fmm2d_batch_plan** out, int count,
     const bool want_strips = b->any_cutoff && nmax < ((int64_t)1 << 30);
     sizes.push_back(a256(want_strips ? 16 * 4 * (size_t)nmax : 0));
     sizes.push_back(a256(want_strips ? 16 * (size_t)nleaf : 0));
+    // the per-target-lane pass's queue, when an instance has sparse leaves
+    bool want_lanes = false;
+    for (const BatchInst& bi : b->inst) want_lanes = want_lanes || near_lane_path(bi.n, bi.g.L);
+    sizes.push_back(a256(want_lanes ? 4 * (size_t)nmax : 0));
     size_t lists_bytes = 0;
     for (int c = 0; c < 2; ++c) {
         lists_bytes += a256(4 * quad_inst[c].size() + 4) * 2 + a256(4 * m2l_inst[c].size() + 4) +
@@ -395,6 +400,10 @@ fmm2d_status fmm2d_batch_plan_create_ex(fmm2d_batch_plan** out, int count,
         float4* rec = (float4*)take(sizes[k++]);
         uint32_t* cnt = (uint32_t*)take(sizes[k++]);
         if (want_strips) b->strips = RingStrips{rec, cnt};
+    }
+    {
+        uint32_t* q = (uint32_t*)take(sizes[k++]);
+        if (want_lanes) b->lane_pos = q;
     }
     b->sb.status = b->d_status;
 
@@ -540,7 +549,7 @@ fmm2d_status fmm2d_batch_autotune(fmm2d_batch_plan* b, const float* xy, const fl
                                     b->sb.leaf_start, b->le,
                                     b->has_class[0] ? tab_l2l(b, 0) : nullptr,
                                     b->has_class[1] ? tab_l2l(b, 1) : nullptr, uv,
-                                    b->any_cutoff, b->strips, b->nleaf_total, s);
+                                    b->any_cutoff, b->strips, b->nleaf_total, b->lane_pos, s);
         });
         if (ms < best) {
             best = ms;

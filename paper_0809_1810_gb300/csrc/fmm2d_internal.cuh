@@ -157,10 +157,14 @@ template <typename R>
 cudaError_t launch_m2l(const Geometry& g, const Tables<R>& t, const R* me, R* le, cudaStream_t s);
 template <typename R>
 cudaError_t launch_l2l(const Geometry& g, const Tables<R>& t, R* le, cudaStream_t s);
+// lane_pos (FP32 forms; may be null): room for n sorted positions, the
+// queue of targets in sparse leaves that the per-target-lane pass takes
+// (counter then needs two words: the work counter and the queue length).
 template <typename R>
 cudaError_t launch_p2p_l2p(const Geometry& g, double sigma, int64_t n, const void* particles,
                            const uint32_t* skeys, const uint32_t* leaf_start, uint32_t* counter,
-                           const R* le, const R* l2l, R* uv, cudaStream_t s);
+                           const R* le, const R* l2l, R* uv, uint32_t* lane_pos,
+                           cudaStream_t s);
 // The FP32 near field without its far part, written to `out` (2 floats per
 // target) at the input indices or (sorted_out) in sorted order, and the L2P
 // that adds the far part afterwards -- reading the near parts in sorted order
@@ -181,7 +185,7 @@ struct RingStrips {
 cudaError_t launch_near_only_f32(const Geometry& g, double sigma, int64_t n,
                                  const void* particles, const uint32_t* skeys,
                                  const uint32_t* leaf_start, uint32_t* counter, float* out,
-                                 bool sorted_out, RingStrips strips,
+                                 bool sorted_out, RingStrips strips, uint32_t* lane_pos,
                                  cudaStream_t s);
 cudaError_t launch_l2p_f32(const Geometry& g, double sigma, const void* particles,
                            const uint32_t* leaf_start, const float* le, const float* l2l,
@@ -243,7 +247,10 @@ cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
                              int ctas_per_sm, const void* particles, const uint32_t* skeys,
                              const uint32_t* leaf_start, const float* le, const float* l2l16,
                              const float* l2l32, float* uv, bool cut, RingStrips strips,
-                             uint32_t nleaf_total, cudaStream_t s);
+                             uint32_t nleaf_total, uint32_t* lane_pos, cudaStream_t s);
+// Whether an evaluation of n particles over 4^L leaves sends its sparse
+// leaves to the per-target-lane pass of the FP32 near field.
+bool near_lane_path(int64_t n, int L);
 cudaError_t launch_batch_direct(const BatchInst* inst, const int64_t* dev_offsets, int count,
                                 int kernel, const float* xy, const float* gamma, int64_t s_count,
                                 const int64_t* targets, double* uv_ref, int* status,

@@ -249,6 +249,8 @@ struct NearF32v3 {
                               // width) holding every source the leaf two leaves away
                               // on that side keeps (0: no cutoff)
     uint32_t ring_mask;       // ring leaves (bit r, ring_offset order) nearer than a
+    uint32_t lane_nt;         // leaves of at most this many targets go to the
+                              // per-target-lane pass (0: none)
     float coef[kF32Deg + 1];  // g(q2) ~ sum_k coef[k] q2^k on [0, qthr)
 };
 
@@ -943,12 +945,38 @@ static WorkSplit work_split(uint64_t n, uint64_t warps) {
     return WorkSplit{(uint32_t)n, span, (uint32_t)nbig, (uint32_t)(nbig + (rest + 31) / 32)};
 }
 
+// Sparse leaves (Sec. 3.3.1's local lists of a few particles each): with at
+// most kLaneMaxT targets a leaf would leave most of a warp idle, and its
+// fixed costs (the ranges of its 25 neighbours, the gathers, its local
+// expansion) outweigh its pairs.  In an evaluation whose mean occupancy is
+// at most kLaneMean particles per leaf, such leaves are queued instead, and
+// the per-target-lane pass (p2p_lane_kernel) gives each queued target a lane
+// of its own.  The choice depends on the leaf's count and the evaluation's
+// n and L alone, so a target gets the same arithmetic in a single and a
+// batched evaluation, whatever warp it lands in.
+constexpr uint32_t kLaneMaxT = 16;
+constexpr int64_t kLaneMean = 32;
+
+// Targets queued for the per-target-lane pass: their sorted positions, and
+// the queue's length (zeroed before the near-field launch).  Null pos: no
+// queue (every leaf takes the warp path).
+struct LaneQueue {
+    uint32_t* pos;
+    uint32_t* count;
+};
+
 // f(key, a, b) for every chunk or round that item w owns: key the leaf index
 // into leaf_start, [a, b) its targets within the leaf.  Warp-uniform calls.
-template <typename F>
+// kQueue: a leaf of nt <= kLaneMaxT targets whose gate(key) (the
+// evaluation's bound, 0 or kLaneMaxT) admits it is queued instead, its nt
+// positions appended to lq by one atomic per warp step (the kernels are
+// compiled with and without the queue: its registers cost the dense
+// evaluations that never use it).
+template <bool kQueue, typename Gate, typename F>
 __device__ __forceinline__ void for_each_piece(const uint32_t* __restrict__ skeys,
                                                const uint32_t* __restrict__ leaf_start,
-                                               const WorkSplit& ws, uint32_t w, F&& f) {
+                                               const WorkSplit& ws, uint32_t w,
+                                               const LaneQueue& lq, Gate&& gate, F&& f) {
     const int lane = threadIdx.x & 31;
     const bool big = w < ws.nbig;
     const uint32_t split = ws.nbig * ws.span;
@@ -957,7 +985,7 @@ __device__ __forceinline__ void for_each_piece(const uint32_t* __restrict__ skey
     const uint32_t r1 = min(r0 + span, ws.n);
     for (uint32_t base = r0; base < r1; base += 32) {
         const uint32_t r = base + lane;
-        uint32_t key = 0, first = 0;
+        uint32_t key = 0, first = 0, nt = 0;
         bool starts = false;
         if (r < r1) {
             key = skeys[r];
@@ -965,6 +993,23 @@ __device__ __forceinline__ void for_each_piece(const uint32_t* __restrict__ skey
             const uint32_t off = r - first;
             starts = (off & (span - 1)) == 0 &&
                      (big || first + (off & ~(ws.span - 1)) >= split);
+            if (kQueue && starts) nt = leaf_start[key + 1] - first;
+        }
+        if constexpr (kQueue) {
+            const bool defer = starts && r == first && nt <= kLaneMaxT && nt <= gate(key);
+            if (__ballot_sync(0xffffffffu, defer)) {
+                uint32_t incl = defer ? nt : 0u;  // inclusive prefix of the queued counts
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                uint32_t at = 0;
+                if (lane == 31) at = atomicAdd(lq.count, incl);
+                at = __shfl_sync(0xffffffffu, at, 31) + incl - nt;
+                if (defer)
+                    for (uint32_t j = 0; j < nt; ++j) lq.pos[at + j] = r + j;
+                starts = starts && !defer;
+            }
         }
         unsigned m = __ballot_sync(0xffffffffu, starts);
         while (m) {
@@ -973,8 +1018,9 @@ __device__ __forceinline__ void for_each_piece(const uint32_t* __restrict__ skey
             const uint32_t k = __shfl_sync(0xffffffffu, key, src);
             const uint32_t f0 = __shfl_sync(0xffffffffu, first, src);
             const uint32_t a = base + (uint32_t)src - f0;
-            const uint32_t nt = leaf_start[k + 1] - f0;
-            f(k, a, min(a + span, nt));
+            const uint32_t ntk =
+                kQueue ? __shfl_sync(0xffffffffu, nt, src) : leaf_start[k + 1] - f0;
+            f(k, a, min(a + span, ntk));
         }
     }
 }
@@ -983,22 +1029,25 @@ __device__ __forceinline__ void for_each_piece(const uint32_t* __restrict__ skey
 // items from a counter (zeroed before the launch) until none is left, so
 // crowded windows balance against light ones and no SM idles behind a
 // partial last wave.
-template <bool kCut, int kMaxT, bool kSorted>
+template <bool kCut, int kMaxT, bool kSorted, bool kQueue>
 __global__ void __launch_bounds__(kLeafWarps * 32, 6)
 p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skeys,
                    const uint32_t* __restrict__ leaf_start, WorkSplit ws, uint32_t* counter,
                    Geometry g, NearF32v3 nm, const float* __restrict__ le,
-                   const float* __restrict__ l2l, float* __restrict__ uv, RingStrips rs) {
+                   const float* __restrict__ l2l, float* __restrict__ uv, RingStrips rs,
+                   LaneQueue lq) {
     __shared__ float4 lists[kLeafWarps][kListCap];
     __shared__ uint32_t ranges[kLeafWarps][kCut ? 52 : 20];
     __shared__ float2 leaf_le[kLeafWarps][kMaxP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    auto gate = [&](uint32_t) { return nm.lane_nt; };
     for (;;) {
         uint32_t w = 0;
         if (lane == 0) w = atomicAdd(counter, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= ws.items) break;
-        for_each_piece(skeys, leaf_start, ws, w, [&](uint32_t leaf, uint32_t a, uint32_t b) {
+        for_each_piece<kQueue>(skeys, leaf_start, ws, w, lq, gate,
+                               [&](uint32_t leaf, uint32_t a, uint32_t b) {
             p2p_chunk_f32<kCut, kMaxT, kSorted>(sp, leaf_start, 0, leaf, a, b, g, nm, le, l2l,
                                                 uv, lists[warp], ranges[warp], leaf_le[warp], rs);
         });
@@ -1011,6 +1060,7 @@ struct NearInst {
     float qa, band_a2;   // the instance's cutoff of Sec. 4.1 (0: none)
     float wstrip;        // its ring strips' width
     uint32_t ring_mask;  // its ring leaves nearer than a
+    uint32_t lane_nt;    // its sparse leaves' bound for the per-target-lane pass
 };
 
 // Ring strips of the cutoff (Sec. 4.1), one warp per leaf: the leaf's
@@ -1079,24 +1129,27 @@ ring_strips_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ l
 // (all instances, packed) from a work counter.  kCut compiles in the cutoff
 // ring of Sec. 4.1 for batches where some instance has a cutoff (the others
 // have an empty ring and skip it).
-template <bool kCut>
+template <bool kCut, bool kQueue>
 __global__ void __launch_bounds__(kLeafWarps * 32, 6)
 p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skeys,
                  const uint32_t* __restrict__ leaf_start, const BatchInst* __restrict__ inst,
                  const NearInst* __restrict__ near_inst, const int32_t* __restrict__ leaf_inst,
                  WorkSplit ws, uint32_t* counter, NearF32v3 shared_nm,
                  const float* __restrict__ le, const float* __restrict__ l2l16,
-                 const float* __restrict__ l2l32, float* __restrict__ uv, RingStrips rs) {
+                 const float* __restrict__ l2l32, float* __restrict__ uv, RingStrips rs,
+                 LaneQueue lq) {
     __shared__ float4 lists[kLeafWarps][kListCap];
     __shared__ uint32_t ranges[kLeafWarps][kCut ? 52 : 20];
     __shared__ float2 leaf_le[kLeafWarps][kMaxP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    auto gate = [&](uint32_t gleaf) { return near_inst[leaf_inst[gleaf]].lane_nt; };
     for (;;) {
         uint32_t w = 0;
         if (lane == 0) w = atomicAdd(counter, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= ws.items) break;
-        for_each_piece(skeys, leaf_start, ws, w, [&](uint32_t gleaf, uint32_t a, uint32_t e) {
+        for_each_piece<kQueue>(skeys, leaf_start, ws, w, lq, gate,
+                               [&](uint32_t gleaf, uint32_t a, uint32_t e) {
             const int i = leaf_inst[gleaf];
             const BatchInst& b = inst[i];
             NearF32v3 nm = shared_nm;
@@ -1116,6 +1169,226 @@ p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ ske
                                               b.g.P <= 16 ? l2l16 : l2l32, uv, lists[warp],
                                               ranges[warp], leaf_le[warp], rs);
         });
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-target-lane pass over the queued targets of sparse leaves.
+//
+// Each lane takes one queued target and walks its local list itself: the 9
+// ranges of its leaf's 3x3 neighbourhood, then (with a cutoff) the 16 ring
+// ranges, reading the sorted records from global memory (the lanes of one
+// leaf read the same records: one broadcast), two records per step as one
+// packed pair.  Every pair of the 3x3 block takes the near-band form (the
+// polynomial below qthr), every ring pair the cutoff correction.  The
+// walk's trip count is the warp's longest list; a lane past its own end
+// evaluates dummies (zero circulation, far away).  Sums: blocks of
+// kLanePairs pairs into fresh registers, then compensated.  Far field (when
+// le is given): the warp forms the local expansion of each leaf it holds
+// once, with the warp path's operations (leaf_le_build_unrolled), in shared
+// memory, and each lane adds its own L2P (l2p_add).  A target's arithmetic
+// does not depend on which warp or lane takes it.
+// ---------------------------------------------------------------------------
+constexpr int kLaneRanges = 25;      // 9 local + 16 ring
+constexpr uint32_t kLanePairs = 32;  // pairs per first-level partial sum
+
+union LaneSmem {
+    struct {
+        uint32_t beg[kLaneRanges][32];  // range r of lane l at [r][l]
+        uint32_t end[kLaneRanges][32];
+    } r;
+    float2 le[32][kMaxP + 1];  // one local expansion per leaf of the warp
+};
+
+// Leaf centre as FP32 hi/lo pairs for the calling lane alone (the table, or
+// the FP64 formula the table is built with: the same values).
+__device__ __forceinline__ void lane_centre_hilo(const Geometry& g, uint32_t ix, uint32_t iy,
+                                                 float* cxh, float* cxl, float* cyh,
+                                                 float* cyl) {
+    if (g.centre_tab) {
+        const float4 a = g.centre_tab[ix], b = g.centre_tab[iy];
+        *cxh = a.x;
+        *cxl = a.y;
+        *cyh = b.z;
+        *cyl = b.w;
+    } else {
+        centre_hilo_1d(g.x0, g.W, g.L, ix, cxh, cxl);
+        centre_hilo_1d(g.y0, g.W, g.L, iy, cyh, cyl);
+    }
+}
+
+// The lane's records of ranges [r, r_end) in order against its target, two
+// per step for `steps` steps (the warp's longest walk).
+template <int kMode>
+__device__ __forceinline__ void lane_walk(const float4* __restrict__ sp, const LaneSmem& sm,
+                                          int r, int r_end, uint32_t steps, const NearF32v3& nm,
+                                          float cxh, float cxl, float cyh, float cyl, float x,
+                                          float y, float& su, float& sv, float& cu, float& cv) {
+    const int lane = threadIdx.x & 31;
+    uint32_t pos = sm.r.beg[r][lane], end = sm.r.end[r][lane];
+    // the next record's position (false: the lane's list is done)
+    auto next = [&](uint32_t& at) {
+        while (pos == end && r + 1 < r_end) {
+            ++r;
+            pos = sm.r.beg[r][lane];
+            end = sm.r.end[r][lane];
+        }
+        at = pos;
+        if (pos == end) return false;
+        ++pos;
+        return true;
+    };
+    const float2 tx = f2_dup(x), ty = f2_dup(y);
+    float2 iu = make_float2(0.f, 0.f), iv = iu;
+#pragma unroll 1
+    for (uint32_t k = 0; k < steps; ++k) {
+        uint32_t ia, ib;
+        const bool va = next(ia), vb = next(ib);
+        const float4 qa = sp[va ? ia : 0u], qb = sp[vb ? ib : 0u];  // both loads in flight
+        const float xa = va ? ((qa.x - cxh) - cxl) * nm.sc : kFarAway;
+        const float ya = va ? ((qa.y - cyh) - cyl) * nm.sc : kFarAway;
+        const float ga = va ? qa.z : 0.f;
+        const float xb = vb ? ((qb.x - cxh) - cxl) * nm.sc : kFarAway;
+        const float yb = vb ? ((qb.y - cyh) - cyl) * nm.sc : kFarAway;
+        const float gb = vb ? qb.z : 0.f;
+        pair_sources<kMode>(nm, make_float4(xa, xb, ya, yb), make_float4(ga, gb, -ga, -gb), tx,
+                            ty, iu, iv);
+        if (k % kLanePairs == kLanePairs - 1) {
+            neumaier_add(su, cu, iu.x + iu.y);
+            neumaier_add(sv, cv, iv.x + iv.y);
+            iu = iv = make_float2(0.f, 0.f);
+        }
+    }
+    neumaier_add(su, cu, iu.x + iu.y);
+    neumaier_add(sv, cv, iv.x + iv.y);
+}
+
+// Persistent: each warp takes 32 queued targets at a time.  kBatch: the
+// targets belong to the instances of a batch (each lane its own instance's
+// geometry and constants); otherwise to one evaluation (g, nm).  kSorted:
+// near parts alone at the sorted positions (le null); otherwise at the
+// input indices.
+template <bool kBatch, bool kCut, bool kSorted>
+__global__ void __launch_bounds__(kLeafWarps * 32, 6)
+p2p_lane_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skeys,
+                const uint32_t* __restrict__ leaf_start, LaneQueue lq, Geometry g, NearF32v3 nm,
+                const BatchInst* __restrict__ inst, const NearInst* __restrict__ near_inst,
+                const int32_t* __restrict__ leaf_inst, const float* __restrict__ le,
+                const float* __restrict__ l2l16, const float* __restrict__ l2l32,
+                float* __restrict__ uv) {
+    __shared__ LaneSmem smem[kLeafWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    LaneSmem& sm = smem[warp];
+    const uint32_t count = *lq.count;
+    for (uint32_t gw = blockIdx.x * kLeafWarps + warp; gw * 32u < count;
+         gw += gridDim.x * kLeafWarps) {
+        const uint32_t qi = gw * 32u + lane;
+        const bool active = qi < count;  // lane 0 always is
+        const uint32_t r = lq.pos[active ? qi : gw * 32u];
+        const uint32_t key = skeys[r];
+        // the target's evaluation: geometry, constants, first leaf
+        int ii = 0;
+        uint32_t leaf_base = 0;
+        NearF32v3 m = nm;
+        const Geometry* gp = &g;
+        if constexpr (kBatch) {
+            ii = leaf_inst[key];
+            const NearInst ni = near_inst[ii];
+            m.sc = ni.sc;
+            m.kvel = ni.kvel;
+            m.kzeta = ni.kzeta;
+            m.inv_s = ni.inv_s;
+            m.qa = ni.qa;
+            m.ring_mask = ni.ring_mask;
+            leaf_base = inst[ii].leaf_base;
+            gp = &inst[ii].g;
+        }
+        const int L = gp->L;
+        const int nl = 1 << L;
+        const uint32_t leaf = key - leaf_base;
+        const uint32_t lx = morton_compact(leaf), ly = morton_compact(leaf >> 1);
+        const float4 rec = sp[r];
+        float cxh, cxl, cyh, cyl;
+        lane_centre_hilo(*gp, lx, ly, &cxh, &cxl, &cyh, &cyl);
+        const float x = ((rec.x - cxh) - cxl) * m.sc, y = ((rec.y - cyh) - cyl) * m.sc;
+
+        // the lane's ranges: 3x3 block in row order, then the ring
+        __syncwarp();  // the warp's previous readers of sm are done
+        uint32_t tot_l = 0, tot_r = 0;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int sx = (int)lx + q % 3 - 1, sy = (int)ly + q / 3 - 1;
+            uint32_t b = 0, e = 0;
+            if (active && sx >= 0 && sy >= 0 && sx < nl && sy < nl) {
+                const uint32_t k = leaf_base + morton_key((uint32_t)sx, (uint32_t)sy);
+                b = leaf_start[k];
+                e = leaf_start[k + 1];
+            }
+            sm.r.beg[q][lane] = b;
+            sm.r.end[q][lane] = e;
+            tot_l += e - b;
+        }
+        if (kCut) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                int dx, dy;
+                ring_offset(q, &dx, &dy);
+                const int sx = (int)lx + dx, sy = (int)ly + dy;
+                uint32_t b = 0, e = 0;
+                if (active && ((m.ring_mask >> q) & 1u) && sx >= 0 && sy >= 0 && sx < nl &&
+                    sy < nl) {
+                    const uint32_t k = leaf_base + morton_key((uint32_t)sx, (uint32_t)sy);
+                    b = leaf_start[k];
+                    e = leaf_start[k + 1];
+                }
+                sm.r.beg[9 + q][lane] = b;
+                sm.r.end[9 + q][lane] = e;
+                tot_r += e - b;
+            }
+        }
+        __syncwarp();
+        float su = 0.f, sv = 0.f, cu = 0.f, cv = 0.f;
+        lane_walk<kNearBand>(sp, sm, 0, 9, __reduce_max_sync(0xffffffffu, (tot_l + 1) >> 1), m,
+                             cxh, cxl, cyh, cyl, x, y, su, sv, cu, cv);
+        if (kCut) {
+            const uint32_t steps = __reduce_max_sync(0xffffffffu, (tot_r + 1) >> 1);
+            if (steps)
+                lane_walk<kRing>(sp, sm, 9, kLaneRanges, steps, m, cxh, cxl, cyh, cyl, x, y, su,
+                                 sv, cu, cv);
+        }
+        su += cu;
+        sv += cv;
+        float u = __fmul_rn(m.kvel, su), v = __fmul_rn(m.kvel, sv);
+
+        if (le) {  // far field: the local expansion of each leaf of the warp, once
+            __syncwarp();  // the ranges are done with; sm now holds expansions
+            const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+            const bool lead = active && (lane == 0 || prev != key);
+            const unsigned lm = __ballot_sync(0xffffffffu, lead);
+            const unsigned upto = lane == 31 ? 0xffffffffu : (2u << lane) - 1u;
+            const int slot = __popc(lm & upto) - 1;  // this lane's leaf
+            for (unsigned todo = lm; todo; todo &= todo - 1) {
+                const int j = __ffs(todo) - 1;
+                const int sj = __popc(lm & ((1u << j) - 1u));
+                const uint32_t jlx = __shfl_sync(0xffffffffu, lx, j);
+                const uint32_t jly = __shfl_sync(0xffffffffu, ly, j);
+                if constexpr (kBatch) {
+                    const BatchInst& b = inst[__shfl_sync(0xffffffffu, ii, j)];
+                    if (b.g.L >= 2)
+                        leaf_le_build_unrolled(b.g, le + b.exp_off, b.g.P <= 16 ? l2l16 : l2l32,
+                                               jlx, jly, sm.le[sj]);
+                } else {
+                    if (g.L >= 2) leaf_le_build_unrolled(g, le, l2l16, jlx, jly, sm.le[sj]);
+                }
+            }
+            __syncwarp();
+            if (active && L >= 2) l2p_add(gp->p, m.kzeta, m.inv_s, sm.le[slot], x, y, u, v);
+        }
+        if (active) {
+            const uint32_t o = kSorted ? r : __float_as_uint(rec.w);
+            uv[2 * (int64_t)o] = u;
+            uv[2 * (int64_t)o + 1] = v;
+        }
     }
 }
 
@@ -1213,6 +1486,7 @@ static NearF32v3 near_constants(double sigma, const Geometry& g, bool* ok) {
     // the ring is gathered from whole leaves (wstrip 0)
     nm.wstrip = qa > 0.0 && wstrip <= hl ? (float)wstrip : 0.f;
     nm.ring_mask = ring_mask(g);
+    nm.lane_nt = 0;  // set by the launch from its particle count
     double coef[kF32Deg + 1];
     *ok = fit_near_polynomial(qthr, coef) <= 1e-8;
     for (int k = 0; k <= kF32Deg; ++k) nm.coef[k] = (float)coef[k];
@@ -1229,23 +1503,33 @@ static unsigned resident_ctas(const void* kernel) {
     return (unsigned)std::max(1, sms * std::max(per_sm, 1));
 }
 
+bool near_lane_path(int64_t n, int L) { return n > 0 && n <= (kLaneMean << (2 * L)); }
+
 // The FP32 near-field launch: the whole persistent grid (all CTAs that fit
 // on the GPU at once), work counter zeroed first.  With le null it writes the
 // near part alone, at the input indices or (sorted_out) in sorted order.
+// With lane_pos and a sparse evaluation (near_lane_path), leaves of at most
+// kLaneMaxT targets are queued there and the per-target-lane pass follows.
 static cudaError_t launch_near_f32(const Geometry& g, double sigma, int64_t n,
                                    const void* particles, const uint32_t* skeys,
                                    const uint32_t* leaf_start, uint32_t* counter,
                                    const float* le, const float* l2l, float* uv, bool sorted_out,
-                                   RingStrips rs, cudaStream_t s) {
+                                   RingStrips rs, uint32_t* lane_pos, cudaStream_t s) {
     bool ok;
     NearF32v3 nm = near_constants(sigma, g, &ok);
     if (!ok) return cudaErrorInvalidValue;
     if (n == 0) return cudaSuccess;
+    LaneQueue lq{nullptr, nullptr};
+    if (lane_pos && near_lane_path(n, g.L)) {
+        nm.lane_nt = kLaneMaxT;
+        lq = LaneQueue{lane_pos, counter + 1};
+    }
     const bool cut = nm.ring_mask != 0;  // some ring leaf can hold a pair closer than a
     auto kernel_of = [&](int max_t) {
-        return cut ? (max_t >= 4 ? reinterpret_cast<const void*>(p2p_l2p_f32_kernel<true, 4, false>)
-                                 : reinterpret_cast<const void*>(p2p_l2p_f32_kernel<true, 2, false>))
-                   : reinterpret_cast<const void*>(p2p_l2p_f32_kernel<false, 4, false>);
+        return cut ? (max_t >= 4
+                          ? reinterpret_cast<const void*>(p2p_l2p_f32_kernel<true, 4, false, false>)
+                          : reinterpret_cast<const void*>(p2p_l2p_f32_kernel<true, 2, false, false>))
+                   : reinterpret_cast<const void*>(p2p_l2p_f32_kernel<false, 4, false, false>);
     };
     const unsigned resident = resident_ctas(kernel_of(4));
     const WorkSplit ws = work_split((uint64_t)n, (uint64_t)resident * kLeafWarps);
@@ -1254,7 +1538,7 @@ static cudaError_t launch_near_f32(const Geometry& g, double sigma, int64_t n,
     if (resident_ctas(kernel_of(max_t)) != resident) return cudaErrorInvalidConfiguration;
     const unsigned needed = (ws.items + kLeafWarps - 1) / kLeafWarps;
     const unsigned blocks = std::min(needed, resident);
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+    cudaError_t e = cudaMemsetAsync(counter, 0, (lq.pos ? 2 : 1) * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const float4* sp = reinterpret_cast<const float4*>(particles);
     if (!cut || !rs.n || !(nm.wstrip > 0.f)) rs.rec = nullptr;
@@ -1269,34 +1553,57 @@ static cudaError_t launch_near_f32(const Geometry& g, double sigma, int64_t n,
         if (resident_ctas(reinterpret_cast<const void*>(kernel)) != resident)
             return cudaErrorInvalidConfiguration;
         kernel<<<dim3(blocks), dim3(kLeafWarps * 32), 0, s>>>(sp, skeys, leaf_start, ws, counter,
-                                                              g, nm, le, l2l, uv, rs);
+                                                              g, nm, le, l2l, uv, rs, lq);
         return cudaGetLastError();
     };
-    if (cut && max_t >= 4)
-        return sorted_out ? go(p2p_l2p_f32_kernel<true, 4, true>)
-                          : go(p2p_l2p_f32_kernel<true, 4, false>);
+    // the kernel for (cut, max_t, sorted_out), with the queue when there is one
+    auto pick = [&](auto queue) {
+        constexpr bool kQ = decltype(queue)::value;
+        if (cut && max_t >= 4)
+            return sorted_out ? go(p2p_l2p_f32_kernel<true, 4, true, kQ>)
+                              : go(p2p_l2p_f32_kernel<true, 4, false, kQ>);
+        if (cut)
+            return sorted_out ? go(p2p_l2p_f32_kernel<true, 2, true, kQ>)
+                              : go(p2p_l2p_f32_kernel<true, 2, false, kQ>);
+        return sorted_out ? go(p2p_l2p_f32_kernel<false, 4, true, kQ>)
+                          : go(p2p_l2p_f32_kernel<false, 4, false, kQ>);
+    };
+    e = lq.pos ? pick(std::true_type{}) : pick(std::false_type{});
+    if (e != cudaSuccess || !lq.pos) return e;
+    // the queued targets: at most n, 32 per warp
+    auto lanes = [&](auto kernel) {
+        const unsigned lb = (unsigned)std::min<uint64_t>(
+            resident_ctas(reinterpret_cast<const void*>(kernel)),
+            ((uint64_t)n + 32 * kLeafWarps - 1) / (32 * kLeafWarps));
+        kernel<<<dim3(lb), dim3(kLeafWarps * 32), 0, s>>>(sp, skeys, leaf_start, lq, g, nm,
+                                                          nullptr, nullptr, nullptr, le, l2l,
+                                                          nullptr, uv);
+        return cudaGetLastError();
+    };
     if (cut)
-        return sorted_out ? go(p2p_l2p_f32_kernel<true, 2, true>)
-                          : go(p2p_l2p_f32_kernel<true, 2, false>);
-    return sorted_out ? go(p2p_l2p_f32_kernel<false, 4, true>)
-                      : go(p2p_l2p_f32_kernel<false, 4, false>);
+        return sorted_out ? lanes(p2p_lane_kernel<false, true, true>)
+                          : lanes(p2p_lane_kernel<false, true, false>);
+    return sorted_out ? lanes(p2p_lane_kernel<false, false, true>)
+                      : lanes(p2p_lane_kernel<false, false, false>);
 }
 
 template <>
 cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, int64_t n,
                                   const void* particles, const uint32_t* skeys,
                                   const uint32_t* leaf_start, uint32_t* counter, const float* le,
-                                  const float* l2l, float* uv, cudaStream_t s) {
+                                  const float* l2l, float* uv, uint32_t* lane_pos,
+                                  cudaStream_t s) {
     return launch_near_f32(g, sigma, n, particles, skeys, leaf_start, counter, le, l2l, uv, false,
-                           RingStrips{nullptr, nullptr}, s);
+                           RingStrips{nullptr, nullptr}, lane_pos, s);
 }
 
 cudaError_t launch_near_only_f32(const Geometry& g, double sigma, int64_t n,
                                  const void* particles, const uint32_t* skeys,
                                  const uint32_t* leaf_start, uint32_t* counter, float* out,
-                                 bool sorted_out, RingStrips strips, cudaStream_t s) {
+                                 bool sorted_out, RingStrips strips, uint32_t* lane_pos,
+                                 cudaStream_t s) {
     return launch_near_f32(g, sigma, n, particles, skeys, leaf_start, counter, nullptr, nullptr,
-                           out, sorted_out, strips, s);
+                           out, sorted_out, strips, lane_pos, s);
 }
 
 // L2P after a near-field-only pass: one warp per leaf adds the leaf's local
@@ -1403,8 +1710,10 @@ cudaError_t batch_near_fill(const BatchInst* host_inst, int count, void* dev_nea
         bool oki;
         NearF32v3 nm = near_constants(host_inst[i].sigma, host_inst[i].g, &oki);
         ok = ok && oki;
-        h[i] = NearInst{nm.sc,        nm.kvel,    nm.kzeta,  nm.inv_s,    nm.half_leaf,
-                        nm.qa,        nm.band_a2, nm.wstrip, nm.ring_mask};
+        const uint32_t lane_nt =
+            near_lane_path(host_inst[i].n, host_inst[i].g.L) ? kLaneMaxT : 0u;
+        h[i] = NearInst{nm.sc, nm.kvel,    nm.kzeta,  nm.inv_s,     nm.half_leaf,
+                        nm.qa, nm.band_a2, nm.wstrip, nm.ring_mask, lane_nt};
     }
     cudaError_t e = ok ? cudaMemcpyAsync(dev_near, h, sizeof(NearInst) * count,
                                          cudaMemcpyHostToDevice, s)
@@ -1419,7 +1728,7 @@ cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
                              int ctas_per_sm, const void* particles, const uint32_t* skeys,
                              const uint32_t* leaf_start, const float* le, const float* l2l16,
                              const float* l2l32, float* uv, bool cut, RingStrips strips,
-                             uint32_t nleaf_total, cudaStream_t s) {
+                             uint32_t nleaf_total, uint32_t* lane_pos, cudaStream_t s) {
     if (ntotal == 0) return cudaSuccess;
     Geometry g1{};
     g1.W = 2.0;
@@ -1431,7 +1740,10 @@ cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     unsigned blocks = (unsigned)(sms * ctas_per_sm);
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+    // lane_pos: some instance sends its sparse leaves to the per-target-lane
+    // pass (queue length in the counter's second word)
+    const LaneQueue lq = lane_pos ? LaneQueue{lane_pos, counter + 1} : LaneQueue{nullptr, nullptr};
+    cudaError_t e = cudaMemsetAsync(counter, 0, (lq.pos ? 2 : 1) * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     if (!cut || !strips.n) strips.rec = nullptr;
     if (strips.rec) {
@@ -1442,19 +1754,31 @@ cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    const float4* sp = reinterpret_cast<const float4*>(particles);
+    const NearInst* ni = static_cast<const NearInst*>(near_inst);
+    const WorkSplit ws = work_split(ntotal, (uint64_t)blocks * kLeafWarps);
+    auto dense = [&](auto kernel) {
+        kernel<<<blocks, kLeafWarps * 32, 0, s>>>(sp, skeys, leaf_start, inst, ni, leaf_inst, ws,
+                                                  counter, shared_nm, le, l2l16, l2l32, uv, strips,
+                                                  lq);
+        return cudaGetLastError();
+    };
     if (cut)
-        p2p_batch_kernel<true><<<blocks, kLeafWarps * 32, 0, s>>>(
-            reinterpret_cast<const float4*>(particles), skeys, leaf_start, inst,
-            static_cast<const NearInst*>(near_inst), leaf_inst,
-            work_split(ntotal, (uint64_t)blocks * kLeafWarps), counter, shared_nm, le, l2l16,
-            l2l32, uv, strips);
+        e = lq.pos ? dense(p2p_batch_kernel<true, true>) : dense(p2p_batch_kernel<true, false>);
     else
-        p2p_batch_kernel<false><<<blocks, kLeafWarps * 32, 0, s>>>(
-            reinterpret_cast<const float4*>(particles), skeys, leaf_start, inst,
-            static_cast<const NearInst*>(near_inst), leaf_inst,
-            work_split(ntotal, (uint64_t)blocks * kLeafWarps), counter, shared_nm, le, l2l16,
-            l2l32, uv, strips);
-    return cudaGetLastError();
+        e = lq.pos ? dense(p2p_batch_kernel<false, true>) : dense(p2p_batch_kernel<false, false>);
+    if (e != cudaSuccess || !lq.pos) return e;
+    auto lanes = [&](auto kernel) {
+        const unsigned lb = (unsigned)std::min<uint64_t>(
+            resident_ctas(reinterpret_cast<const void*>(kernel)),
+            ((uint64_t)ntotal + 32 * kLeafWarps - 1) / (32 * kLeafWarps));
+        kernel<<<dim3(lb), dim3(kLeafWarps * 32), 0, s>>>(sp, skeys, leaf_start, lq, Geometry{},
+                                                          shared_nm, inst, ni, leaf_inst, le,
+                                                          l2l16, l2l32, uv);
+        return cudaGetLastError();
+    };
+    return cut ? lanes(p2p_lane_kernel<true, true, false>)
+               : lanes(p2p_lane_kernel<true, false, false>);
 }
 
 template <>
@@ -1462,8 +1786,9 @@ cudaError_t launch_p2p_l2p<double>(const Geometry& g, double sigma, int64_t n,
                                    const void* particles, const uint32_t* skeys,
                                    const uint32_t* leaf_start, uint32_t* counter,
                                    const double* le, const double* l2l, double* uv,
-                                   cudaStream_t s) {
+                                   uint32_t* lane_pos, cudaStream_t s) {
     (void)n;
+    (void)lane_pos;  // FP64: one CTA per leaf, no per-target-lane pass
     (void)skeys;
     (void)counter;  // one CTA per leaf
     NearF64 nm;
