@@ -76,7 +76,6 @@ struct fmm2d_plan {
     // FP32 forms: the far field's branch of the graph and its fork/join events
     cudaStream_t cap2 = nullptr;
     float* uv_sorted = nullptr;  // FP32 forms: near-field velocities in sorted order
-    uint32_t* lane_pos = nullptr;  // FP32 forms: queue of the per-target-lane pass
     RingStrips strips{};         // FP32 forms with a cutoff: the ring strips (else null)
     bool use_strips = true;      // gather the ring from them (else from whole leaves)
     uint64_t l2_bytes = 0;       // the device's L2 size
@@ -197,8 +196,7 @@ cudaError_t enqueue(fmm2d_plan* pl, int64_t n, const R* xy, const R* gamma, R* u
         auto near_only = [&]() {
             return launch_near_only_f32(g, pl->prm.sigma, n, pl->particles, skeys,
                                         pl->sb.leaf_start, pl->p2p_counter,
-                                        sorted ? pl->uv_sorted : uvf, sorted, strips_of(pl),
-                                        pl->lane_pos, s);
+                                        sorted ? pl->uv_sorted : uvf, sorted, strips_of(pl), s);
         };
         cudaStream_t s2 = s;
         if (fork) {
@@ -228,7 +226,7 @@ cudaError_t enqueue(fmm2d_plan* pl, int64_t n, const R* xy, const R* gamma, R* u
         } else {
             STEP(near_only());
         }
-        STEP(launch_l2p_f32(g, pl->prm.sigma, pl->particles, pl->sb.leaf_start,
+        STEP(launch_l2p_f32(g, pl->prm.sigma, n, pl->particles, pl->sb.leaf_start,
                             reinterpret_cast<const float*>(le),
                             reinterpret_cast<const float*>(t.l2l),
                             sorted ? pl->uv_sorted : nullptr, uvf, s));
@@ -255,7 +253,7 @@ cudaError_t enqueue(fmm2d_plan* pl, int64_t n, const R* xy, const R* gamma, R* u
     if (g.L >= 4) STEP(launch_l2l<R>(g, t, le, s));
     STEP(mark(pl, 5, s));
     STEP(launch_p2p_l2p<R>(g, pl->prm.sigma, n, pl->particles, skeys, pl->sb.leaf_start,
-                           pl->p2p_counter, le, t.l2l, uv, pl->lane_pos, s));
+                           pl->p2p_counter, le, t.l2l, uv, s));
     STEP(mark(pl, 6, s));
     return cudaSuccess;
 }
@@ -301,15 +299,15 @@ cudaError_t enqueue_partial(fmm2d_plan* pl, bool upward, int64_t n, const R* xy,
         const bool sorted = (uint64_t)n * 4 * sizeof(float) <= pl->l2_bytes / 2;
         STEP(launch_near_only_f32(g, pl->prm.sigma, n, pl->particles, skeys, pl->sb.leaf_start,
                                   pl->p2p_counter, sorted ? pl->uv_sorted : uvf, sorted,
-                                  strips_of(pl), pl->lane_pos, s));
-        STEP(launch_l2p_f32(g, pl->prm.sigma, pl->particles, pl->sb.leaf_start,
+                                  strips_of(pl), s));
+        STEP(launch_l2p_f32(g, pl->prm.sigma, n, pl->particles, pl->sb.leaf_start,
                             reinterpret_cast<const float*>(le),
                             reinterpret_cast<const float*>(t.l2l),
                             sorted ? pl->uv_sorted : nullptr, uvf, s));
         return cudaSuccess;
     }
     STEP(launch_p2p_l2p<R>(g, pl->prm.sigma, n, pl->particles, skeys, pl->sb.leaf_start,
-                           pl->p2p_counter, le, t.l2l, uv, pl->lane_pos, s));
+                           pl->p2p_counter, le, t.l2l, uv, s));
     return cudaSuccess;
 }
 #undef STEP
@@ -495,16 +493,15 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
         align256(pl->elem == 4 ? nmax * 2 * sizeof(float) : 0),  // near field, sorted order
         align256(strips ? (size_t)nmax * 4 * sizeof(float4) : 0),  // ring strips
         align256(strips ? (size_t)nleaf * 4 * 4 : 0),               // their counts
-        align256(pl->elem == 4 ? nmax * 4 : 0),  // queue of the per-target-lane pass
     };
     size_t total = 0;
     for (size_t s : sizes) total += s;
     cudaError_t e = cudaMalloc(&pl->ws, total);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "workspace cudaMalloc"));
     char* p = static_cast<char*>(pl->ws);
-    void* slots[19];
-    static_assert(sizeof(sizes) / sizeof(sizes[0]) == 19, "one size per slot");
-    for (int i = 0; i < 19; ++i) {
+    void* slots[18];
+    static_assert(sizeof(sizes) / sizeof(sizes[0]) == 18, "one size per slot");
+    for (int i = 0; i < 18; ++i) {
         slots[i] = p;
         p += sizes[i];
     }
@@ -527,7 +524,6 @@ fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm) {
     float4* centres = (float4*)slots[14];
     pl->uv_sorted = (float*)slots[15];
     if (strips) pl->strips = RingStrips{(float4*)slots[16], (uint32_t*)slots[17]};
-    if (pl->elem == 4) pl->lane_pos = (uint32_t*)slots[18];
 
     e = cudaHostAlloc((void**)&pl->h_status, sizeof(int), cudaHostAllocDefault);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaHostAlloc"));

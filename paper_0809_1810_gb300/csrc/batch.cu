@@ -78,7 +78,10 @@ struct fmm2d_batch_plan {
     int tc_policy = 0;
     bool any_cutoff = false;
     RingStrips strips{};  // with a cutoff: the near field's ring strips
-    uint32_t* lane_pos = nullptr;  // queue of the per-target-lane pass (null: no sparse instance)
+    // windows of 32 sorted positions holding particles of instances whose
+    // sparse leaves take the near field's per-target-lane pass
+    uint32_t* lane_win = nullptr;
+    uint32_t lane_win_count = 0;
     // graph
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
@@ -147,7 +150,7 @@ cudaError_t enqueue_batch(fmm2d_batch_plan* b, const float* xy, const float* gam
                            b->sb.keys[sort_passes(b->key_bits) & 1], b->sb.leaf_start, b->le,
                            b->has_class[0] ? tab_l2l(b, 0) : nullptr,
                            b->has_class[1] ? tab_l2l(b, 1) : nullptr, uv, b->any_cutoff, b->strips,
-                           b->nleaf_total, b->lane_pos, s));
+                           b->nleaf_total, b->lane_win, b->lane_win_count, s));
     BMARK(5);
 #undef BMARK
 #undef BSTEP
@@ -324,15 +327,25 @@ fmm2d_status fmm2d_batch_plan_create_ex(fmm2d_batch_plan** out, int count,
         for (uint32_t k = 0; k < (1u << (2 * g.L)); ++k) leaf_inst[b->inst[i].leaf_base + k] = i;
         if (g.L < 2) continue;
         int c = class_of(g.P);
-        for (uint32_t q = 0; q < (1u << (2 * (g.L - 1))); ++q) {
-            quad_inst[c].push_back(i);
-            quad_local[c].push_back(q);
-        }
         m2l_inst[c].push_back(i);
         m2l_prefix[c].push_back(m2l_prefix[c].back() + g.nboxes);
         for (int l = 2; l <= g.L - 2; ++l) lvl_m2m[c][l].push_back(i);
         for (int l = 3; l <= g.L - 1; ++l) lvl_l2l[c][l].push_back(i);
     }
+    // P2M parent boxes per class: first those of the instances with at most 32
+    // particles per leaf on average (one warp per box), then the others
+    int64_t nquads_warp[2] = {0, 0};
+    for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < count; ++i) {
+            const Geometry& g = b->inst[i].g;
+            if (g.L < 2 || near_lane_path(b->inst[i].n, g.L) != (pass == 0)) continue;
+            const int c = class_of(g.P);
+            for (uint32_t q = 0; q < (1u << (2 * (g.L - 1))); ++q) {
+                quad_inst[c].push_back(i);
+                quad_local[c].push_back(q);
+            }
+            if (pass == 0) nquads_warp[c] = (int64_t)quad_inst[c].size();
+        }
     // one device allocation
     int64_t nmax = ntotal > 0 ? ntotal : 1;
     int64_t nblocks = (nmax + kSortTile - 1) / kSortTile;
@@ -348,14 +361,28 @@ fmm2d_status fmm2d_batch_plan_create_ex(fmm2d_batch_plan** out, int count,
         a256(4 * (size_t)std::max<int64_t>(exp_total, 1)), a256(8 * tab_count[0]),
         a256(8 * tab_count[1]), a256(4 * tab_count[0]), a256(4 * tab_count[1]),
         a256(8 * 65 * 65)};  // binomial scratch
+    // leaf centres per instance and axis index (FP32 hi/lo pairs, formed once
+    // with the single plans' FP64 arithmetic: the same bits, and no FP64 in
+    // the kernels that read them)
+    std::vector<int64_t> centre_off(count + 1, 0);
+    for (int i = 0; i < count; ++i)
+        centre_off[i + 1] = centre_off[i] + ((int64_t)1 << b->inst[i].g.L);
+    sizes.push_back(a256(sizeof(float4) * (size_t)centre_off[count]));
     // ring strips of the cutoff: 4 records per particle, 4 counts per leaf
     const bool want_strips = b->any_cutoff && nmax < ((int64_t)1 << 30);
     sizes.push_back(a256(want_strips ? 16 * 4 * (size_t)nmax : 0));
     sizes.push_back(a256(want_strips ? 16 * (size_t)nleaf : 0));
     // the per-target-lane pass's queue, when an instance has sparse leaves
-    bool want_lanes = false;
-    for (const BatchInst& bi : b->inst) want_lanes = want_lanes || near_lane_path(bi.n, bi.g.L);
-    sizes.push_back(a256(want_lanes ? 4 * (size_t)nmax : 0));
+    std::vector<uint32_t> lane_win;  // each window once, in increasing order
+    for (int i = 0; i < count; ++i) {
+        const BatchInst& bi = b->inst[i];
+        if (bi.n == 0 || !near_lane_path(bi.n, bi.g.L)) continue;
+        const uint32_t w0 = (uint32_t)(offsets[i] / 32);
+        const uint32_t w1 = (uint32_t)((offsets[i] + bi.n - 1) / 32);
+        for (uint32_t w = lane_win.empty() ? w0 : std::max(w0, lane_win.back() + 1); w <= w1; ++w)
+            lane_win.push_back(w);
+    }
+    sizes.push_back(a256(4 * lane_win.size()));
     size_t lists_bytes = 0;
     for (int c = 0; c < 2; ++c) {
         lists_bytes += a256(4 * quad_inst[c].size() + 4) * 2 + a256(4 * m2l_inst[c].size() + 4) +
@@ -396,6 +423,8 @@ fmm2d_status fmm2d_batch_plan_create_ex(fmm2d_batch_plan** out, int count,
     b->tab32[0] = (float*)take(sizes[k++]);
     b->tab32[1] = (float*)take(sizes[k++]);
     double* binom = (double*)take(sizes[k++]);
+    float4* centres = (float4*)take(sizes[k++]);
+    for (int i = 0; i < count; ++i) b->inst[i].g.centre_tab = centres + centre_off[i];
     {
         float4* rec = (float4*)take(sizes[k++]);
         uint32_t* cnt = (uint32_t*)take(sizes[k++]);
@@ -403,7 +432,10 @@ fmm2d_status fmm2d_batch_plan_create_ex(fmm2d_batch_plan** out, int count,
     }
     {
         uint32_t* q = (uint32_t*)take(sizes[k++]);
-        if (want_lanes) b->lane_pos = q;
+        if (!lane_win.empty()) {
+            b->lane_win = q;
+            b->lane_win_count = (uint32_t)lane_win.size();
+        }
     }
     b->sb.status = b->d_status;
 
@@ -414,9 +446,12 @@ fmm2d_status fmm2d_batch_plan_create_ex(fmm2d_batch_plan** out, int count,
     auto up = [&](void* dst, const void* src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
     };
-    e = up(b->d_inst, b->inst.data(), sizeof(BatchInst) * count);
+    for (int i = 0; i < count && e == cudaSuccess; ++i)
+        e = launch_centre_table(b->inst[i].g, centres + centre_off[i], s);
+    if (e == cudaSuccess) e = up(b->d_inst, b->inst.data(), sizeof(BatchInst) * count);
     if (e == cudaSuccess) e = up(b->d_offsets, offsets.data(), 8 * (count + 1));
     if (e == cudaSuccess) e = up(b->d_leaf_inst, leaf_inst.data(), 4 * nleaf);
+    if (e == cudaSuccess) e = up(b->lane_win, lane_win.data(), 4 * (size_t)b->lane_win_count);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), s);
     for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
         BatchLists& bl = b->lists[c];
@@ -431,6 +466,7 @@ fmm2d_status fmm2d_batch_plan_create_ex(fmm2d_batch_plan** out, int count,
         bl.quad_inst = qi;
         bl.quad_local = ql;
         bl.nquads = (int64_t)quad_inst[c].size();
+        bl.nquads_warp = nquads_warp[c];
         bl.m2l_inst = mi;
         bl.m2l_prefix = mp;
         bl.m2l_count = (int)m2l_inst[c].size();
@@ -549,7 +585,8 @@ fmm2d_status fmm2d_batch_autotune(fmm2d_batch_plan* b, const float* xy, const fl
                                     b->sb.leaf_start, b->le,
                                     b->has_class[0] ? tab_l2l(b, 0) : nullptr,
                                     b->has_class[1] ? tab_l2l(b, 1) : nullptr, uv,
-                                    b->any_cutoff, b->strips, b->nleaf_total, b->lane_pos, s);
+                                    b->any_cutoff, b->strips, b->nleaf_total, b->lane_win,
+                                    b->lane_win_count, s);
         });
         if (ms < best) {
             best = ms;

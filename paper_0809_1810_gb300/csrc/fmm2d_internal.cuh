@@ -157,14 +157,10 @@ template <typename R>
 cudaError_t launch_m2l(const Geometry& g, const Tables<R>& t, const R* me, R* le, cudaStream_t s);
 template <typename R>
 cudaError_t launch_l2l(const Geometry& g, const Tables<R>& t, R* le, cudaStream_t s);
-// lane_pos (FP32 forms; may be null): room for n sorted positions, the
-// queue of targets in sparse leaves that the per-target-lane pass takes
-// (counter then needs two words: the work counter and the queue length).
 template <typename R>
 cudaError_t launch_p2p_l2p(const Geometry& g, double sigma, int64_t n, const void* particles,
                            const uint32_t* skeys, const uint32_t* leaf_start, uint32_t* counter,
-                           const R* le, const R* l2l, R* uv, uint32_t* lane_pos,
-                           cudaStream_t s);
+                           const R* le, const R* l2l, R* uv, cudaStream_t s);
 // The FP32 near field without its far part, written to `out` (2 floats per
 // target) at the input indices or (sorted_out) in sorted order, and the L2P
 // that adds the far part afterwards -- reading the near parts in sorted order
@@ -185,9 +181,8 @@ struct RingStrips {
 cudaError_t launch_near_only_f32(const Geometry& g, double sigma, int64_t n,
                                  const void* particles, const uint32_t* skeys,
                                  const uint32_t* leaf_start, uint32_t* counter, float* out,
-                                 bool sorted_out, RingStrips strips, uint32_t* lane_pos,
-                                 cudaStream_t s);
-cudaError_t launch_l2p_f32(const Geometry& g, double sigma, const void* particles,
+                                 bool sorted_out, RingStrips strips, cudaStream_t s);
+cudaError_t launch_l2p_f32(const Geometry& g, double sigma, int64_t n, const void* particles,
                            const uint32_t* leaf_start, const float* le, const float* l2l,
                            const float* uv_sorted, float* uv, cudaStream_t s);
 
@@ -213,6 +208,8 @@ struct BatchLists {
     const int32_t* quad_inst;    // P2M: instance of every parent box (level L-1) of the class
     const uint32_t* quad_local;  // its local index (Morton key at level L-1)
     int64_t nquads;
+    int64_t nquads_warp;         // the first ones: instances of at most 32 particles
+                                 // per leaf on average (one warp per box)
     const int32_t* m2l_inst;     // M2L: instances of the class ...
     const int64_t* m2l_prefix;   // ... and the prefix of their box counts (levels 2..L)
     int m2l_count;
@@ -247,9 +244,12 @@ cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
                              int ctas_per_sm, const void* particles, const uint32_t* skeys,
                              const uint32_t* leaf_start, const float* le, const float* l2l16,
                              const float* l2l32, float* uv, bool cut, RingStrips strips,
-                             uint32_t nleaf_total, uint32_t* lane_pos, cudaStream_t s);
+                             uint32_t nleaf_total, const uint32_t* lane_win,
+                             uint32_t lane_win_count, cudaStream_t s);
 // Whether an evaluation of n particles over 4^L leaves sends its sparse
-// leaves to the per-target-lane pass of the FP32 near field.
+// leaves to the per-target-lane pass of the FP32 near field.  A batch lists
+// the windows of 32 sorted positions that hold such instances' particles
+// (lane_win, lane_win_count; null: none).
 bool near_lane_path(int64_t n, int L);
 cudaError_t launch_batch_direct(const BatchInst* inst, const int64_t* dev_offsets, int count,
                                 int kernel, const float* xy, const float* gamma, int64_t s_count,

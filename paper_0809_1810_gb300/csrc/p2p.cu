@@ -575,6 +575,56 @@ __device__ __forceinline__ void l2p_add(int p, float kzeta, float inv_s, const f
     v = fmaf(-inv_s, w.y, v);
 }
 
+// Far field of a target in a lane-pass leaf (Eq. 12), from the two parts the
+// leaf's local expansion is the sum of: its own M2L part (level L, `own`) at
+// zeta = (z - z_leaf)/s, and its parent's complete expansion (level L - 1,
+// `par`; null at L = 2) at zeta_p = (z - z_parent)/(2 s) = (zeta + t)/2,
+// t = (z_leaf - z_parent)/s = (+-1/2, +-1/2) by the leaf's quadrant (cx, cy).
+// The L2L shift of a polynomial is exact, so this is the value of the leaf's
+// expansion up to rounding, without the P^2 products of forming it.
+__device__ __forceinline__ void l2p_two_levels(int p, float kzeta, float inv_s,
+                                               const float2* own, const float2* par,
+                                               uint32_t cx, uint32_t cy, float x, float y,
+                                               float& u, float& v) {
+    const float2 zeta = make_float2(x * kzeta, y * kzeta);
+    float2 w = own[p - 1];
+    for (int m = p - 2; m >= 0; --m) {
+        const float2 t = cmul(w, zeta);
+        const float2 lm = own[m];
+        w = make_float2(t.x + lm.x, t.y + lm.y);
+    }
+    u = fmaf(inv_s, w.x, u);
+    v = fmaf(-inv_s, w.y, v);
+    if (par) {
+        const float2 zp = make_float2((zeta.x + (cx ? 0.5f : -0.5f)) * 0.5f,
+                                      (zeta.y + (cy ? 0.5f : -0.5f)) * 0.5f);
+        float2 wp = par[p - 1];
+        for (int m = p - 2; m >= 0; --m) {
+            const float2 t = cmul(wp, zp);
+            const float2 lm = par[m];
+            wp = make_float2(t.x + lm.x, t.y + lm.y);
+        }
+        const float hs = 0.5f * inv_s;  // 1 / s_parent
+        u = fmaf(hs, wp.x, u);
+        v = fmaf(-hs, wp.y, v);
+    }
+}
+
+// A lane-pass leaf's two expansion parts into shared memory (own[0 .. P),
+// par[0 .. P)), one warp; par only with a parent (L >= 3).
+__device__ __forceinline__ void stage_two_levels(const Geometry& g, const float* __restrict__ le,
+                                                 uint32_t lx, uint32_t ly, float2* own,
+                                                 float2* par) {
+    const int lane = threadIdx.x & 31;
+    if (lane < g.P) {
+        own[lane] = reinterpret_cast<const float2*>(
+            le + box_slot(g.level_base, g.L, lx, ly) * (2 * g.P))[lane];
+        if (g.L >= 3)
+            par[lane] = reinterpret_cast<const float2*>(
+                le + box_slot(g.level_base, g.L - 1, lx >> 1, ly >> 1) * (2 * g.P))[lane];
+    }
+}
+
 // Gather local-list records [cb, cb + cnt) (cnt <= kListChunk) into the
 // warp's buffer in scaled leaf-relative coordinates: nn near-band sources
 // from the front (sources 0, 1, ...), nf far-band sources from the back
@@ -949,34 +999,25 @@ static WorkSplit work_split(uint64_t n, uint64_t warps) {
 // most kLaneMaxT targets a leaf would leave most of a warp idle, and its
 // fixed costs (the ranges of its 25 neighbours, the gathers, its local
 // expansion) outweigh its pairs.  In an evaluation whose mean occupancy is
-// at most kLaneMean particles per leaf, such leaves are queued instead, and
-// the per-target-lane pass (p2p_lane_kernel) gives each queued target a lane
-// of its own.  The choice depends on the leaf's count and the evaluation's
-// n and L alone, so a target gets the same arithmetic in a single and a
-// batched evaluation, whatever warp it lands in.
+// at most kLaneMean particles per leaf, such leaves are skipped here and
+// taken by the per-target-lane pass (p2p_lane_kernel), which gives each of
+// their targets a lane.  The choice depends on the leaf's count and the
+// evaluation's n and L alone, so a target gets the same arithmetic in a
+// single and a batched evaluation, whatever warp it lands in.
 constexpr uint32_t kLaneMaxT = 16;
 constexpr int64_t kLaneMean = 32;
 
-// Targets queued for the per-target-lane pass: their sorted positions, and
-// the queue's length (zeroed before the near-field launch).  Null pos: no
-// queue (every leaf takes the warp path).
-struct LaneQueue {
-    uint32_t* pos;
-    uint32_t* count;
-};
-
 // f(key, a, b) for every chunk or round that item w owns: key the leaf index
 // into leaf_start, [a, b) its targets within the leaf.  Warp-uniform calls.
-// kQueue: a leaf of nt <= kLaneMaxT targets whose gate(key) (the
-// evaluation's bound, 0 or kLaneMaxT) admits it is queued instead, its nt
-// positions appended to lq by one atomic per warp step (the kernels are
-// compiled with and without the queue: its registers cost the dense
-// evaluations that never use it).
-template <bool kQueue, typename Gate, typename F>
+// kSkip: leaves of nt <= kLaneMaxT targets whose gate(key) (the evaluation's
+// bound, 0 or kLaneMaxT) admits them are left to the per-target-lane pass
+// (the kernels are compiled with and without the test: its registers cost
+// the dense evaluations that never use it).
+template <bool kSkip, typename Gate, typename F>
 __device__ __forceinline__ void for_each_piece(const uint32_t* __restrict__ skeys,
                                                const uint32_t* __restrict__ leaf_start,
-                                               const WorkSplit& ws, uint32_t w,
-                                               const LaneQueue& lq, Gate&& gate, F&& f) {
+                                               const WorkSplit& ws, uint32_t w, Gate&& gate,
+                                               F&& f) {
     const int lane = threadIdx.x & 31;
     const bool big = w < ws.nbig;
     const uint32_t split = ws.nbig * ws.span;
@@ -993,22 +1034,9 @@ __device__ __forceinline__ void for_each_piece(const uint32_t* __restrict__ skey
             const uint32_t off = r - first;
             starts = (off & (span - 1)) == 0 &&
                      (big || first + (off & ~(ws.span - 1)) >= split);
-            if (kQueue && starts) nt = leaf_start[key + 1] - first;
-        }
-        if constexpr (kQueue) {
-            const bool defer = starts && r == first && nt <= kLaneMaxT && nt <= gate(key);
-            if (__ballot_sync(0xffffffffu, defer)) {
-                uint32_t incl = defer ? nt : 0u;  // inclusive prefix of the queued counts
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += t;
-                }
-                uint32_t at = 0;
-                if (lane == 31) at = atomicAdd(lq.count, incl);
-                at = __shfl_sync(0xffffffffu, at, 31) + incl - nt;
-                if (defer)
-                    for (uint32_t j = 0; j < nt; ++j) lq.pos[at + j] = r + j;
-                starts = starts && !defer;
+            if (kSkip && starts) {
+                nt = leaf_start[key + 1] - first;
+                if (nt <= kLaneMaxT && nt <= gate(key)) starts = false;
             }
         }
         unsigned m = __ballot_sync(0xffffffffu, starts);
@@ -1019,7 +1047,7 @@ __device__ __forceinline__ void for_each_piece(const uint32_t* __restrict__ skey
             const uint32_t f0 = __shfl_sync(0xffffffffu, first, src);
             const uint32_t a = base + (uint32_t)src - f0;
             const uint32_t ntk =
-                kQueue ? __shfl_sync(0xffffffffu, nt, src) : leaf_start[k + 1] - f0;
+                kSkip ? __shfl_sync(0xffffffffu, nt, src) : leaf_start[k + 1] - f0;
             f(k, a, min(a + span, ntk));
         }
     }
@@ -1029,13 +1057,12 @@ __device__ __forceinline__ void for_each_piece(const uint32_t* __restrict__ skey
 // items from a counter (zeroed before the launch) until none is left, so
 // crowded windows balance against light ones and no SM idles behind a
 // partial last wave.
-template <bool kCut, int kMaxT, bool kSorted, bool kQueue>
+template <bool kCut, int kMaxT, bool kSorted, bool kSkip>
 __global__ void __launch_bounds__(kLeafWarps * 32, 6)
 p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skeys,
                    const uint32_t* __restrict__ leaf_start, WorkSplit ws, uint32_t* counter,
                    Geometry g, NearF32v3 nm, const float* __restrict__ le,
-                   const float* __restrict__ l2l, float* __restrict__ uv, RingStrips rs,
-                   LaneQueue lq) {
+                   const float* __restrict__ l2l, float* __restrict__ uv, RingStrips rs) {
     __shared__ float4 lists[kLeafWarps][kListCap];
     __shared__ uint32_t ranges[kLeafWarps][kCut ? 52 : 20];
     __shared__ float2 leaf_le[kLeafWarps][kMaxP];
@@ -1046,8 +1073,8 @@ p2p_l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ s
         if (lane == 0) w = atomicAdd(counter, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= ws.items) break;
-        for_each_piece<kQueue>(skeys, leaf_start, ws, w, lq, gate,
-                               [&](uint32_t leaf, uint32_t a, uint32_t b) {
+        for_each_piece<kSkip>(skeys, leaf_start, ws, w, gate,
+                              [&](uint32_t leaf, uint32_t a, uint32_t b) {
             p2p_chunk_f32<kCut, kMaxT, kSorted>(sp, leaf_start, 0, leaf, a, b, g, nm, le, l2l,
                                                 uv, lists[warp], ranges[warp], leaf_le[warp], rs);
         });
@@ -1129,15 +1156,14 @@ ring_strips_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ l
 // (all instances, packed) from a work counter.  kCut compiles in the cutoff
 // ring of Sec. 4.1 for batches where some instance has a cutoff (the others
 // have an empty ring and skip it).
-template <bool kCut, bool kQueue>
+template <bool kCut, bool kSkip>
 __global__ void __launch_bounds__(kLeafWarps * 32, 6)
 p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skeys,
                  const uint32_t* __restrict__ leaf_start, const BatchInst* __restrict__ inst,
                  const NearInst* __restrict__ near_inst, const int32_t* __restrict__ leaf_inst,
                  WorkSplit ws, uint32_t* counter, NearF32v3 shared_nm,
                  const float* __restrict__ le, const float* __restrict__ l2l16,
-                 const float* __restrict__ l2l32, float* __restrict__ uv, RingStrips rs,
-                 LaneQueue lq) {
+                 const float* __restrict__ l2l32, float* __restrict__ uv, RingStrips rs) {
     __shared__ float4 lists[kLeafWarps][kListCap];
     __shared__ uint32_t ranges[kLeafWarps][kCut ? 52 : 20];
     __shared__ float2 leaf_le[kLeafWarps][kMaxP];
@@ -1148,8 +1174,8 @@ p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ ske
         if (lane == 0) w = atomicAdd(counter, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= ws.items) break;
-        for_each_piece<kQueue>(skeys, leaf_start, ws, w, lq, gate,
-                               [&](uint32_t gleaf, uint32_t a, uint32_t e) {
+        for_each_piece<kSkip>(skeys, leaf_start, ws, w, gate,
+                              [&](uint32_t gleaf, uint32_t a, uint32_t e) {
             const int i = leaf_inst[gleaf];
             const BatchInst& b = inst[i];
             NearF32v3 nm = shared_nm;
@@ -1173,31 +1199,50 @@ p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ ske
 }
 
 // ---------------------------------------------------------------------------
-// Per-target-lane pass over the queued targets of sparse leaves.
+// Per-target-lane pass over the targets of sparse leaves.
 //
-// Each lane takes one queued target and walks its local list itself: the 9
-// ranges of its leaf's 3x3 neighbourhood, then (with a cutoff) the 16 ring
-// ranges, reading the sorted records from global memory (the lanes of one
-// leaf read the same records: one broadcast), two records per step as one
-// packed pair.  Every pair of the 3x3 block takes the near-band form (the
-// polynomial below qthr), every ring pair the cutoff correction.  The
-// walk's trip count is the warp's longest list; a lane past its own end
-// evaluates dummies (zero circulation, far away).  Sums: blocks of
-// kLanePairs pairs into fresh registers, then compensated.  Far field (when
-// le is given): the warp forms the local expansion of each leaf it holds
-// once, with the warp path's operations (leaf_le_build_unrolled), in shared
-// memory, and each lane adds its own L2P (l2p_add).  A target's arithmetic
-// does not depend on which warp or lane takes it.
+// Warps take windows of 32 sorted positions (a CTA four consecutive ones, so
+// that its warps read neighbouring records and share them in L1); a lane
+// whose target lies in a leaf of at most kLaneMaxT targets (in a sparse
+// evaluation) walks that target's local list itself: the 9 ranges of its
+// leaf's 3x3 neighbourhood, then (with a cutoff) the 16 ring ranges,
+// reading the sorted records from global memory (the lanes of one leaf read
+// the same records: one broadcast), two records per step as one packed
+// pair.  Every pair of the 3x3 block takes the near-band form (the
+// polynomial below qthr), every ring pair the cutoff correction.  The walk's
+// trip count is the warp's longest list; a lane past its own end evaluates
+// dummies (zero circulation, far away).  Sums: blocks of kLanePairs pairs
+// into fresh registers, then compensated.  Far field (when le is given):
+// the warp forms the local expansion of each leaf it holds once, with the
+// warp path's operations (leaf_le_build_unrolled), in shared memory, and
+// each lane adds its own L2P (l2p_add).  A target's arithmetic does not
+// depend on which warp or lane takes it.
 // ---------------------------------------------------------------------------
 constexpr int kLaneRanges = 25;      // 9 local + 16 ring
 constexpr uint32_t kLanePairs = 32;  // pairs per first-level partial sum
+constexpr int kLaneSlots = 12;       // leaves' expansion parts staged at a time
 
+// Per warp: the lanes' source ranges while the sums run, then the two
+// expansion parts of the warp's leaves (6.4 KB: with 6 CTAs of 4 warps,
+// 150 KB of shared memory per SM, the rest left to L1 for the records).
 union LaneSmem {
     struct {
         uint32_t beg[kLaneRanges][32];  // range r of lane l at [r][l]
         uint32_t end[kLaneRanges][32];
     } r;
-    float2 le[32][kMaxP + 1];  // one local expansion per leaf of the warp
+    struct {
+        float2 own[kMaxP + 1];  // padded: lanes of different leaves in different banks
+        float2 par[kMaxP + 1];
+    } le[kLaneSlots];
+};
+
+// The windows of 32 sorted positions a lane pass visits: win[0 .. count)
+// (window w covers positions 32 w .. 32 w + 31 below n), or with win null
+// windows 0 .. count - 1.
+struct LaneWindows {
+    const uint32_t* win;
+    uint32_t count;
+    uint32_t n;
 };
 
 // Leaf centre as FP32 hi/lo pairs for the calling lane alone (the table, or
@@ -1217,78 +1262,83 @@ __device__ __forceinline__ void lane_centre_hilo(const Geometry& g, uint32_t ix,
     }
 }
 
-// The lane's records of ranges [r, r_end) in order against its target, two
-// per step for `steps` steps (the warp's longest walk).
+// The lane's records against its target, two per step for `steps` steps
+// (the warp's longest walk): `left` records from the non-empty ranges
+// r0, r0 + 1, ... (compacted in shared memory).  Past its own end a lane
+// evaluates dummies.
 template <int kMode>
 __device__ __forceinline__ void lane_walk(const float4* __restrict__ sp, const LaneSmem& sm,
-                                          int r, int r_end, uint32_t steps, const NearF32v3& nm,
-                                          float cxh, float cxl, float cyh, float cyl, float x,
+                                          int r0, uint32_t left, uint32_t steps,
+                                          const NearF32v3& nm, float2 ch, float2 cl, float x,
                                           float y, float& su, float& sv, float& cu, float& cv) {
     const int lane = threadIdx.x & 31;
+    int r = r0;
     uint32_t pos = sm.r.beg[r][lane], end = sm.r.end[r][lane];
-    // the next record's position (false: the lane's list is done)
-    auto next = [&](uint32_t& at) {
-        while (pos == end && r + 1 < r_end) {
-            ++r;
-            pos = sm.r.beg[r][lane];
-            end = sm.r.end[r][lane];
-        }
+    // the record at pos (false: the lane's list is done), then the walk moves
+    // on, to the next range at the end of this one (branch-free)
+    auto take = [&](uint32_t& at) {
         at = pos;
-        if (pos == end) return false;
+        const bool v = left > 0;
+        left -= v ? 1u : 0u;
         ++pos;
-        return true;
+        const bool adv = pos == end;
+        r += adv ? 1 : 0;
+        const int rr = min(r, kLaneRanges - 1);
+        const uint32_t nb = sm.r.beg[rr][lane], ne = sm.r.end[rr][lane];
+        pos = adv ? nb : pos;
+        end = adv ? ne : end;
+        return v;
     };
-    const float2 tx = f2_dup(x), ty = f2_dup(y);
-    float2 iu = make_float2(0.f, 0.f), iv = iu;
+    const float2 tx = f2_dup(x), ty = f2_dup(y), scv = f2_dup(nm.sc);
 #pragma unroll 1
-    for (uint32_t k = 0; k < steps; ++k) {
-        uint32_t ia, ib;
-        const bool va = next(ia), vb = next(ib);
-        const float4 qa = sp[va ? ia : 0u], qb = sp[vb ? ib : 0u];  // both loads in flight
-        const float xa = va ? ((qa.x - cxh) - cxl) * nm.sc : kFarAway;
-        const float ya = va ? ((qa.y - cyh) - cyl) * nm.sc : kFarAway;
-        const float ga = va ? qa.z : 0.f;
-        const float xb = vb ? ((qb.x - cxh) - cxl) * nm.sc : kFarAway;
-        const float yb = vb ? ((qb.y - cyh) - cyl) * nm.sc : kFarAway;
-        const float gb = vb ? qb.z : 0.f;
-        pair_sources<kMode>(nm, make_float4(xa, xb, ya, yb), make_float4(ga, gb, -ga, -gb), tx,
-                            ty, iu, iv);
-        if (k % kLanePairs == kLanePairs - 1) {
-            neumaier_add(su, cu, iu.x + iu.y);
-            neumaier_add(sv, cv, iv.x + iv.y);
-            iu = iv = make_float2(0.f, 0.f);
+    for (uint32_t k0 = 0; k0 < steps; k0 += kLanePairs) {
+        const uint32_t k1 = min(k0 + kLanePairs, steps);
+        float2 iu = make_float2(0.f, 0.f), iv = iu;
+#pragma unroll 2  // two steps' loads in flight: 5% faster than one
+        for (uint32_t k = k0; k < k1; ++k) {
+            uint32_t ia, ib;
+            const bool va = take(ia), vb = take(ib);
+            const float4 qa = sp[va ? ia : 0u], qb = sp[vb ? ib : 0u];  // both loads in flight
+            // scaled leaf-relative (x, y) of each, ((x - c_hi) - c_lo) sc, packed
+            const float2 da = f2_mul(f2_sub(f2_sub(make_float2(qa.x, qa.y), ch), cl), scv);
+            const float2 db = f2_mul(f2_sub(f2_sub(make_float2(qb.x, qb.y), ch), cl), scv);
+            const float xa = va ? da.x : kFarAway, ya = va ? da.y : kFarAway;
+            const float xb = vb ? db.x : kFarAway, yb = vb ? db.y : kFarAway;
+            const float ga = va ? qa.z : 0.f, gb = vb ? qb.z : 0.f;
+            pair_sources<kMode>(nm, make_float4(xa, xb, ya, yb), make_float4(ga, gb, -ga, -gb),
+                                tx, ty, iu, iv);
         }
+        neumaier_add(su, cu, iu.x + iu.y);
+        neumaier_add(sv, cv, iv.x + iv.y);
     }
-    neumaier_add(su, cu, iu.x + iu.y);
-    neumaier_add(sv, cv, iv.x + iv.y);
 }
 
-// Persistent: each warp takes 32 queued targets at a time.  kBatch: the
-// targets belong to the instances of a batch (each lane its own instance's
-// geometry and constants); otherwise to one evaluation (g, nm).  kSorted:
-// near parts alone at the sorted positions (le null); otherwise at the
-// input indices.
+// Persistent over the windows.  kBatch: the targets belong to the instances
+// of a batch (each lane its own instance's geometry and constants);
+// otherwise to one evaluation (g, nm).  kSorted: near parts alone at the
+// sorted positions (le null); otherwise at the input indices.
 template <bool kBatch, bool kCut, bool kSorted>
 __global__ void __launch_bounds__(kLeafWarps * 32, 6)
 p2p_lane_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skeys,
-                const uint32_t* __restrict__ leaf_start, LaneQueue lq, Geometry g, NearF32v3 nm,
-                const BatchInst* __restrict__ inst, const NearInst* __restrict__ near_inst,
-                const int32_t* __restrict__ leaf_inst, const float* __restrict__ le,
-                const float* __restrict__ l2l16, const float* __restrict__ l2l32,
-                float* __restrict__ uv) {
+                const uint32_t* __restrict__ leaf_start, LaneWindows lw, Geometry g,
+                NearF32v3 nm, const BatchInst* __restrict__ inst,
+                const NearInst* __restrict__ near_inst, const int32_t* __restrict__ leaf_inst,
+                const float* __restrict__ le, const float* __restrict__ l2l16,
+                const float* __restrict__ l2l32, float* __restrict__ uv) {
     __shared__ LaneSmem smem[kLeafWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     LaneSmem& sm = smem[warp];
-    const uint32_t count = *lq.count;
-    for (uint32_t gw = blockIdx.x * kLeafWarps + warp; gw * 32u < count;
+    for (uint32_t gw = blockIdx.x * kLeafWarps + warp; gw < lw.count;
          gw += gridDim.x * kLeafWarps) {
-        const uint32_t qi = gw * 32u + lane;
-        const bool active = qi < count;  // lane 0 always is
-        const uint32_t r = lq.pos[active ? qi : gw * 32u];
-        const uint32_t key = skeys[r];
-        // the target's evaluation: geometry, constants, first leaf
+        const uint32_t r = (lw.win ? lw.win[gw] : gw) * 32u + lane;
+        // the target's leaf and evaluation: geometry, constants, first leaf
+        uint32_t key = 0, nt = 0;
+        if (r < lw.n) {
+            key = skeys[r];
+            nt = leaf_start[key + 1] - leaf_start[key];
+        }
         int ii = 0;
-        uint32_t leaf_base = 0;
+        uint32_t leaf_base = 0, gate = nm.lane_nt;
         NearF32v3 m = nm;
         const Geometry* gp = &g;
         if constexpr (kBatch) {
@@ -1300,21 +1350,26 @@ p2p_lane_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skey
             m.inv_s = ni.inv_s;
             m.qa = ni.qa;
             m.ring_mask = ni.ring_mask;
+            gate = ni.lane_nt;
             leaf_base = inst[ii].leaf_base;
             gp = &inst[ii].g;
         }
+        const bool active = r < lw.n && nt <= kLaneMaxT && nt <= gate;
+        if (!__any_sync(0xffffffffu, active)) continue;
         const int L = gp->L;
         const int nl = 1 << L;
         const uint32_t leaf = key - leaf_base;
         const uint32_t lx = morton_compact(leaf), ly = morton_compact(leaf >> 1);
-        const float4 rec = sp[r];
+        const float4 rec = sp[r < lw.n ? r : 0u];
         float cxh, cxl, cyh, cyl;
         lane_centre_hilo(*gp, lx, ly, &cxh, &cxl, &cyh, &cyl);
         const float x = ((rec.x - cxh) - cxl) * m.sc, y = ((rec.y - cyh) - cyl) * m.sc;
 
-        // the lane's ranges: 3x3 block in row order, then the ring
+        // the lane's non-empty ranges, compacted: the 3x3 block in row order
+        // from slot 0, then the ring from slot 9
         __syncwarp();  // the warp's previous readers of sm are done
         uint32_t tot_l = 0, tot_r = 0;
+        int nr = 0;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             const int sx = (int)lx + q % 3 - 1, sy = (int)ly + q / 3 - 1;
@@ -1324,11 +1379,17 @@ p2p_lane_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skey
                 b = leaf_start[k];
                 e = leaf_start[k + 1];
             }
-            sm.r.beg[q][lane] = b;
-            sm.r.end[q][lane] = e;
+            if (e > b) {
+                sm.r.beg[nr][lane] = b;
+                sm.r.end[nr][lane] = e;
+                ++nr;
+            }
             tot_l += e - b;
         }
         if (kCut) {
+            nr = 9;
+            sm.r.beg[9][lane] = 0;  // an empty ring reads one dummy range
+            sm.r.end[9][lane] = 0;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 int dx, dy;
@@ -1341,48 +1402,58 @@ p2p_lane_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skey
                     b = leaf_start[k];
                     e = leaf_start[k + 1];
                 }
-                sm.r.beg[9 + q][lane] = b;
-                sm.r.end[9 + q][lane] = e;
+                if (e > b) {
+                    sm.r.beg[nr][lane] = b;
+                    sm.r.end[nr][lane] = e;
+                    ++nr;
+                }
                 tot_r += e - b;
             }
         }
         __syncwarp();
+        const float2 ch = make_float2(cxh, cyh), cl = make_float2(cxl, cyl);
         float su = 0.f, sv = 0.f, cu = 0.f, cv = 0.f;
-        lane_walk<kNearBand>(sp, sm, 0, 9, __reduce_max_sync(0xffffffffu, (tot_l + 1) >> 1), m,
-                             cxh, cxl, cyh, cyl, x, y, su, sv, cu, cv);
+        lane_walk<kNearBand>(sp, sm, 0, tot_l, __reduce_max_sync(0xffffffffu, (tot_l + 1) >> 1),
+                             m, ch, cl, x, y, su, sv, cu, cv);
         if (kCut) {
             const uint32_t steps = __reduce_max_sync(0xffffffffu, (tot_r + 1) >> 1);
-            if (steps)
-                lane_walk<kRing>(sp, sm, 9, kLaneRanges, steps, m, cxh, cxl, cyh, cyl, x, y, su,
-                                 sv, cu, cv);
+            if (steps) lane_walk<kRing>(sp, sm, 9, tot_r, steps, m, ch, cl, x, y, su, sv, cu, cv);
         }
         su += cu;
         sv += cv;
         float u = __fmul_rn(m.kvel, su), v = __fmul_rn(m.kvel, sv);
 
-        if (le) {  // far field: the local expansion of each leaf of the warp, once
-            __syncwarp();  // the ranges are done with; sm now holds expansions
+        if (le) {  // far field: each leaf's two expansion parts staged once per warp
             const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
             const bool lead = active && (lane == 0 || prev != key);
             const unsigned lm = __ballot_sync(0xffffffffu, lead);
             const unsigned upto = lane == 31 ? 0xffffffffu : (2u << lane) - 1u;
-            const int slot = __popc(lm & upto) - 1;  // this lane's leaf
-            for (unsigned todo = lm; todo; todo &= todo - 1) {
-                const int j = __ffs(todo) - 1;
-                const int sj = __popc(lm & ((1u << j) - 1u));
-                const uint32_t jlx = __shfl_sync(0xffffffffu, lx, j);
-                const uint32_t jly = __shfl_sync(0xffffffffu, ly, j);
-                if constexpr (kBatch) {
-                    const BatchInst& b = inst[__shfl_sync(0xffffffffu, ii, j)];
-                    if (b.g.L >= 2)
-                        leaf_le_build_unrolled(b.g, le + b.exp_off, b.g.P <= 16 ? l2l16 : l2l32,
-                                               jlx, jly, sm.le[sj]);
-                } else {
-                    if (g.L >= 2) leaf_le_build_unrolled(g, le, l2l16, jlx, jly, sm.le[sj]);
+            const int mine = __popc(lm & upto) - 1;  // this lane's leaf among the leaders
+            const unsigned far = __ballot_sync(0xffffffffu, L >= 2);
+            unsigned todo = lm;
+            for (int base = 0; todo; base += kLaneSlots) {  // kLaneSlots leaves at a time
+                __syncwarp();  // earlier readers of sm are done
+                for (int sj = 0; sj < kLaneSlots && todo; ++sj, todo &= todo - 1) {
+                    const int j = __ffs(todo) - 1;
+                    if (!((far >> j) & 1u)) continue;
+                    const uint32_t jlx = __shfl_sync(0xffffffffu, lx, j);
+                    const uint32_t jly = __shfl_sync(0xffffffffu, ly, j);
+                    if constexpr (kBatch) {
+                        const BatchInst& b = inst[__shfl_sync(0xffffffffu, ii, j)];
+                        stage_two_levels(b.g, le + b.exp_off, jlx, jly, sm.le[sj].own,
+                                         sm.le[sj].par);
+                    } else {
+                        stage_two_levels(g, le, jlx, jly, sm.le[sj].own, sm.le[sj].par);
+                    }
+                }
+                __syncwarp();
+                if (active && L >= 2 && mine >= base && mine < base + kLaneSlots) {
+                    const int sl = mine - base;
+                    l2p_two_levels(gp->p, m.kzeta, m.inv_s, sm.le[sl].own,
+                                   L >= 3 ? sm.le[sl].par : nullptr, lx & 1u, ly & 1u, x, y, u,
+                                   v);
                 }
             }
-            __syncwarp();
-            if (active && L >= 2) l2p_add(gp->p, m.kzeta, m.inv_s, sm.le[slot], x, y, u, v);
         }
         if (active) {
             const uint32_t o = kSorted ? r : __float_as_uint(rec.w);
@@ -1505,26 +1576,45 @@ static unsigned resident_ctas(const void* kernel) {
 
 bool near_lane_path(int64_t n, int L) { return n > 0 && n <= (kLaneMean << (2 * L)); }
 
-// The FP32 near-field launch: the whole persistent grid (all CTAs that fit
-// on the GPU at once), work counter zeroed first.  With le null it writes the
-// near part alone, at the input indices or (sorted_out) in sorted order.
-// With lane_pos and a sparse evaluation (near_lane_path), leaves of at most
-// kLaneMaxT targets are queued there and the per-target-lane pass follows.
+// The FP32 near field's launches: for a sparse evaluation (near_lane_path)
+// the per-target-lane pass over every window of 32 sorted positions, then
+// the warp path on the whole persistent grid (all CTAs that fit on the GPU
+// at once; work counter zeroed first), skipping the lane pass's leaves.
+// With le null they write the near part alone, at the input indices or
+// (sorted_out) in sorted order.
 static cudaError_t launch_near_f32(const Geometry& g, double sigma, int64_t n,
                                    const void* particles, const uint32_t* skeys,
                                    const uint32_t* leaf_start, uint32_t* counter,
                                    const float* le, const float* l2l, float* uv, bool sorted_out,
-                                   RingStrips rs, uint32_t* lane_pos, cudaStream_t s) {
+                                   RingStrips rs, cudaStream_t s) {
     bool ok;
     NearF32v3 nm = near_constants(sigma, g, &ok);
     if (!ok) return cudaErrorInvalidValue;
     if (n == 0) return cudaSuccess;
-    LaneQueue lq{nullptr, nullptr};
-    if (lane_pos && near_lane_path(n, g.L)) {
-        nm.lane_nt = kLaneMaxT;
-        lq = LaneQueue{lane_pos, counter + 1};
-    }
+    const bool lanes = near_lane_path(n, g.L);
+    if (lanes) nm.lane_nt = kLaneMaxT;
     const bool cut = nm.ring_mask != 0;  // some ring leaf can hold a pair closer than a
+    const float4* sp = reinterpret_cast<const float4*>(particles);
+    cudaError_t e;
+    if (lanes) {
+        const LaneWindows lw{nullptr, (uint32_t)((n + 31) / 32), (uint32_t)n};
+        auto run = [&](auto kernel) {
+            const unsigned lb = (unsigned)std::min<uint64_t>(
+                resident_ctas(reinterpret_cast<const void*>(kernel)),
+                (lw.count + kLeafWarps - 1) / kLeafWarps);
+            kernel<<<dim3(lb), dim3(kLeafWarps * 32), 0, s>>>(sp, skeys, leaf_start, lw, g, nm,
+                                                              nullptr, nullptr, nullptr, le,
+                                                              l2l, nullptr, uv);
+            return cudaGetLastError();
+        };
+        if (cut)
+            e = sorted_out ? run(p2p_lane_kernel<false, true, true>)
+                           : run(p2p_lane_kernel<false, true, false>);
+        else
+            e = sorted_out ? run(p2p_lane_kernel<false, false, true>)
+                           : run(p2p_lane_kernel<false, false, false>);
+        if (e != cudaSuccess) return e;
+    }
     auto kernel_of = [&](int max_t) {
         return cut ? (max_t >= 4
                           ? reinterpret_cast<const void*>(p2p_l2p_f32_kernel<true, 4, false, false>)
@@ -1538,9 +1628,8 @@ static cudaError_t launch_near_f32(const Geometry& g, double sigma, int64_t n,
     if (resident_ctas(kernel_of(max_t)) != resident) return cudaErrorInvalidConfiguration;
     const unsigned needed = (ws.items + kLeafWarps - 1) / kLeafWarps;
     const unsigned blocks = std::min(needed, resident);
-    cudaError_t e = cudaMemsetAsync(counter, 0, (lq.pos ? 2 : 1) * sizeof(uint32_t), s);
+    e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    const float4* sp = reinterpret_cast<const float4*>(particles);
     if (!cut || !rs.n || !(nm.wstrip > 0.f)) rs.rec = nullptr;
     if (rs.rec) {
         const uint32_t nleaf = 1u << (2 * g.L);
@@ -1553,57 +1642,40 @@ static cudaError_t launch_near_f32(const Geometry& g, double sigma, int64_t n,
         if (resident_ctas(reinterpret_cast<const void*>(kernel)) != resident)
             return cudaErrorInvalidConfiguration;
         kernel<<<dim3(blocks), dim3(kLeafWarps * 32), 0, s>>>(sp, skeys, leaf_start, ws, counter,
-                                                              g, nm, le, l2l, uv, rs, lq);
+                                                              g, nm, le, l2l, uv, rs);
         return cudaGetLastError();
     };
-    // the kernel for (cut, max_t, sorted_out), with the queue when there is one
-    auto pick = [&](auto queue) {
-        constexpr bool kQ = decltype(queue)::value;
+    // the kernel for (cut, max_t, sorted_out), skipping the lane pass's leaves
+    // when there is one
+    auto pick = [&](auto skip) {
+        constexpr bool kS = decltype(skip)::value;
         if (cut && max_t >= 4)
-            return sorted_out ? go(p2p_l2p_f32_kernel<true, 4, true, kQ>)
-                              : go(p2p_l2p_f32_kernel<true, 4, false, kQ>);
+            return sorted_out ? go(p2p_l2p_f32_kernel<true, 4, true, kS>)
+                              : go(p2p_l2p_f32_kernel<true, 4, false, kS>);
         if (cut)
-            return sorted_out ? go(p2p_l2p_f32_kernel<true, 2, true, kQ>)
-                              : go(p2p_l2p_f32_kernel<true, 2, false, kQ>);
-        return sorted_out ? go(p2p_l2p_f32_kernel<false, 4, true, kQ>)
-                          : go(p2p_l2p_f32_kernel<false, 4, false, kQ>);
+            return sorted_out ? go(p2p_l2p_f32_kernel<true, 2, true, kS>)
+                              : go(p2p_l2p_f32_kernel<true, 2, false, kS>);
+        return sorted_out ? go(p2p_l2p_f32_kernel<false, 4, true, kS>)
+                          : go(p2p_l2p_f32_kernel<false, 4, false, kS>);
     };
-    e = lq.pos ? pick(std::true_type{}) : pick(std::false_type{});
-    if (e != cudaSuccess || !lq.pos) return e;
-    // the queued targets: at most n, 32 per warp
-    auto lanes = [&](auto kernel) {
-        const unsigned lb = (unsigned)std::min<uint64_t>(
-            resident_ctas(reinterpret_cast<const void*>(kernel)),
-            ((uint64_t)n + 32 * kLeafWarps - 1) / (32 * kLeafWarps));
-        kernel<<<dim3(lb), dim3(kLeafWarps * 32), 0, s>>>(sp, skeys, leaf_start, lq, g, nm,
-                                                          nullptr, nullptr, nullptr, le, l2l,
-                                                          nullptr, uv);
-        return cudaGetLastError();
-    };
-    if (cut)
-        return sorted_out ? lanes(p2p_lane_kernel<false, true, true>)
-                          : lanes(p2p_lane_kernel<false, true, false>);
-    return sorted_out ? lanes(p2p_lane_kernel<false, false, true>)
-                      : lanes(p2p_lane_kernel<false, false, false>);
+    return lanes ? pick(std::true_type{}) : pick(std::false_type{});
 }
 
 template <>
 cudaError_t launch_p2p_l2p<float>(const Geometry& g, double sigma, int64_t n,
                                   const void* particles, const uint32_t* skeys,
                                   const uint32_t* leaf_start, uint32_t* counter, const float* le,
-                                  const float* l2l, float* uv, uint32_t* lane_pos,
-                                  cudaStream_t s) {
+                                  const float* l2l, float* uv, cudaStream_t s) {
     return launch_near_f32(g, sigma, n, particles, skeys, leaf_start, counter, le, l2l, uv, false,
-                           RingStrips{nullptr, nullptr}, lane_pos, s);
+                           RingStrips{nullptr, nullptr}, s);
 }
 
 cudaError_t launch_near_only_f32(const Geometry& g, double sigma, int64_t n,
                                  const void* particles, const uint32_t* skeys,
                                  const uint32_t* leaf_start, uint32_t* counter, float* out,
-                                 bool sorted_out, RingStrips strips, uint32_t* lane_pos,
-                                 cudaStream_t s) {
+                                 bool sorted_out, RingStrips strips, cudaStream_t s) {
     return launch_near_f32(g, sigma, n, particles, skeys, leaf_start, counter, nullptr, nullptr,
-                           out, sorted_out, strips, lane_pos, s);
+                           out, sorted_out, strips, s);
 }
 
 // L2P after a near-field-only pass: one warp per leaf adds the leaf's local
@@ -1621,8 +1693,9 @@ __global__ void __launch_bounds__(kLeafWarps * 32)
 l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start, Geometry g,
                float sc, float kzeta, float inv_s, const float* __restrict__ le,
                const float* __restrict__ l2l, const float2* __restrict__ uvs,
-               float* __restrict__ uv) {
+               float* __restrict__ uv, uint32_t lane_nt) {
     __shared__ float2 leaf_le[kLeafWarps][kMaxP];
+    __shared__ float2 parts[kLeafWarps][2][kMaxP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t leaf = blockIdx.x * kLeafWarps + warp;
     if (leaf >= (1u << (2 * g.L))) return;  // warp-uniform
@@ -1640,10 +1713,42 @@ l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_
             uv[2 * (int64_t)idx + 1] = v;
         }
     };
+    // a leaf of the per-target-lane pass: its far field as that pass forms it
+    // (the expansion's two parts, l2p_two_levels)
+    auto lane_leaf = [&](uint32_t t0, uint32_t t1) {
+        stage_two_levels(g, le, lx, ly, parts[warp][0], parts[warp][1]);
+        __syncwarp();
+        for (uint32_t k = t0 + lane; k < t1; k += 32) {
+            const float4 rec = sp[k];
+            const uint32_t idx = __float_as_uint(rec.w);
+            float u, v;
+            if (kSorted) {
+                const float2 w = uvs[k];
+                u = w.x;
+                v = w.y;
+            } else {
+                u = uv[2 * (int64_t)idx];
+                v = uv[2 * (int64_t)idx + 1];
+            }
+            const float x = ((rec.x - cxh) - cxl) * sc, y = ((rec.y - cyh) - cyl) * sc;
+            l2p_two_levels(g.p, kzeta, inv_s, parts[warp][0], g.L >= 3 ? parts[warp][1] : nullptr,
+                           lx & 1u, ly & 1u, x, y, u, v);
+            if (kSorted && uv8) {
+                *reinterpret_cast<float2*>(uv + 2 * (int64_t)idx) = make_float2(u, v);
+            } else {
+                uv[2 * (int64_t)idx] = u;
+                uv[2 * (int64_t)idx + 1] = v;
+            }
+        }
+    };
     if (!kSorted) {
         const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
         if (t0 == t1) return;
         leaf_centre_hilo(g, lx, ly, &cxh, &cxl, &cyh, &cyl);
+        if (t1 - t0 <= lane_nt) {
+            lane_leaf(t0, t1);
+            return;
+        }
         leaf_le_build(g, le, l2l, lx, ly, leaf_le[warp]);
         for (uint32_t k = t0 + lane; k < t1; k += 32) {
             const float4 rec = sp[k];
@@ -1656,6 +1761,10 @@ l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_
     leaf_centre_hilo(g, lx, ly, &cxh, &cxl, &cyh, &cyl);
     const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
     if (t0 == t1) return;
+    if (t1 - t0 <= lane_nt) {
+        lane_leaf(t0, t1);
+        return;
+    }
     const uint32_t k0 = t0 + lane, k1 = k0 + 32;
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
     float2 w0 = make_float2(0.f, 0.f), w1 = w0;
@@ -1681,22 +1790,23 @@ l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_
     }
 }
 
-cudaError_t launch_l2p_f32(const Geometry& g, double sigma, const void* particles,
+cudaError_t launch_l2p_f32(const Geometry& g, double sigma, int64_t n, const void* particles,
                            const uint32_t* leaf_start, const float* le, const float* l2l,
                            const float* uv_sorted, float* uv, cudaStream_t s) {
     if (g.L < 2) return cudaSuccess;
     bool ok;
     const NearF32v3 nm = near_constants(sigma, g, &ok);
     if (!ok) return cudaErrorInvalidValue;
+    const uint32_t lane_nt = near_lane_path(n, g.L) ? kLaneMaxT : 0u;
     const unsigned blocks = (unsigned)(((uint64_t)1 << (2 * g.L)) / kLeafWarps);
     const float4* sp = reinterpret_cast<const float4*>(particles);
     const float2* uvs = reinterpret_cast<const float2*>(uv_sorted);
     if (uv_sorted)
-        l2p_f32_kernel<true><<<blocks, kLeafWarps * 32, 0, s>>>(sp, leaf_start, g, nm.sc, nm.kzeta,
-                                                                nm.inv_s, le, l2l, uvs, uv);
+        l2p_f32_kernel<true><<<blocks, kLeafWarps * 32, 0, s>>>(
+            sp, leaf_start, g, nm.sc, nm.kzeta, nm.inv_s, le, l2l, uvs, uv, lane_nt);
     else
         l2p_f32_kernel<false><<<blocks, kLeafWarps * 32, 0, s>>>(
-            sp, leaf_start, g, nm.sc, nm.kzeta, nm.inv_s, le, l2l, uvs, uv);
+            sp, leaf_start, g, nm.sc, nm.kzeta, nm.inv_s, le, l2l, uvs, uv, lane_nt);
     return cudaGetLastError();
 }
 
@@ -1728,7 +1838,8 @@ cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
                              int ctas_per_sm, const void* particles, const uint32_t* skeys,
                              const uint32_t* leaf_start, const float* le, const float* l2l16,
                              const float* l2l32, float* uv, bool cut, RingStrips strips,
-                             uint32_t nleaf_total, uint32_t* lane_pos, cudaStream_t s) {
+                             uint32_t nleaf_total, const uint32_t* lane_win,
+                             uint32_t lane_win_count, cudaStream_t s) {
     if (ntotal == 0) return cudaSuccess;
     Geometry g1{};
     g1.W = 2.0;
@@ -1740,10 +1851,26 @@ cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     unsigned blocks = (unsigned)(sms * ctas_per_sm);
-    // lane_pos: some instance sends its sparse leaves to the per-target-lane
-    // pass (queue length in the counter's second word)
-    const LaneQueue lq = lane_pos ? LaneQueue{lane_pos, counter + 1} : LaneQueue{nullptr, nullptr};
-    cudaError_t e = cudaMemsetAsync(counter, 0, (lq.pos ? 2 : 1) * sizeof(uint32_t), s);
+    const float4* sp = reinterpret_cast<const float4*>(particles);
+    const NearInst* ni = static_cast<const NearInst*>(near_inst);
+    cudaError_t e;
+    // the per-target-lane pass over the windows of the sparse instances
+    const bool lanes = lane_win && lane_win_count > 0;
+    if (lanes) {
+        const LaneWindows lw{lane_win, lane_win_count, ntotal};
+        auto run = [&](auto kernel) {
+            const unsigned lb = (unsigned)std::min<uint64_t>(
+                resident_ctas(reinterpret_cast<const void*>(kernel)),
+                (lw.count + kLeafWarps - 1) / kLeafWarps);
+            kernel<<<dim3(lb), dim3(kLeafWarps * 32), 0, s>>>(sp, skeys, leaf_start, lw,
+                                                              Geometry{}, shared_nm, inst, ni,
+                                                              leaf_inst, le, l2l16, l2l32, uv);
+            return cudaGetLastError();
+        };
+        e = cut ? run(p2p_lane_kernel<true, true, false>) : run(p2p_lane_kernel<true, false, false>);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     if (!cut || !strips.n) strips.rec = nullptr;
     if (strips.rec) {
@@ -1754,31 +1881,16 @@ cudaError_t launch_batch_p2p(const BatchInst* inst, const void* near_inst,
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    const float4* sp = reinterpret_cast<const float4*>(particles);
-    const NearInst* ni = static_cast<const NearInst*>(near_inst);
     const WorkSplit ws = work_split(ntotal, (uint64_t)blocks * kLeafWarps);
     auto dense = [&](auto kernel) {
         kernel<<<blocks, kLeafWarps * 32, 0, s>>>(sp, skeys, leaf_start, inst, ni, leaf_inst, ws,
-                                                  counter, shared_nm, le, l2l16, l2l32, uv, strips,
-                                                  lq);
+                                                  counter, shared_nm, le, l2l16, l2l32, uv,
+                                                  strips);
         return cudaGetLastError();
     };
     if (cut)
-        e = lq.pos ? dense(p2p_batch_kernel<true, true>) : dense(p2p_batch_kernel<true, false>);
-    else
-        e = lq.pos ? dense(p2p_batch_kernel<false, true>) : dense(p2p_batch_kernel<false, false>);
-    if (e != cudaSuccess || !lq.pos) return e;
-    auto lanes = [&](auto kernel) {
-        const unsigned lb = (unsigned)std::min<uint64_t>(
-            resident_ctas(reinterpret_cast<const void*>(kernel)),
-            ((uint64_t)ntotal + 32 * kLeafWarps - 1) / (32 * kLeafWarps));
-        kernel<<<dim3(lb), dim3(kLeafWarps * 32), 0, s>>>(sp, skeys, leaf_start, lq, Geometry{},
-                                                          shared_nm, inst, ni, leaf_inst, le,
-                                                          l2l16, l2l32, uv);
-        return cudaGetLastError();
-    };
-    return cut ? lanes(p2p_lane_kernel<true, true, false>)
-               : lanes(p2p_lane_kernel<true, false, false>);
+        return lanes ? dense(p2p_batch_kernel<true, true>) : dense(p2p_batch_kernel<true, false>);
+    return lanes ? dense(p2p_batch_kernel<false, true>) : dense(p2p_batch_kernel<false, false>);
 }
 
 template <>
@@ -1786,9 +1898,8 @@ cudaError_t launch_p2p_l2p<double>(const Geometry& g, double sigma, int64_t n,
                                    const void* particles, const uint32_t* skeys,
                                    const uint32_t* leaf_start, uint32_t* counter,
                                    const double* le, const double* l2l, double* uv,
-                                   uint32_t* lane_pos, cudaStream_t s) {
+                                   cudaStream_t s) {
     (void)n;
-    (void)lane_pos;  // FP64: one CTA per leaf, no per-target-lane pass
     (void)skeys;
     (void)counter;  // one CTA per leaf
     NearF64 nm;

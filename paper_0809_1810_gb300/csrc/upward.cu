@@ -21,21 +21,18 @@ namespace {
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr int kTopLevel = 2;  // levels <= kTopLevel run in the single-CTA kernel
 
-// One warp per leaf, four sibling leaves per CTA; lanes stride over the
-// leaf's particles, accumulate all coefficients, then reduce across the warp.
-// `quad` is the parent box (Morton key at level L-1); leaf keys are offset by
-// leaf_base in leaf_start (zero for a single evaluation).
+// P2M of one leaf by one warp: lanes stride over the leaf's particles,
+// accumulate all coefficients, then reduce across the warp.  Writes the
+// leaf's expansion to me and a copy to kid (2 PMAX reals) for the parent's
+// translation.  Leaf keys are offset by leaf_base in leaf_start (zero for a
+// single evaluation).
 template <typename R, int PMAX>
-__device__ __forceinline__ void p2m_quad(const typename ParticleOf<R>::type* __restrict__ sp,
+__device__ __forceinline__ void p2m_leaf(const typename ParticleOf<R>::type* __restrict__ sp,
                                          const uint32_t* __restrict__ leaf_start,
-                                         uint32_t leaf_base, uint32_t quad, const Geometry& g,
-                                         const R* __restrict__ m2m, bool fuse_parent,
-                                         R* __restrict__ me,
-                                         typename Cplx<R>::T (*child_me)[PMAX],
-                                         typename Cplx<R>::T (*part)[PMAX]) {
+                                         uint32_t leaf_base, uint32_t leaf, const Geometry& g,
+                                         R* __restrict__ me, R* kid) {
     using C = typename Cplx<R>::T;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t leaf = quad * 4 + warp;
+    const int lane = threadIdx.x & 31;
     const uint32_t ix = morton_compact(leaf), iy = morton_compact(leaf >> 1);
     const uint32_t b = leaf_start[leaf_base + leaf], e = leaf_start[leaf_base + leaf + 1];
     const double scale = g.scale;
@@ -96,12 +93,29 @@ __device__ __forceinline__ void p2m_quad(const typename ParticleOf<R>::type* __r
     }
     constexpr int W = N / 32;
     R* dst = me + box_slot(g.level_base, g.L, ix, iy) * (2 * g.P);
-    R* kid = reinterpret_cast<R*>(child_me[warp]);
 #pragma unroll
     for (int j = 0; j < W; ++j) {
         dst[lane * W + j] = v[j];
         kid[lane * W + j] = v[j];
     }
+}
+
+// One warp per leaf, four sibling leaves per CTA (p2m_leaf), then the parent.
+// `quad` is the parent box (Morton key at level L-1).
+template <typename R, int PMAX>
+__device__ __forceinline__ void p2m_quad(const typename ParticleOf<R>::type* __restrict__ sp,
+                                         const uint32_t* __restrict__ leaf_start,
+                                         uint32_t leaf_base, uint32_t quad, const Geometry& g,
+                                         const R* __restrict__ m2m, bool fuse_parent,
+                                         R* __restrict__ me,
+                                         typename Cplx<R>::T (*child_me)[PMAX],
+                                         typename Cplx<R>::T (*part)[PMAX]) {
+    using C = typename Cplx<R>::T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t leaf = quad * 4 + warp;
+    const uint32_t ix = morton_compact(leaf), iy = morton_compact(leaf >> 1);
+    p2m_leaf<R, PMAX>(sp, leaf_start, leaf_base, leaf, g, me,
+                      reinterpret_cast<R*>(child_me[warp]));
     if (!fuse_parent) return;  // uniform over the CTA
     __syncthreads();
     // parent at level L-1: warp q translates its own child quadrant q (one
@@ -135,17 +149,158 @@ p2m_kernel(const typename ParticleOf<R>::type* __restrict__ sp,
     p2m_quad<R, PMAX>(sp, leaf_start, 0, blockIdx.x, g, m2m, fuse_parent, me, child_me, part);
 }
 
-// Batched: one CTA per parent box of any instance of the class.
+// One warp per parent box (batched instances of at most 32 particles per leaf
+// on average, whose boxes are mostly sparse).  A sparse box, every child
+// leaf holding at most kQuadSparse particles, is formed with eight lanes per
+// child (child q in lanes 8q .. 8q + 7, its particle j in lane 8q + j)
+// instead of a warp per child with most lanes idle; another box one child
+// after the other (p2m_leaf).  Either way the expansions are p2m_quad's, bit
+// for bit: in the sparse form a lane's one particle enters its coefficients
+// as 0 + c zeta^m as there, and the sum over a child's eight lanes pairs
+// lanes as the last three steps of p2m_quad's butterfly do (its first two
+// steps only add the zeros of its empty lanes, exactly; no partial sum is
+// -0, since each starts from +0).  The parent's translation runs the same
+// chains (child q, coefficient n) and adds the four in quadrant order.
+constexpr uint32_t kQuadSparse = 8;
+
+template <int PMAX>
+__device__ __forceinline__ void p2m_quad_warp(const float4* __restrict__ sp,
+                                              const uint32_t* __restrict__ leaf_start,
+                                              uint32_t leaf_base, uint32_t quad,
+                                              const Geometry& g, const float* __restrict__ m2m,
+                                              bool fuse_parent, float* __restrict__ me,
+                                              float2 (*child_me)[PMAX], float2 (*part)[PMAX]) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t* cnt = leaf_start + leaf_base + quad * 4;
+    const uint32_t s0 = cnt[0], s1 = cnt[1], s2 = cnt[2], s3 = cnt[3], s4 = cnt[4];
+    const bool sparse = s1 - s0 <= kQuadSparse && s2 - s1 <= kQuadSparse &&
+                        s3 - s2 <= kQuadSparse && s4 - s3 <= kQuadSparse;
+    __syncwarp();  // earlier readers of child_me are done
+    if (sparse) {
+        const int q = lane >> 3, j = lane & 7;
+        const uint32_t leaf = quad * 4 + q;
+        const uint32_t ix = morton_compact(leaf), iy = morton_compact(leaf >> 1);
+        const uint32_t b = leaf_start[leaf_base + leaf], e = leaf_start[leaf_base + leaf + 1];
+        float cxh, cxl, cyh, cyl;  // the lane's own leaf centre (no warp broadcast)
+        if (g.centre_tab) {
+            const float4 tx = g.centre_tab[ix], ty = g.centre_tab[iy];
+            cxh = tx.x;
+            cxl = tx.y;
+            cyh = ty.z;
+            cyl = ty.w;
+        } else {
+            centre_hilo_1d(g.x0, g.W, g.L, ix, &cxh, &cxl);
+            centre_hilo_1d(g.y0, g.W, g.L, iy, &cyh, &cyl);
+        }
+        const float inv_s = (float)g.scale;
+        const float inv2pi = (float)(1.0 / kTwoPi);
+        float2 acc[PMAX];
+#pragma unroll
+        for (int m = 0; m < PMAX; ++m) acc[m] = make_float2(0.f, 0.f);
+        if (b + j < e) {
+            const float4 rec = sp[b + j];
+            const float2 zeta =
+                make_float2(((rec.x - cxh) - cxl) * inv_s, ((rec.y - cyh) - cyl) * inv_s);
+            float2 pw = make_float2(0.f, -rec.z * inv2pi);  // c_i = -j Gamma / 2pi
+#pragma unroll
+            for (int m = 0; m < PMAX; ++m) {
+                if (m < g.p) {
+                    acc[m].x += pw.x;
+                    acc[m].y += pw.y;
+                    pw = cmul(pw, zeta);
+                }
+            }
+        }
+        // reduce-scatter over the child's eight lanes: lane j keeps reals
+        // [j W8, (j + 1) W8) of the child's 2 PMAX
+        constexpr int N = 2 * PMAX;
+        float v[N];
+#pragma unroll
+        for (int m = 0; m < PMAX; ++m) {
+            v[2 * m] = acc[m].x;
+            v[2 * m + 1] = acc[m].y;
+        }
+#pragma unroll
+        for (int step = 0; step < 3; ++step) {
+            const int o = 4 >> step;
+            const int half = (N >> step) >> 1;
+            const bool upper = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < half; ++i) {
+                const float send = upper ? v[i] : v[i + half];
+                const float keep = upper ? v[i + half] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+        constexpr int W8 = N / 8;
+        float* dst = me + box_slot(g.level_base, g.L, ix, iy) * (2 * g.P);
+        float* kid = reinterpret_cast<float*>(child_me[q]);
+#pragma unroll
+        for (int t = 0; t < W8; ++t) {
+            dst[j * W8 + t] = v[t];
+            kid[j * W8 + t] = v[t];
+        }
+    } else {
+        for (int q = 0; q < 4; ++q)
+            p2m_leaf<float, PMAX>(sp, leaf_start, leaf_base, quad * 4 + q, g, me,
+                                  reinterpret_cast<float*>(child_me[q]));
+    }
+    if (!fuse_parent) return;  // uniform over the warp
+    __syncwarp();
+    // parent at level L-1: the four children's translations, chain (cq, n)
+    for (int c = lane; c < 4 * PMAX; c += 32) {
+        const int cq = c / PMAX, n = c % PMAX;
+        if (n < g.P) {
+            const float2* tq = reinterpret_cast<const float2*>(m2m) + (int64_t)cq * g.P * g.P;
+            float2 acc_q = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < PMAX; ++k)
+                if (k < g.P) acc_q = cfma(tq[k * g.P + n], child_me[cq][k], acc_q);
+            part[cq][n] = acc_q;
+        }
+    }
+    __syncwarp();
+    if (lane < g.P) {
+        float2 out = part[0][lane];
+        for (int k = 1; k < 4; ++k)
+            out = make_float2(out.x + part[k][lane].x, out.y + part[k][lane].y);
+        if (lane >= g.p) out = make_float2(0.f, 0.f);
+        const uint32_t px = morton_compact(quad), py = morton_compact(quad >> 1);
+        reinterpret_cast<float2*>(me + box_slot(g.level_base, g.L - 1, px, py) *
+                                           (2 * g.P))[lane] = out;
+    }
+}
+
+// Batched: one CTA per parent box of the class's other instances (the quads
+// from nquads_warp on).
 template <int PMAX>
 __global__ void __launch_bounds__(128)
 p2m_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
                  const BatchInst* __restrict__ inst, const int32_t* __restrict__ quad_inst,
-                 const uint32_t* __restrict__ quad_local, const float* __restrict__ m2m,
-                 float* __restrict__ me) {
+                 const uint32_t* __restrict__ quad_local, int64_t first,
+                 const float* __restrict__ m2m, float* __restrict__ me) {
     __shared__ float2 child_me[4][PMAX], part[4][PMAX];
-    const BatchInst& b = inst[quad_inst[blockIdx.x]];
-    p2m_quad<float, PMAX>(sp, leaf_start, b.leaf_base, quad_local[blockIdx.x], b.g, m2m,
-                          b.g.L >= 3, me + b.exp_off, child_me, part);
+    const int64_t qi = first + blockIdx.x;
+    const BatchInst& b = inst[quad_inst[qi]];
+    p2m_quad<float, PMAX>(sp, leaf_start, b.leaf_base, quad_local[qi], b.g, m2m, b.g.L >= 3,
+                          me + b.exp_off, child_me, part);
+}
+
+// Batched, instances of at most 32 particles per leaf on average: one warp
+// per parent box (p2m_quad_warp), four per CTA, quads [0, count).
+template <int PMAX>
+__global__ void __launch_bounds__(128)
+p2m_batch_warp_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
+                      const BatchInst* __restrict__ inst, const int32_t* __restrict__ quad_inst,
+                      const uint32_t* __restrict__ quad_local, int64_t count,
+                      const float* __restrict__ m2m, float* __restrict__ me) {
+    __shared__ float2 child_me[4][4][PMAX], part[4][4][PMAX];
+    const int warp = threadIdx.x >> 5;
+    const int64_t qi = (int64_t)blockIdx.x * 4 + warp;
+    if (qi >= count) return;  // uniform over the warp
+    const BatchInst& b = inst[quad_inst[qi]];
+    p2m_quad_warp<PMAX>(sp, leaf_start, b.leaf_base, quad_local[qi], b.g, m2m, b.g.L >= 3,
+                        me + b.exp_off, child_me[warp], part[warp]);
 }
 
 // M2M of one box with G lanes (lane n computes b~_n); children read by lane k
@@ -235,14 +390,24 @@ cudaError_t launch_batch_p2m(const BatchInst* inst, const BatchLists& bl, int P,
                              float* me, cudaStream_t s) {
     if (bl.nquads == 0) return cudaSuccess;
     const float4* sp = reinterpret_cast<const float4*>(particles);
-    if (P <= 16)
-        p2m_batch_kernel<16><<<(unsigned)bl.nquads, 128, 0, s>>>(sp, leaf_start, inst,
-                                                                bl.quad_inst, bl.quad_local, m2m,
-                                                                me);
-    else
-        p2m_batch_kernel<32><<<(unsigned)bl.nquads, 128, 0, s>>>(sp, leaf_start, inst,
-                                                                bl.quad_inst, bl.quad_local, m2m,
-                                                                me);
+    const int64_t nw = bl.nquads_warp, nc = bl.nquads - bl.nquads_warp;
+    if (nw > 0) {
+        const unsigned blocks = (unsigned)((nw + 3) / 4);
+        if (P <= 16)
+            p2m_batch_warp_kernel<16><<<blocks, 128, 0, s>>>(sp, leaf_start, inst, bl.quad_inst,
+                                                             bl.quad_local, nw, m2m, me);
+        else
+            p2m_batch_warp_kernel<32><<<blocks, 128, 0, s>>>(sp, leaf_start, inst, bl.quad_inst,
+                                                             bl.quad_local, nw, m2m, me);
+    }
+    if (nc > 0) {
+        if (P <= 16)
+            p2m_batch_kernel<16><<<(unsigned)nc, 128, 0, s>>>(sp, leaf_start, inst, bl.quad_inst,
+                                                              bl.quad_local, nw, m2m, me);
+        else
+            p2m_batch_kernel<32><<<(unsigned)nc, 128, 0, s>>>(sp, leaf_start, inst, bl.quad_inst,
+                                                              bl.quad_local, nw, m2m, me);
+    }
     return cudaGetLastError();
 }
 

@@ -8,8 +8,7 @@ Bars:
   on both sides of both thresholds (leaf counts 16 / 17, mean occupancy 32 /
   just above), with and without the Sec. 4.1 cutoff, at every L the near
   field handles alone (0, 1) and with a far field;
-* repeat evaluations bit-identical: the queue's order changes from run to
-  run, a target's arithmetic does not;
+* repeat evaluations bit-identical;
 * the pass runs exactly when the evaluation is sparse (one more kernel per
   call);
 * a batch of sparse instances equal to their single plans bit for bit.
