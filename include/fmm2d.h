@@ -89,11 +89,8 @@ const char* fmm2d_last_error(void);
  * translation tables (M2M of Sec. 3.3.2, M2L of Eq. 22, L2L of Sec. 3.3.3)
  * in double precision on the device.  FP32 plans with a cutoff (L >= 2,
  * max_n < 2^30) also hold the near field's ring strips: 64 bytes per
- * particle and 16 per leaf.  FP32 plans hold 4 bytes per particle more for
- * the queue of sparse leaves' targets (an evaluation of at most 32
- * particles per leaf on average evaluates its leaves of at most 16
- * particles one target per lane).  Synchronous.  On failure *out is set to
- * NULL and nothing is leaked. */
+ * particle and 16 per leaf.  Synchronous.  On failure *out is set to NULL and
+ * nothing is leaked. */
 fmm2d_status fmm2d_plan_create(fmm2d_plan** out, const fmm2d_params* prm);
 
 /* Release the plan and its workspace.  Synchronises the device first.
@@ -267,9 +264,7 @@ const char* fmm2d_batch_last_error(void);
 
 /* Create a batch plan for `count` instances (copied): validates them, packs
  * them (sum of n and sum of 4^L below 2^32), allocates the workspace on the
- * current device (with 4 bytes per particle for the sparse-leaf queue when
- * some instance has at most 32 particles per leaf on average) and builds the
- * translation tables.  Synchronous. */
+ * current device and builds the translation tables.  Synchronous. */
 fmm2d_status fmm2d_batch_plan_create(fmm2d_batch_plan** out, int count,
                                      const fmm2d_instance* instances);
 /* The same with a precision: FMM2D_FP32 (as fmm2d_batch_plan_create: float

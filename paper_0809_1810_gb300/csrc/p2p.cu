@@ -1205,18 +1205,17 @@ p2p_batch_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ ske
 // that its warps read neighbouring records and share them in L1); a lane
 // whose target lies in a leaf of at most kLaneMaxT targets (in a sparse
 // evaluation) walks that target's local list itself: the 9 ranges of its
-// leaf's 3x3 neighbourhood, then (with a cutoff) the 16 ring ranges,
-// reading the sorted records from global memory (the lanes of one leaf read
-// the same records: one broadcast), two records per step as one packed
-// pair.  Every pair of the 3x3 block takes the near-band form (the
-// polynomial below qthr), every ring pair the cutoff correction.  The walk's
-// trip count is the warp's longest list; a lane past its own end evaluates
-// dummies (zero circulation, far away).  Sums: blocks of kLanePairs pairs
-// into fresh registers, then compensated.  Far field (when le is given):
-// the warp forms the local expansion of each leaf it holds once, with the
-// warp path's operations (leaf_le_build_unrolled), in shared memory, and
-// each lane adds its own L2P (l2p_add).  A target's arithmetic does not
-// depend on which warp or lane takes it.
+// leaf's 3x3 neighbourhood, then (with a cutoff) the ring leaves that come
+// within the cutoff of the target, reading the sorted records from global
+// memory (the lanes of one leaf read the same records: one broadcast), two
+// records per step as one packed pair.  Every pair of the 3x3 block takes
+// the near-band form (the polynomial below qthr), every ring pair the cutoff
+// correction.  The walk's trip count is the warp's longest list; a lane past
+// its own end evaluates dummies (zero circulation, far away).  Sums: blocks
+// of kLanePairs pairs into fresh registers, then compensated.  Far field
+// (when le is given): the leaf's two expansion parts, staged once per warp
+// in shared memory, evaluated by each lane (l2p_two_levels).  A target's
+// arithmetic does not depend on which warp or lane takes it.
 // ---------------------------------------------------------------------------
 constexpr int kLaneRanges = 25;      // 9 local + 16 ring
 constexpr uint32_t kLanePairs = 32;  // pairs per first-level partial sum
@@ -1350,6 +1349,8 @@ p2p_lane_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skey
             m.inv_s = ni.inv_s;
             m.qa = ni.qa;
             m.ring_mask = ni.ring_mask;
+            m.half_leaf = ni.half_leaf;
+            m.band_a2 = ni.band_a2;
             gate = ni.lane_nt;
             leaf_base = inst[ii].leaf_base;
             gp = &inst[ii].g;
@@ -1396,8 +1397,14 @@ p2p_lane_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ skey
                 ring_offset(q, &dx, &dy);
                 const int sx = (int)lx + dx, sy = (int)ly + dy;
                 uint32_t b = 0, e = 0;
+                // a ring leaf farther than the cutoff from the target itself holds
+                // no pair under it (band_a2's 2% margin covers the roundings)
+                const float ex =
+                    fmaxf(fabsf(x - (float)(2 * dx) * m.half_leaf) - m.half_leaf, 0.f);
+                const float ey =
+                    fmaxf(fabsf(y - (float)(2 * dy) * m.half_leaf) - m.half_leaf, 0.f);
                 if (active && ((m.ring_mask >> q) & 1u) && sx >= 0 && sy >= 0 && sx < nl &&
-                    sy < nl) {
+                    sy < nl && fmaf(ex, ex, ey * ey) < m.band_a2) {
                     const uint32_t k = leaf_base + morton_key((uint32_t)sx, (uint32_t)sy);
                     b = leaf_start[k];
                     e = leaf_start[k + 1];
