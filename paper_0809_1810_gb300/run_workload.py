@@ -1,7 +1,7 @@
 """Run full FMM evaluations of a named synthetic workload on cuda:0.
 
     python -m paper_0809_1810_gb300.run_workload --workload uniform_1m --steps 3 [--p P --L L]
-    python -m paper_0809_1810_gb300.run_workload --workload batch_sweep --steps 3
+    python -m paper_0809_1810_gb300.run_workload --workload batch_sweep --steps 3 [--per-leaf 0 32]
 
 Each step is one complete fmm2d_velocity call (tree build to velocities),
 or for batch_sweep one fmm2d_batch_velocity call over the 512 instances of
@@ -37,6 +37,9 @@ WORKLOADS = {
 
 def run_batch_sweep(args):
     ws = [W.make_instance(s) for s in W.batch_instances(512, seed=3)[:args.instances]]
+    if args.per_leaf:  # one class of mean leaf occupancy, as its own batch
+        lo, hi = args.per_leaf
+        ws = [w for w in ws if lo <= w.n / 4 ** w.L < hi]
     xy = torch.tensor(np.concatenate([np.stack([w.x, w.y], 1) for w in ws]), device="cuda")
     g = torch.tensor(np.concatenate([w.gamma for w in ws]), device="cuda")
     insts = [{"n": w.n, "p": w.p, "L": w.L, "sigma": w.sigma, "root": w.root,
@@ -76,6 +79,8 @@ def main():
                     help="also print the mean per-phase times (events inside the graph)")
     ap.add_argument("--instances", type=int, default=512,
                     help="batch_sweep: the first this many of its 512 instances")
+    ap.add_argument("--per-leaf", type=float, nargs=2, default=None, metavar=("LO", "HI"),
+                    help="batch_sweep: only the instances with LO <= n / 4^L < HI")
     args = ap.parse_args()
     if args.workload == "batch_sweep":
         run_batch_sweep(args)
