@@ -247,10 +247,16 @@ __device__ __forceinline__ void p2m_quad_warp(const float4* __restrict__ sp,
     }
     if (!fuse_parent) return;  // uniform over the warp
     __syncwarp();
-    // parent at level L-1: the four children's translations, chain (cq, n)
+    // parent at level L-1: the four children's translations, chain (cq, n).
+    // An empty child's expansion is +0 throughout, and so is its chain's
+    // result (each step adds +0): it is written without the chain.
+    const unsigned empty = (s1 == s0 ? 1u : 0u) | (s2 == s1 ? 2u : 0u) | (s3 == s2 ? 4u : 0u) |
+                           (s4 == s3 ? 8u : 0u);
     for (int c = lane; c < 4 * PMAX; c += 32) {
         const int cq = c / PMAX, n = c % PMAX;
-        if (n < g.P) {
+        if (n < g.P && ((empty >> cq) & 1u)) {
+            part[cq][n] = make_float2(0.f, 0.f);
+        } else if (n < g.P) {
             const float2* tq = reinterpret_cast<const float2*>(m2m) + (int64_t)cq * g.P * g.P;
             float2 acc_q = make_float2(0.f, 0.f);
 #pragma unroll
