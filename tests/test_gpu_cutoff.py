@@ -111,6 +111,32 @@ def test_fp32_cutoff_matches_oracle(name, make, af, prec):
     assert _rel(plain, ref) > 10 * FP32_TOL, _rel(plain, ref)
 
 
+# (n, p, L, sigma / h, a / leaf width) where ring strips apply (a at most 1.5
+# leaf widths) and a >= 4.4 sigma, so that the FP32 bar holds against the
+# oracle's cut FMM: mean occupancy 47 and 39 per leaf (the warp path for
+# every leaf, its ring gathered from the strips), and 8 (mostly the
+# per-target-lane pass, which walks whole ring leaves).
+STRIP_ORACLE_CASES = [(12000, 14, 4, 2.0, 1.40), (40000, 12, 5, 1.8, 1.45),
+                      (8192, 10, 5, 0.83, 1.45)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_tc"])
+@pytest.mark.parametrize("n,p,L,soh,af", STRIP_ORACLE_CASES)
+def test_strip_geometry_matches_oracle(n, p, L, soh, af, prec):
+    w = W.uniform_random(n, n + 11, 2.0 / np.sqrt(n), sigma_over_h=soh, p=p, L=L,
+                         dtype=np.float32)
+    a = af * _leaf(w)
+    assert a >= 4.4 * w.sigma
+    ref = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.p, w.L, w.root, a=a)
+    xy, g = _dev(w, torch.float32)
+    with _plan(w, prec, a) as plan:
+        uv = plan.velocity(xy, g, check=True).double().cpu().numpy()
+    assert _rel(uv, ref) <= FP32_TOL, _rel(uv, ref)
+    # the ring corrections are there: without them the FMM is off the bar
+    plain = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.p, w.L, w.root)
+    assert _rel(plain, ref) > FP32_TOL, _rel(plain, ref)
+
+
 # (n, L, sigma / h, a / leaf width): the ring sources of every leaf fit one
 # shared-memory chunk (at most 558) from whole leaves and from strips alike;
 # strips are used up to a = 1.5 leaf widths (half-leaf strips)
