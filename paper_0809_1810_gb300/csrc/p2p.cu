@@ -1695,14 +1695,14 @@ cudaError_t launch_near_only_f32(const Geometry& g, double sigma, int64_t n,
 // first two targets, are all issued before the expansion is formed.
 // Otherwise the near parts are read back at the targets' input indices, leaf
 // by leaf.
-template <bool kSorted>
+template <bool kSorted, bool kLanes>
 __global__ void __launch_bounds__(kLeafWarps * 32)
 l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start, Geometry g,
                float sc, float kzeta, float inv_s, const float* __restrict__ le,
                const float* __restrict__ l2l, const float2* __restrict__ uvs,
                float* __restrict__ uv, uint32_t lane_nt) {
     __shared__ float2 leaf_le[kLeafWarps][kMaxP];
-    __shared__ float2 parts[kLeafWarps][2][kMaxP];
+    __shared__ float2 parts[kLeafWarps][kLanes ? 2 : 1][kLanes ? kMaxP : 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t leaf = blockIdx.x * kLeafWarps + warp;
     if (leaf >= (1u << (2 * g.L))) return;  // warp-uniform
@@ -1723,7 +1723,7 @@ l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_
     // a leaf of the per-target-lane pass: its far field as that pass forms it
     // (the expansion's two parts, l2p_two_levels)
     auto lane_leaf = [&](uint32_t t0, uint32_t t1) {
-        stage_two_levels(g, le, lx, ly, parts[warp][0], parts[warp][1]);
+        stage_two_levels(g, le, lx, ly, parts[warp][0], parts[warp][kLanes ? 1 : 0]);
         __syncwarp();
         for (uint32_t k = t0 + lane; k < t1; k += 32) {
             const float4 rec = sp[k];
@@ -1738,8 +1738,9 @@ l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_
                 v = uv[2 * (int64_t)idx + 1];
             }
             const float x = ((rec.x - cxh) - cxl) * sc, y = ((rec.y - cyh) - cyl) * sc;
-            l2p_two_levels(g.p, kzeta, inv_s, parts[warp][0], g.L >= 3 ? parts[warp][1] : nullptr,
-                           lx & 1u, ly & 1u, x, y, u, v);
+            l2p_two_levels(g.p, kzeta, inv_s, parts[warp][0],
+                           g.L >= 3 ? parts[warp][kLanes ? 1 : 0] : nullptr, lx & 1u, ly & 1u,
+                           x, y, u, v);
             if (kSorted && uv8) {
                 *reinterpret_cast<float2*>(uv + 2 * (int64_t)idx) = make_float2(u, v);
             } else {
@@ -1752,7 +1753,7 @@ l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_
         const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
         if (t0 == t1) return;
         leaf_centre_hilo(g, lx, ly, &cxh, &cxl, &cyh, &cyl);
-        if (t1 - t0 <= lane_nt) {
+        if (kLanes && t1 - t0 <= lane_nt) {
             lane_leaf(t0, t1);
             return;
         }
@@ -1768,7 +1769,7 @@ l2p_f32_kernel(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_
     leaf_centre_hilo(g, lx, ly, &cxh, &cxl, &cyh, &cyl);
     const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
     if (t0 == t1) return;
-    if (t1 - t0 <= lane_nt) {
+    if (kLanes && t1 - t0 <= lane_nt) {
         lane_leaf(t0, t1);
         return;
     }
@@ -1808,12 +1809,16 @@ cudaError_t launch_l2p_f32(const Geometry& g, double sigma, int64_t n, const voi
     const unsigned blocks = (unsigned)(((uint64_t)1 << (2 * g.L)) / kLeafWarps);
     const float4* sp = reinterpret_cast<const float4*>(particles);
     const float2* uvs = reinterpret_cast<const float2*>(uv_sorted);
+    // the lane pass's leaves compiled in only where there are some: their
+    // branch costs the dense evaluations that never take it
+    auto run = [&](auto kernel) {
+        kernel<<<blocks, kLeafWarps * 32, 0, s>>>(sp, leaf_start, g, nm.sc, nm.kzeta, nm.inv_s, le,
+                                                  l2l, uvs, uv, lane_nt);
+    };
     if (uv_sorted)
-        l2p_f32_kernel<true><<<blocks, kLeafWarps * 32, 0, s>>>(
-            sp, leaf_start, g, nm.sc, nm.kzeta, nm.inv_s, le, l2l, uvs, uv, lane_nt);
+        lane_nt ? run(l2p_f32_kernel<true, true>) : run(l2p_f32_kernel<true, false>);
     else
-        l2p_f32_kernel<false><<<blocks, kLeafWarps * 32, 0, s>>>(
-            sp, leaf_start, g, nm.sc, nm.kzeta, nm.inv_s, le, l2l, uvs, uv, lane_nt);
+        lane_nt ? run(l2p_f32_kernel<false, true>) : run(l2p_f32_kernel<false, false>);
     return cudaGetLastError();
 }
 
