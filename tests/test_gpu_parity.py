@@ -217,6 +217,26 @@ def test_above_the_l2_threshold_every_output():
         assert _rel(uv, ref) <= FP32_TOL, (a, _rel(uv, ref))
 
 
+def test_above_the_l2_threshold_sparse_leaves():
+    """The same size at L = 9 (20 particles per leaf on average): the leaves
+    of at most 16 take the per-target-lane pass, whose near parts also go to
+    the input indices here, and L2P forms their far field from the two
+    expansion parts there.  Every output against the oracle FMM, with and
+    without the cutoff (a = 5 sigma, 1.1 leaf widths: the ring strips)."""
+    n = 5 << 20
+    w = W.uniform_random(n, 78, 2.0 / np.sqrt(n), sigma_over_h=1.0, p=12, L=9,
+                         dtype=np.float32)
+    assert w.n <= 32 << (2 * w.L)
+    xy, g = _dev(w, torch.float32)
+    for a in (0.0, 5.0 * w.sigma):
+        from paper_0809_1810_gb300 import Plan
+
+        with Plan(w.p, w.L, w.sigma, "fp32_tc", root=w.root, max_n=w.n, cutoff=a) as plan:
+            uv = plan.velocity(xy, g, check=True).double().cpu().numpy()
+        ref = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.p, w.L, w.root, a=a)
+        assert _rel(uv, ref) <= FP32_TOL, (a, _rel(uv, ref))
+
+
 def test_clustered_16m_against_direct_sum():
     """The large clustered workload (2^24 particles in 64 Gaussian patches,
     sigma = h, p = 20, L = 9, uneven leaf occupancy) in FP32_TC: the GPU FP64
