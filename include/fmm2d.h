@@ -126,7 +126,9 @@ fmm2d_status fmm2d_velocity_host(fmm2d_plan* plan, int64_t n, const void* xy_hos
  *   xy_host[k], gamma_host[k], uv_host[k]   the host buffers of set k, as in
  *              fmm2d_velocity_host (page-locked, or the copies cannot overlap)
  * Allocates on first use two more staging sets of max_n particles, two
- * streams and eight events, kept until the plan is destroyed.  Returns after
+ * streams and eight events, kept until the plan is destroyed, and (without
+ * phase timing) records one evaluation graph per staging set for each new n,
+ * reading that set's inputs and writing its output set directly.  Returns after
  * the last set's velocities are in host memory, with the device-detected
  * status of all sets (fmm2d_plan_check).  Errors: FMM2D_INVALID_ARG for
  * count < 0, n outside [0, max_n] or a null buffer. */

@@ -71,6 +71,11 @@ struct fmm2d_plan {
     void* pipe_in_xy[2]{}, *pipe_in_g[2]{}, *pipe_out[2]{};
     cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr;
     cudaEvent_t pipe_staged[2]{}, pipe_consumed[2]{}, pipe_result[2]{}, pipe_drained[2]{};
+    // one recorded evaluation per staging set (reading its inputs and writing
+    // its output set directly), for n = pipe_n
+    cudaGraph_t pipe_graph[2]{};
+    cudaGraphExec_t pipe_exec[2]{};
+    int64_t pipe_n = -1;
     // graph cache
     cudaStream_t cap = nullptr;
     // FP32 forms: the far field's branch of the graph and its fork/join events
@@ -312,7 +317,7 @@ cudaError_t enqueue_partial(fmm2d_plan* pl, bool upward, int64_t n, const R* xy,
 }
 #undef STEP
 
-void drop_graph(fmm2d_plan* pl) {
+void drop_main_graph(fmm2d_plan* pl) {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->graph) cudaGraphDestroy(pl->graph);
     pl->exec = nullptr;
@@ -320,8 +325,20 @@ void drop_graph(fmm2d_plan* pl) {
     pl->g_n = -1;
 }
 
+// Every recorded evaluation (a setting recorded in the kernels changed).
+void drop_graph(fmm2d_plan* pl) {
+    drop_main_graph(pl);
+    for (int b = 0; b < 2; ++b) {
+        if (pl->pipe_exec[b]) cudaGraphExecDestroy(pl->pipe_exec[b]);
+        if (pl->pipe_graph[b]) cudaGraphDestroy(pl->pipe_graph[b]);
+        pl->pipe_exec[b] = nullptr;
+        pl->pipe_graph[b] = nullptr;
+    }
+    pl->pipe_n = -1;
+}
+
 fmm2d_status record_graph(fmm2d_plan* pl, int64_t n, const void* xy, const void* gamma, void* uv) {
-    drop_graph(pl);
+    drop_main_graph(pl);
     CK(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = pl->elem == 8
                         ? enqueue<double>(pl, n, static_cast<const double*>(xy),
@@ -765,6 +782,25 @@ fmm2d_status fmm2d_velocity_host_many(fmm2d_plan* pl, int count, int64_t n,
     sst = ensure_pipe(pl);
     if (sst != FMM2D_OK) return sst;
     const size_t bxy = 2 * (size_t)n * pl->elem, bg = (size_t)n * pl->elem;
+    // one recorded evaluation per staging set, so that no copy between the
+    // staging sets and the plan's buffers is needed (not with phase timing,
+    // whose marks belong to the plan's own graph)
+    const bool direct = pl->ring == 0;
+    if (direct && pl->pipe_n != n) {
+        for (int b = 0; b < 2; ++b) {
+            fmm2d_status st = record_graph(pl, n, pl->pipe_in_xy[b], pl->pipe_in_g[b],
+                                           pl->pipe_out[b]);
+            if (st != FMM2D_OK) return st;
+            if (pl->pipe_exec[b]) cudaGraphExecDestroy(pl->pipe_exec[b]);
+            if (pl->pipe_graph[b]) cudaGraphDestroy(pl->pipe_graph[b]);
+            pl->pipe_graph[b] = pl->graph;  // moved out of the plan's own cache
+            pl->pipe_exec[b] = pl->exec;
+            pl->graph = nullptr;
+            pl->exec = nullptr;
+            pl->g_n = -1;
+        }
+        pl->pipe_n = n;
+    }
     // the copy streams start after whatever `stream` has queued before this call
     CK(cudaEventRecord(pl->pipe_consumed[0], stream));
     CK(cudaEventRecord(pl->pipe_consumed[1], stream));
@@ -779,6 +815,21 @@ fmm2d_status fmm2d_velocity_host_many(fmm2d_plan* pl, int count, int64_t n,
         CK(cudaMemcpyAsync(pl->pipe_in_g[b], gamma_host[k], bg, cudaMemcpyHostToDevice,
                            pl->pipe_h2d));
         CK(cudaEventRecord(pl->pipe_staged[b], pl->pipe_h2d));
+        if (direct) {
+            // set b's own graph: reads staging set b, writes output set b once
+            // set k - 2's velocities have been read back from it
+            CK(cudaStreamWaitEvent(stream, pl->pipe_staged[b], 0));
+            CK(cudaStreamWaitEvent(stream, pl->pipe_drained[b], 0));
+            CK(cudaGraphLaunch(pl->pipe_exec[b], stream));
+            pl->calls++;
+            CK(cudaEventRecord(pl->pipe_consumed[b], stream));
+            CK(cudaEventRecord(pl->pipe_result[b], stream));
+            CK(cudaStreamWaitEvent(pl->pipe_d2h, pl->pipe_result[b], 0));
+            CK(cudaMemcpyAsync(uv_host[k], pl->pipe_out[b], bxy, cudaMemcpyDeviceToHost,
+                               pl->pipe_d2h));
+            CK(cudaEventRecord(pl->pipe_drained[b], pl->pipe_d2h));
+            continue;
+        }
         // the evaluation reads the plan's fixed buffers (one recorded graph)
         CK(cudaStreamWaitEvent(stream, pl->pipe_staged[b], 0));
         CK(cudaMemcpyAsync(pl->st_xy, pl->pipe_in_xy[b], bxy, cudaMemcpyDeviceToDevice, stream));
